@@ -157,6 +157,23 @@ def vector_dofs(S):
     return V
 
 
+def remove_rigid_motion(p, ue, hx=1.0, hy=1.0):
+    """u_e minus its least-squares rigid motion (translation and infinitesimal rotation).
+
+    Every K0_s annihilates rigid motions, so u^T K0_s u, K_e u and the QR energies are unchanged
+    in exact arithmetic; removing the (often dominant) rigid part first avoids the cancellation
+    that otherwise costs digits when an element moves far but strains little."""
+    xy = node_coords(p, hx, hy)
+    xc = xy[:, 0] - xy[:, 0].mean()
+    yc = xy[:, 1] - xy[:, 1].mean()
+    ux, uy = ue[0::2], ue[1::2]
+    om = np.sum(xc * uy - yc * ux) / np.sum(xc * xc + yc * yc)
+    out = np.empty_like(ue)
+    out[0::2] = ux - ux.mean() + om * yc
+    out[1::2] = uy - uy.mean() - om * xc
+    return out
+
+
 def node_coords(p, hx=1.0, hy=1.0):
     """Physical coordinates (x, y) of the (p+1)^2 local nodes, in local node order."""
     z = gll_nodes(p)

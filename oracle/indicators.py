@@ -13,7 +13,7 @@ import numpy as np
 import scipy.linalg
 
 from .basis import gauss_legendre
-from .element import (interpolation_matrix, scalar_mass, shape_grad, simp, vector_dofs)
+from .element import (interpolation_matrix, remove_rigid_motion, scalar_mass, shape_grad, simp, vector_dofs)
 from .solve import K0_table
 
 
@@ -144,8 +144,12 @@ def qr_error_element(p, d, rho_e, ue, E0, Emin, nu, q, hx=1.0, hy=1.0, fixed=Non
     u^(p+1): 3 DOFs copied from the interpolant T u^(p) (bottom-left u_x, u_y; bottom-right u_y),
     the rest from K^(p+1) u = f^(p+1) by dense Cholesky.  J = 1/2 u^T K u for both orders.
     When J^(p+1) = 0 (rigid or zero u) eps is 0.  ``fixed`` overrides the three pinned local DOFs of
-    the order-(p+1) problem (any set that removes the rigid modes gives the same eps).
+    the order-(p+1) problem (any set that removes the rigid modes gives the same eps).  eps does not
+    change when a rigid motion is added to u^(p) (f^(p), both energies and the relative solution are
+    unchanged), so the element's rigid motion is removed first to keep the energies free of
+    cancellation.
     """
+    ue = remove_rigid_motion(p, np.asarray(ue, dtype=np.float64), hx, hy)
     E = simp(rho_e, E0, Emin, q)
     Kp = np.tensordot(E, K0_table(p, d, nu, hx, hy), axes=(0, 0))
     K1 = np.tensordot(E, K0_table(p + 1, d, nu, hx, hy), axes=(0, 0))

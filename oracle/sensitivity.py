@@ -7,11 +7,13 @@ self-adjoint (adjoint lambda = -u), and with the composite stiffness K_e = sum_s
 
     dC/drho_s = -E'(rho_s) u_e^T K0[s] u_e,      E'(rho) = q rho^(q-1) (E0 - Emin).
 
-The oracle evaluates each quadratic form naively with a dense K0[s] matrix-vector product.
+The oracle evaluates each quadratic form naively with a dense K0[s] matrix-vector product, after
+removing the element's rigid motion (which every K0[s] annihilates) so that no digits are lost to
+cancellation.
 """
 import numpy as np
 
-from .element import simp, simp_deriv
+from .element import remove_rigid_motion, simp, simp_deriv
 from .solve import K0_table
 
 
@@ -25,7 +27,7 @@ def subcell_energies(mesh, u, nu):
     w = np.zeros(mesh.design_len)
     for e in range(mesh.nel):
         p, d = int(mesh.p[e]), int(mesh.d[e])
-        ue = mesh.gather(e, u)
+        ue = remove_rigid_motion(p, mesh.gather(e, u), mesh.hx, mesh.hy)
         K0 = K0_table(p, d, nu, mesh.hx, mesh.hy)
         off = mesh.design_off[e]
         for s in range(d * d):

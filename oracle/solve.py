@@ -55,26 +55,37 @@ def free_dofs(ndof, fixed):
     return np.nonzero(mask)[0]
 
 
-def solve_direct(K, f, fixed):
+def solve_direct(K, f, fixed, refine=3):
     """Exact solve of the supported system: dense Cholesky for small systems (library primitive),
-    sparse LU (SuperLU, library primitive) otherwise.  Returns the full-length u (0 on supports)."""
+    sparse LU (SuperLU, library primitive) otherwise.  The system is first equilibrated with the
+    symmetric diagonal scaling S = diag(A)^-1/2 (A -> S A S, b -> S b, u = S y), which removes the
+    1e9 row-scale spread that Emin = 1e-9 E0 creates, then ``refine`` steps of FP64 iterative
+    refinement y += Ahat^-1 (bhat - Ahat y) follow.  Returns the full-length u (0 on supports)."""
     free = free_dofs(K.shape[0], fixed)
-    Kff = K[free][:, free]
-    u = np.zeros(K.shape[0])
+    Kff = K[free][:, free].tocsr()
+    s = 1.0 / np.sqrt(Kff.diagonal())
+    Ahat = (scipy.sparse.diags(s) @ Kff @ scipy.sparse.diags(s)).tocsr()
+    b = s * f[free]
     if len(free) <= 4000:
-        c = scipy.linalg.cho_factor(Kff.toarray(), lower=True)
-        u[free] = scipy.linalg.cho_solve(c, f[free])
+        c = scipy.linalg.cho_factor(Ahat.toarray(), lower=True)
+        solve1 = lambda r: scipy.linalg.cho_solve(c, r)
     else:
-        lu = scipy.sparse.linalg.splu(Kff.tocsc(), permc_spec="MMD_AT_PLUS_A")
-        u[free] = lu.solve(f[free])
+        lu = scipy.sparse.linalg.splu(Ahat.tocsc(), permc_spec="MMD_AT_PLUS_A")
+        solve1 = lu.solve
+    y = solve1(b)
+    for _ in range(refine):
+        y = y + solve1(b - Ahat @ y)
+    u = np.zeros(K.shape[0])
+    u[free] = s * y
     return u
 
 
-def pcg(K, f, fixed, rtol=1e-12, maxiter=200000, x0=None):
+def pcg(K, f, fixed, rtol=1e-12, maxiter=200000, x0=None, scaled=False):
     """Plain FP64 Jacobi-preconditioned conjugate gradients on the supported system.
 
-    Textbook PCG (Hestenes-Stiefel with z = D^-1 r), stopped when ||r||_2 <= rtol ||f||_2.
-    Returns (u, iterations, final relative residual).
+    Textbook PCG (Hestenes-Stiefel with z = D^-1 r), stopped when ||r|| <= rtol ||f|| in the l2
+    norm, or in the D^-1 norm (||r||^2 = r^T D^-1 r) when ``scaled``.
+    Returns (u, iterations, final relative residual in that norm).
     """
     free = free_dofs(K.shape[0], fixed)
     A = K[free][:, free].tocsr()
@@ -85,9 +96,10 @@ def pcg(K, f, fixed, rtol=1e-12, maxiter=200000, x0=None):
     z = dinv * r
     pdir = z.copy()
     rz = r @ z
-    nb = np.linalg.norm(b)
+    norm = (lambda v: np.sqrt(v @ (dinv * v))) if scaled else np.linalg.norm
+    nb = norm(b)
     it = 0
-    while np.linalg.norm(r) > rtol * nb and it < maxiter:
+    while norm(r) > rtol * nb and it < maxiter:
         qv = A @ pdir
         alpha = rz / (pdir @ qv)
         x += alpha * pdir
@@ -99,7 +111,7 @@ def pcg(K, f, fixed, rtol=1e-12, maxiter=200000, x0=None):
         it += 1
     u = np.zeros(K.shape[0])
     u[free] = x
-    return u, it, np.linalg.norm(r) / nb
+    return u, it, norm(r) / nb
 
 
 def solve(mesh, rho, fixed, f, E0=1.0, Emin=1e-9, nu=0.3, q=3.0):

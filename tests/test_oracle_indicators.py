@@ -118,6 +118,27 @@ def test_qr_error_range_and_fixed_dof_independence():
             assert abs(e1 - e3) < 1e-10
 
 
+def test_qr_error_invariant_to_rigid_motion():
+    """eps is unchanged by adding a rigid motion to u^(p) (checked at a magnitude where the
+    unremoved computation is still accurate)."""
+    from oracle.element import remove_rigid_motion
+    rng = np.random.default_rng(5)
+    for p in (1, 2, 3):
+        xy = node_coords(p)
+        ue = 1e-3 * rng.standard_normal(2 * len(xy))
+        r = np.zeros_like(ue)
+        r[0::2] = 0.3 - 0.02 * xy[:, 1]
+        r[1::2] = -0.1 + 0.02 * xy[:, 0]
+        e1 = qr_error_element(p, 2, rng.uniform(0.1, 1, 4), ue, 1.0, 1e-9, 0.3, 3.0)
+        e2 = qr_error_element(p, 2, rng.uniform(0.1, 1, 4) * 0 + 1, ue + r, 1.0, 1e-9, 0.3, 3.0)
+        e3 = qr_error_element(p, 2, np.ones(4), ue, 1.0, 1e-9, 0.3, 3.0)
+        assert abs(e2 - e3) < 1e-10
+        # the removed part is exactly rigid: K annihilates the difference
+        Kh = subcell_stiffness(p, 1, 0.3)[0]
+        dlt = (ue + r) - remove_rigid_motion(p, ue + r)
+        assert np.abs(Kh @ dlt).max() < 1e-14
+
+
 def test_qr_error_zero_displacement():
     assert qr_error_element(2, 4, np.ones(16), np.zeros(18), 1.0, 1e-9, 0.3, 3.0) == 0.0
 

@@ -85,6 +85,15 @@ def pack_mixed(fine, nelx, nely, d_map, r):
     return np.concatenate(out).astype(np.float64)
 
 
+def _frame_bias(ny, nx, width):
+    """1 on a band of ``width`` cells along all four sides of an ny x nx grid, else 0: a load-carrying
+    frame, so that loads and supports always sit in material."""
+    b = np.zeros((ny, nx))
+    b[:width, :] = b[-width:, :] = 1.0
+    b[:, :width] = b[:, -width:] = 1.0
+    return b
+
+
 def _threshold_volume(s, vol):
     """Binary 0/1 field with exactly round(vol * size) ones at the largest values of s."""
     flat = s.ravel()
@@ -92,6 +101,34 @@ def _threshold_volume(s, vol):
     out = np.zeros(flat.size)
     out[np.argsort(-flat, kind="stable")[:k]] = 1.0
     return out.reshape(s.shape)
+
+
+def _connected_threshold(s, vol, seed_mask):
+    """Binary 0/1 field with exactly round(vol * size) ones, grown from ``seed_mask`` through
+    4-connected cells in decreasing order of s (a priority flood), so every solid cell is connected
+    to the seed: no floating solid islands."""
+    import heapq
+    ny, nx = s.shape
+    k = int(round(vol * s.size))
+    out = np.zeros(s.size, dtype=bool)
+    flat = s.ravel()
+    heap = [(-flat[i], int(i)) for i in np.flatnonzero(seed_mask.ravel())]
+    heapq.heapify(heap)
+    queued = np.zeros(s.size, dtype=bool)
+    queued[[i for _, i in heap]] = True
+    count = 0
+    while heap and count < k:
+        _, i = heapq.heappop(heap)
+        out[i] = True
+        count += 1
+        y, x = divmod(i, nx)
+        for yy, xx in ((y - 1, x), (y + 1, x), (y, x - 1), (y, x + 1)):
+            if 0 <= yy < ny and 0 <= xx < nx:
+                j = yy * nx + xx
+                if not queued[j]:
+                    queued[j] = True
+                    heapq.heappush(heap, (-flat[j], j))
+    return out.reshape(s.shape).astype(np.float64)
 
 
 def _sigmoid_volume(s, vol, width=0.35, floor=1e-3):
@@ -116,12 +153,18 @@ def cantilever_small(nelx=20, nely=10, p=2, d=4, seed_index=1):
                    np.full(nel, d, np.int32), rho, CANTILEVER)
 
 
-def mbb_binary(nelx=160, nely=80, p=3, d=8, vol=0.3, sigma=8.0, seed_index=2):
+def mbb_binary(nelx=160, nely=80, p=3, d=8, vol=0.3, sigma=8.0, seed_index=2, connected=True):
     """MBB half-beam, uniform order and design count, a Gaussian-smoothed white-noise field
-    (std sigma design cells) thresholded to exactly ``vol`` material (0/1 densities)."""
+    (std sigma design cells) thresholded to exactly ``vol`` material (0/1 densities).  A solid frame
+    one element wide (at least 1/20 of the height) is selected first, so the load path exists.
+    ``connected``: the threshold is a priority flood from the frame (every solid cell connected to
+    it); otherwise a plain threshold, which leaves floating solid islands held only by void."""
     rng = np.random.default_rng(SEED_BASE + seed_index)
     s = _smooth_noise(rng, nely * d, nelx * d, sigma)
-    rho = pack_uniform(_threshold_volume(s, vol), nelx, nely, d)
+    frame = _frame_bias(nely * d, nelx * d, max(d, (nely * d) // 20))
+    s = s + 100.0 * frame
+    field = _connected_threshold(s, vol, frame > 0) if connected else _threshold_volume(s, vol)
+    rho = pack_uniform(field, nelx, nely, d)
     nel = nelx * nely
     return Problem(f"mbb_{nelx}x{nely}_p{p}_d{d}_binary{vol}", nelx, nely, np.full(nel, p, np.int32),
                    np.full(nel, d, np.int32), rho, MBB)
@@ -131,6 +174,7 @@ def mbb_smooth(nelx=1024, nely=512, p=3, d=8, vol=0.2, sigma=8.0, seed_index=5):
     """MBB half-beam with smooth densities in [1e-3, 1] at mean ``vol`` (a logistic of smoothed noise)."""
     rng = np.random.default_rng(SEED_BASE + seed_index)
     s = _smooth_noise(rng, nely * d, nelx * d, sigma)
+    s = s + 4.0 * _frame_bias(nely * d, nelx * d, max(d, (nely * d) // 40))
     rho = pack_uniform(_sigmoid_volume(s, vol), nelx, nely, d)
     nel = nelx * nely
     return Problem(f"mbb_{nelx}x{nely}_p{p}_d{d}_smooth{vol}", nelx, nely, np.full(nel, p, np.int32),
@@ -148,6 +192,7 @@ def dp_cantilever(nelx=320, nely=160, vol=0.1, seed_index=3, p_levels=(1, 2, 3, 
     rng = np.random.default_rng(SEED_BASE + seed_index)
     r = 8
     s = _smooth_noise(rng, nely * r, nelx * r, 3.0 * r)
+    s = s + 4.0 * _frame_bias(nely * r, nelx * r, max(r, (nely * r) // 40))
     fine = _sigmoid_volume(s, vol)
     # per-element gradient magnitude of the element-mean density
     em = fine.reshape(nely, r, nelx, r).mean(axis=(1, 3))
@@ -180,6 +225,7 @@ def batched(n_instances=64, seed_index=4, sizes=((40, 20), (80, 40), (160, 80), 
         d = int(rng.choice(d_levels))
         vol = float(rng.uniform(0.3, 0.5))
         s = _smooth_noise(rng, nely * d, nelx * d, 2.0 * d)
+        s = s + 100.0 * _frame_bias(nely * d, nelx * d, max(d, (nely * d) // 20))
         rho = pack_uniform(_threshold_volume(s, vol), nelx, nely, d)
         nel = nelx * nely
         out.append(Problem(f"inst{k}_{nelx}x{nely}_p{p}_d{d}", nelx, nely, np.full(nel, p, np.int32),
@@ -193,6 +239,7 @@ def named(name):
         "cantilever_20x10_p2_d4": lambda: cantilever_small(),
         "mbb_160x80_p3_d8": lambda: mbb_binary(),
         "mbb_40x20_p3_d8": lambda: mbb_binary(40, 20, sigma=4.0, seed_index=12),
+        "mbb_40x20_p3_d8_islands": lambda: mbb_binary(40, 20, sigma=4.0, seed_index=12, connected=False),
         "dp_cantilever_320x160": lambda: dp_cantilever(),
         "dp_cantilever_40x20": lambda: dp_cantilever(40, 20, seed_index=13),
         "mbb_1024x512_p3_d8": lambda: mbb_smooth(),
