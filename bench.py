@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the dp-adaptive MTO hot path on GB300.
+
+Metric: TO iterations/s (solve + sensitivity) and MDOF x PCG-iterations/s, mixed precision vs the
+plain FP64 GPU path.  One step = one pass of the whole hot path over one design: element build
+(step a), PCG solve to the stated residual from a zero start (b), compliance and sensitivities (c)
+and the composite indicator with the dp map update (d).
+
+Default workload: the 160 x 80 MBB half-beam, Q3 elements with 8 x 8 design subcells (1280 x 640
+density field), a seeded binary design at volume fraction 0.3, Emin = 1e-9 E0, relative residual
+1e-8 (l2).  Both paths run the same steps; `value` is the mixed path.
+
+Multi-GPU: every rank solves its own replica (independent problems, no data-path collective);
+value = total steps of all ranks / max over ranks of the timed wall.  The oracle (CPU, FP64) is
+timed on a bounded sample as `cpu_baseline`; `--impl reference` times only the oracle.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TO iterations/s (solve+sensitivity) & MDOF·PCG-iter/s, mixed vs plain FP64 GPU"
+UNIT = "TO-iter/s"
+DEFAULT_WORKLOAD = "mbb_160x80_p3_d8"
+SAMPLE_WORKLOAD = {"mbb_160x80_p3_d8": "mbb_40x20_p3_d8", "dp_cantilever_320x160": "dp_cantilever_40x20",
+                   "cantilever_20x10_p2_d4": "cantilever_20x10_p2_d4", "mbb_40x20_p3_d8": "mbb_40x20_p3_d8",
+                   "mbb_1024x512_p3_d8": "mbb_40x20_p3_d8"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------ CPU oracle
+def oracle_step_script(workload):
+    """Python source that times one full oracle pass (build, assemble, exact solve, sensitivity,
+    indicators, map update) on `workload` and prints JSON."""
+    return f"""
+import json, sys, time
+sys.path.insert(0, {ROOT!r})
+import workloads as W
+from oracle import mesh as om, solve as osv, sensitivity as ose, indicators as oi
+pr = W.named({workload!r})
+t0 = time.perf_counter()
+m = om.DPMesh(pr.nelx, pr.nely, pr.p, pr.d)
+fixed, f = (om.mbb_bc if pr.load == W.MBB else om.cantilever_bc)(m)
+K = osv.assemble(m, osv.element_matrices(m, pr.rho, pr.E0, pr.Emin, pr.nu, pr.q))
+u = osv.solve_direct(K, f, fixed)
+t1 = time.perf_counter()
+dc = ose.sensitivity(m, u, pr.rho, pr.E0, pr.Emin, pr.nu, pr.q)
+C = ose.compliance(f, u)
+t2 = time.perf_counter()
+ga = oi.kelly(m, u); gd = oi.gamma_d(m, pr.rho); eq = oi.qr_error(m, u, pr.rho, pr.E0, pr.Emin, pr.nu, pr.q)
+oi.map_update(pr.nelx, pr.nely, pr.p, ga, gd, eq)
+t3 = time.perf_counter()
+print(json.dumps(dict(seconds=t3 - t0, build_solve=t1 - t0, sens=t2 - t1, indicator=t3 - t2,
+                      free_dofs=int(m.ndof - len(fixed)), C=C)))
+"""
+
+
+def run_oracle_sample(workload, steps=1):
+    """Time the oracle single-threaded (BLAS/OpenMP pinned to 1 thread) on a bounded sample of the
+    workload; returns (seconds per pass, info)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    res = []
+    for _ in range(steps):
+        r = subprocess.run([sys.executable, "-c", oracle_step_script(workload)], capture_output=True, text=True,
+                           env=env, timeout=900)
+        if r.returncode != 0:
+            raise RuntimeError(r.stderr[-2000:])
+        res.append(json.loads(r.stdout.strip().splitlines()[-1]))
+    return statistics.median(x["seconds"] for x in res), res[-1]
+
+
+def free_dofs_of(workload):
+    import workloads as W
+    from oracle import mesh as om
+    pr = W.named(workload)
+    m = om.DPMesh(pr.nelx, pr.nely, pr.p, pr.d)
+    fixed, _ = (om.mbb_bc if pr.load == W.MBB else om.cantilever_bc)(m)
+    return int(m.ndof - len(fixed))
+
+
+def cpu_baseline(workload, steps=1):
+    """Oracle on the bounded sample, scaled to the workload by free DOFs (the oracle's cost grows
+    at least linearly with the DOFs, so the scaled rate is an upper bound on its full-size rate)."""
+    sample = SAMPLE_WORKLOAD.get(workload, workload)
+    sec, info = run_oracle_sample(sample, steps)
+    scale = info["free_dofs"] / free_dofs_of(workload)
+    value = scale / sec
+    return dict(value=value, unit=UNIT, cores=1, kind="oracle",
+                sample=f"{sample}: one full oracle pass (assemble, equilibrated sparse LU + refinement, "
+                       f"sensitivity, indicators, map update) in {sec:.2f} s single-threaded, scaled by free "
+                       f"DOFs {info['free_dofs']}/{free_dofs_of(workload)}")
+
+
+# ------------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.lines = index, None, []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------ GPU arm
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import paper_1811_09821_gb300 as mto
+    import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pr = W.named(args.workload)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    h = mto.Handle(local_rank, stream=stream)
+    ndof, dlen = h.setup(pr.nelx, pr.nely, pr.p, pr.d)
+    fixed, f = mto.load_case(h, pr.load)
+    h.set_supports(fixed)
+    nfree = ndof - len(fixed)
+    mat = mto.material(pr.E0, pr.Emin, pr.nu, pr.q)
+    rho = torch.tensor(pr.rho, dtype=torch.float64, device=dev)
+    u = torch.zeros(ndof, dtype=torch.float64, device=dev)
+    dc = torch.zeros(dlen, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
+
+    def step(prec):
+        h.build_elements(rho, mat, prec)
+        it, rr = h.solve(f, u, precision=prec, rtol=args.rtol, max_iter=400000, check_every=64)
+        C = h.sensitivity(u, f, rho, mat, dc, precision=prec, want_C=False)
+        h.indicator(u, rho, mat)
+        return it, rr
+
+    def timed(prec, steps, warmup):
+        for _ in range(warmup):
+            step(prec)
+        torch.cuda.synchronize(dev)
+        h.timing_enable(True)
+        l0 = h.launch_count()
+        total_ms, iters, rrs = 0.0, 0, []
+        for _ in range(steps):
+            flush.fill_(1.0)                     # L2 flush outside the timed step
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            it, rr = step(prec)
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            iters += it
+            rrs.append(rr)
+        tm = h.timing_read()
+        h.timing_enable(False)
+        return dict(ms=total_ms, iters=iters, relres=max(rrs), launches=h.launch_count() - l0, families=tm)
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local_rank) as clk:
+        wall0 = time.perf_counter()
+        mixed = timed(mto.MTO_MIXED, args.steps, args.warmup)
+        wall1 = time.perf_counter()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([mixed["ms"]], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        mixed_ms_max = float(t.item())
+    else:
+        mixed_ms_max = mixed["ms"]
+    C_mixed = h.sensitivity(u, f, rho, mat, dc, precision=mto.MTO_MIXED)
+
+    fp64 = None
+    if not args.no_fp64:
+        fp64 = timed(mto.MTO_FP64, max(1, min(args.steps, 3)), 1)
+        C_fp64 = h.sensitivity(u, f, rho, mat, dc, precision=mto.MTO_FP64)
+
+    # end to end through the public API with host buffers: pinned rho and f in, u and dc out
+    rho_h = torch.tensor(pr.rho, dtype=torch.float64).pin_memory()
+    f_h = f.cpu().pin_memory()
+    u_h = torch.empty(ndof, dtype=torch.float64).pin_memory()
+    dc_h = torch.empty(dlen, dtype=torch.float64).pin_memory()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        rho.copy_(rho_h, non_blocking=True)
+        f.copy_(f_h, non_blocking=True)
+        h.build_elements(rho, mat, mto.MTO_MIXED)
+        h.solve(f, u, precision=mto.MTO_MIXED, rtol=args.rtol, max_iter=400000, check_every=64)
+        h.sensitivity(u, f, rho, mat, dc, precision=mto.MTO_MIXED, want_C=False)
+        h.indicator(u, rho, mat)
+        u_h.copy_(u, non_blocking=True)
+        dc_h.copy_(dc, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    n_apply, apply_ms = mixed["families"]["apply32"]
+    # algorithmic bytes of one inner operator launch: the split-precision pair of the packed K_e
+    # (2 x 4 bytes per entry, 528 entries for Q3) and the node map per element, one read of x and
+    # one write of y (FP32) per DOF
+    nn = [(int(p) + 1) ** 2 for p in pr.p]
+    kbytes = sum(8 * ((2 * n) * (2 * n + 1) // 2) + 4 * n for n in nn)
+    bytes_per_launch = kbytes + 2 * 4 * ndof
+    ncls = len(set(int(p) for p in pr.p))
+    avg_ms = apply_ms / max(n_apply, 1) * ncls     # one apply = ncls class launches
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9 if n_apply else None
+    steps = args.steps
+    out = {
+        "metric": METRIC,
+        "value": world * steps / (mixed_ms_max * 1e-3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": steps,
+        "warmup": args.warmup,
+        "ms_per_step": mixed_ms_max / steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 inner PCG + f64 refinement/dots/compliance; f64 build, sensitivity in f32 after f64 rigid removal",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "nelx": pr.nelx, "nely": pr.nely, "p": int(pr.p[0]),
+                   "d": int(pr.d[0]), "free_dofs": nfree, "design_values": dlen, "rtol": args.rtol,
+                   "residual_norm": "l2", "l2_flush": "512 MB write between timed steps",
+                   "parallelism": f"replicas x{world}"},
+        "mdof_pcg_iter_per_s": nfree * mixed["iters"] / (mixed["ms"] * 1e-3) / 1e6,
+        "pcg_iters_per_step": mixed["iters"] / steps,
+        "relres": mixed["relres"],
+        "families_ms": {k: round(v[1] / steps, 4) for k, v in mixed["families"].items()},
+        "gpu_launches": mixed["launches"],
+        "roofline": {"bound": "hbm", "kernel": "apply_df_kernel<3,float> (split-precision EbE operator)",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_ms * 1e3,
+                     "note": "peak = measured HBM copy; K_e of this workload is L2-resident across CG iterations"},
+        "clocks": clk.summary(),
+        "e2e": {"value": world * steps / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": 8 * (dlen + ndof), "d2h_bytes_per_step": 8 * (ndof + dlen)},
+    }
+    if fp64:
+        out["fp64_path"] = {"value": fp64["ms"] and (max(1, min(steps, 3)) / (fp64["ms"] * 1e-3)), "unit": UNIT,
+                            "ms_per_step": fp64["ms"] / max(1, min(steps, 3)),
+                            "mdof_pcg_iter_per_s": nfree * fp64["iters"] / (fp64["ms"] * 1e-3) / 1e6,
+                            "pcg_iters_per_step": fp64["iters"] / max(1, min(steps, 3)),
+                            "relres": fp64["relres"],
+                            "families_ms": {k: round(v[1] / max(1, min(steps, 3)), 4) for k, v in fp64["families"].items()}}
+        out["speedup_vs_fp64"] = out["value"] / world / out["fp64_path"]["value"]
+        out["C_rel_diff_mixed_vs_fp64"] = abs(C_mixed - C_fp64) / abs(C_fp64)
+    h.close()
+    return out
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        if world > 1 and False:
+            pass
+        sample = SAMPLE_WORKLOAD.get(args.workload, args.workload)
+        for _ in range(args.warmup):
+            run_oracle_sample(sample, 1)
+        t0 = time.perf_counter()
+        sec, info = run_oracle_sample(sample, args.steps)
+        scale = info["free_dofs"] / free_dofs_of(args.workload)
+        value = scale / sec
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{sample}, median of {args.steps} single-threaded oracle passes "
+                                       f"({sec:.2f} s each), scaled by free DOFs"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }), flush=True)
+        return 0
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    out = run_gpu(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_cpu:
+            try:
+                out["cpu_baseline"] = cpu_baseline(args.workload)
+            except Exception as ex:      # the oracle is only a reported baseline
+                out["cpu_baseline"] = {"error": str(ex)[:300]}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,242 @@
+/*
+ * mto.h - C ABI of the GB300 hot path of dp-adaptive multi-resolution topology optimization
+ * (Gupta, van Keulen, Langelaar, "Design and analysis adaptivity in multi-resolution topology
+ * optimization", arXiv:1811.09821), for 2D linear-elastic compliance problems.
+ *
+ * One analysis-plus-sensitivity pass per design iteration:
+ *   (a) mto_build_elements  K_e = sum_s E(rho_s) K0_s over each element's d x d constant-density
+ *                           subcells, SIMP E(rho) = Emin + rho^q (E0 - Emin)      (Eqs. 2-3, App. B)
+ *   (b) mto_solve           K u = f by matrix-free Jacobi-preconditioned CG, minimum-rule
+ *                           conformity across p-jumps                              (Eq. 1)
+ *   (c) mto_sensitivity     C = f^T u and dC/drho_s = -E'(rho_s) u_e^T K0_s u_e   (self-adjoint)
+ *   (d) mto_indicator       Kelly Gamma^a (Eq. 9), density Gamma^d (Sec. 3.2.2), QR error
+ *                           (Eq. 14) and the dp map update (Sec. 3.3)
+ * plus the optimality-criteria design update mto_oc_update (the paper does not name its optimizer).
+ *
+ * Conventions
+ *  - Mesh: nelx x nely structured quadrilaterals of size hx x hy; element e = ey*nelx + ex.
+ *  - Element order p_e in 1..MTO_P_MAX; per-axis design count d_e in 1..MTO_D_MAX, the element
+ *    carrying d_e^2 constant-density subcells, subcell s = j*d_e + i (i along x).
+ *  - Packed design vectors (rho, dc): element e owns d_e^2 consecutive doubles starting at the
+ *    exclusive prefix sum of d^2 ("design_len" values in total).
+ *  - Global DOF numbering (identical to the oracle's): vertices row-major; interior nodes of
+ *    horizontal edges (edge iy*nelx+ix, left to right); of vertical edges (edge iy*(nelx+1)+ix,
+ *    bottom to top); cell-interior nodes (elements row-major, local nodes row-major);
+ *    DOF = 2*node + component.  An edge carries order min(p_left, p_right) (minimum rule).
+ *  - Pointers documented "device" are caller-owned device memory on the handle's device; "host"
+ *    pointers are caller-owned host memory.  The handle owns its tables and workspace.
+ *  - All device work is enqueued on the handle's stream.  Calls that return host scalars
+ *    (iterations, residuals, compliance) synchronise that stream before returning.
+ *  - Every call returns an mto_status.  On failure the outputs are unspecified and
+ *    mto_last_error(h) gives a message.  Device-side failures (non-convergence, non-finite
+ *    values, bounded waits that expire) are reported through status words read back by the
+ *    host; no kernel traps.
+ */
+#ifndef MTO_H
+#define MTO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MTO_P_MAX 6   /* largest shape-function order accepted by mto_setup (QR uses p+1) */
+#define MTO_D_MAX 16  /* largest per-axis design count */
+
+typedef struct mto_handle_s* mto_handle;
+
+typedef enum {
+  MTO_OK = 0,
+  MTO_EINVAL = 1,    /* bad argument (sizes, ranges, null pointers, call order) */
+  MTO_ENOMEM = 2,    /* device or host allocation failed */
+  MTO_ECUDA = 3,     /* a CUDA runtime call failed */
+  MTO_ENOCONV = 4,   /* the solve hit its iteration limit before the tolerance */
+  MTO_ENAN = 5,      /* a non-finite value or a non-positive diagonal appeared */
+  MTO_ETIMEOUT = 6   /* a bounded device wait expired */
+} mto_status;
+
+typedef enum { MTO_FP64 = 0, MTO_MIXED = 1 } mto_precision;
+
+/* Material of Eq. 3 and Sec. 4.1 (E0 = 1, nu = 0.3, q = 3, Emin = 1e-9 E0 in the paper).
+ * Plane stress. */
+typedef struct {
+  double E0, Emin, nu, q;
+} mto_material;
+
+/* Solver options.
+ *  precision   MTO_FP64: one Jacobi-PCG with FP64 vectors on the built operator.
+ *              MTO_MIXED (needs the MTO_MIXED build): inner Jacobi-PCG with FP32 vectors inside an
+ *              FP64 iterative refinement whose residual r = f - K u uses FP64 vectors; the operator
+ *              is the split-precision pair on the FP32 pipes in both.  Dot products are
+ *              accumulated in FP64 in every mode.
+ *  rtol        stop when ||f - K u||_2 <= rtol ||f||_2 (free DOFs, FP64 residual).
+ *  inner_rtol  MTO_MIXED only: relative residual reduction asked of each inner FP32 solve.
+ *  max_iter    limit on the total number of (inner) PCG iterations.
+ *  max_outer   MTO_MIXED only: limit on refinement steps.
+ *  warm_start  nonzero: u on entry is the initial guess (else zero).
+ *  check_every PCG iterations between host convergence checks (>= 1).
+ *  norm        residual norm of the stopping tests: MTO_NORM_L2 (||r||_2 / ||f||_2) or
+ *              MTO_NORM_JACOBI (sqrt(r^T D^-1 r / f^T D^-1 f), D = diag(K)); the scaled norm also
+ *              weighs the rows of nearly void regions (stiffness ~ Emin), which the l2 norm ignores. */
+typedef struct {
+  int32_t precision;
+  double rtol;
+  double inner_rtol;
+  int32_t max_iter;
+  int32_t max_outer;
+  int32_t warm_start;
+  int32_t check_every;
+  int32_t norm;
+} mto_solve_opts;
+
+#define MTO_NORM_L2 0
+#define MTO_NORM_JACOBI 1
+
+/* Indicator / map-update options (Sec. 3.2, 3.3; values of the paper in brackets).
+ *  cycle           adaptive cycle index k~, from 1                                    [1, 2, ...]
+ *  alpha, beta     density-band tuning parameters of Eqs. 10-13                       [0.2, 0.8]
+ *  frac_a_refine   fraction of elements with the largest Gamma^a raised by one order  [0.10]
+ *  frac_a_coarsen  fraction with the smallest Gamma^a lowered by one order            [0.05]
+ *  alpha_d_refine, alpha_d_coarsen   fractions of the elements with Gamma^d > 0 (resp. < 0)
+ *                  refined (coarsened)                                                [1, 1]
+ *  alpha_qr        QR-error threshold                                                 [0.9]
+ *  p_max, d_max    caps on the order and on the number of design points per element  [5, 64] */
+typedef struct {
+  int32_t cycle;
+  double alpha, beta;
+  double frac_a_refine, frac_a_coarsen;
+  double alpha_d_refine, alpha_d_coarsen;
+  double alpha_qr;
+  int32_t p_max, d_max;
+} mto_indicator_opts;
+
+/* Create a handle bound to CUDA device `device` and CUDA stream `stream` (a cudaStream_t; NULL
+ * means the legacy default stream).  The handle allocates nothing on the device until mto_setup. */
+mto_status mto_create(mto_handle* h, int device, void* stream);
+
+/* Free the handle and all device memory it owns.  Accepts NULL. */
+mto_status mto_destroy(mto_handle h);
+
+/* Message of the last failure on this handle (empty string when none).  Owned by the handle. */
+const char* mto_last_error(mto_handle h);
+
+/* Re-bind the handle to another stream of the same device. */
+mto_status mto_set_stream(mto_handle h, void* stream);
+
+/* Define the analysis and design meshes (Sec. 2.1, 3.3): nelx x nely elements of size hx x hy with
+ * orders p_map[nel] and per-axis design counts d_map[nel] (host int32, row-major elements).
+ * Builds the minimum-rule DOF numbering, the element classes and the subcell stiffness tables
+ * K0_s (App. B composite integration) on the device.  Any order jump is accepted (the paper's
+ * smoothing keeps jumps <= 2).  Returns the number of DOFs (including supported ones) and the
+ * packed design length.  May be called again to change the maps; previous tables are freed.
+ * Errors: MTO_EINVAL for sizes < 1, p outside 1..MTO_P_MAX, d outside 1..MTO_D_MAX. */
+mto_status mto_setup(mto_handle h, int32_t nelx, int32_t nely, double hx, double hy,
+                     const int32_t* p_map, const int32_t* d_map, int64_t* ndof, int64_t* design_len);
+
+/* Homogeneous Dirichlet supports (Eq. 1 "Ku = f" on the free DOFs): fixed[n] host int64 global
+ * DOF indices, duplicates allowed.  Must follow mto_setup (which clears them).
+ * Errors: MTO_EINVAL for an index outside 0..ndof-1. */
+mto_status mto_set_supports(mto_handle h, const int64_t* fixed, int64_t n);
+
+/* Global DOF of component `comp` (0 = x, 1 = y) at mesh vertex (ix, iy), 0 <= ix <= nelx,
+ * 0 <= iy <= nely.  Host output. */
+mto_status mto_vertex_dof(mto_handle h, int32_t ix, int32_t iy, int32_t comp, int64_t* dof);
+
+/* Global DOFs of component `comp` (0, 1, or -1 for both) of every node on one side of the
+ * domain: 0 = left (x = 0), 1 = right, 2 = bottom (y = 0), 3 = top; ascending.  Host output of
+ * capacity `cap`; *count receives the number of DOFs (call with cap = 0 to size the buffer). */
+mto_status mto_side_dofs(mto_handle h, int32_t side, int32_t comp, int64_t* out, int64_t cap,
+                         int64_t* count);
+
+/* Inspection of the numbering (for tests and tools): for element e, fills per local node
+ * (row-major, (p_e+1)^2 nodes) up to 8 (global node, weight) pairs: nodes[ln*8 + k],
+ * weights[ln*8 + k], counts[ln].  A weight differs from 1 only on an edge whose order is below
+ * p_e (minimum rule).  Host outputs sized (MTO_P_MAX+1)^2 * 8 and (MTO_P_MAX+1)^2. */
+mto_status mto_element_nodes(mto_handle h, int64_t e, int64_t* nodes, double* weights, int32_t* counts);
+
+/* Step (a): element stiffness matrices K_e = sum_s E(rho_s) K0_s (Eqs. 2-3 with the composite
+ * integration of App. B) for every element, plus the Jacobi diagonal of the assembled operator.
+ * rho: device double[design_len] (packed).  precision MTO_FP64 stores FP64 matrices, applied on
+ * the FP64 pipes (the plain FP64 path).  MTO_MIXED stores each matrix as a split-precision FP32
+ * pair (hi = fl32(K_e), lo = fl32(K_e - hi), ~48 bits), applied on the FP32 pipes with error-free
+ * products and sums.  Matrices stay in the handle (packed upper triangles, element-interleaved).
+ * Asynchronous. */
+mto_status mto_build_elements(mto_handle h, const double* rho, const mto_material* mat, int32_t precision);
+
+/* Inspection (tests, tools): the current matrix of element e as its packed upper triangle
+ * (row-major, i <= j, local DOF 2*node + component), n_e (n_e + 1) / 2 doubles into host memory;
+ * from the split pair the value is hi + lo.  Allocates a small device buffer; synchronises. */
+mto_status mto_element_matrix(mto_handle h, int64_t e, double* packed);
+
+/* Step (b): solve K u = f on the free DOFs (u = 0 on supports) with the options above, using the
+ * matrices of the last mto_build_elements.  f: device double[ndof]; u: device double[ndof]
+ * (initial guess when opts->warm_start, overwritten with the solution).  *iters receives the
+ * total PCG iterations, *relres the final FP64 relative residual (host outputs, may be NULL).
+ * Returns MTO_ENOCONV when max_iter or max_outer is reached first (u holds the last iterate),
+ * MTO_ENAN on a breakdown.  Synchronises the stream. */
+mto_status mto_solve(mto_handle h, const double* f, double* u, const mto_solve_opts* opts,
+                     int32_t* iters, double* relres);
+
+/* y = K x on all DOFs (the assembled operator including supported rows), FP64, with the FP64
+ * matrices of the last build.  x, y: device double[ndof].  Asynchronous. */
+mto_status mto_apply(mto_handle h, const double* x, double* y);
+
+/* Step (c): compliance C = f^T u (Eq. 1 with z = f) and the design sensitivities
+ * dc[s] = -E'(rho_s) u_e^T K0_s u_e, E'(rho) = q rho^(q-1) (E0 - Emin): the adjoint of the
+ * self-adjoint compliance problem is -u.  u, f: device double[ndof]; rho, dc: device
+ * double[design_len]; C: host double (may be NULL: then no synchronisation).  precision as for
+ * the build: MTO_MIXED evaluates the quadratic forms in FP32 after an FP64 removal of the
+ * element's rigid-body motion. */
+mto_status mto_sensitivity(mto_handle h, const double* u, const double* f, const double* rho,
+                           const mto_material* mat, int32_t precision, double* dc, double* C);
+
+/* Step (d): composite refinement indicator and dp map update (Sec. 3.2, 3.3).
+ * u: device double[ndof] (the solved displacement), rho: device double[design_len].
+ * Outputs (device, [nel]): gamma_a (Kelly, Eq. 9, no square root), gamma_d (density indicator),
+ * eps_qr (Eq. 14), p_new, d_new (int32, per-axis design count), theta (int8 flag: -2, -1, 0, 1).
+ * Any output pointer may be NULL except those the later stages need internally (all are
+ * computed).  Asynchronous. */
+mto_status mto_indicator(mto_handle h, const double* u, const double* rho, const mto_material* mat,
+                         const mto_indicator_opts* opts, double* gamma_a, double* gamma_d,
+                         double* eps_qr, int32_t* p_new, int32_t* d_new, int8_t* theta);
+
+/* Map update only (Sec. 3.3 steps 2-4) from given indicator values (device [nel] each) and the
+ * handle's current orders.  For testing the integer logic in isolation. */
+mto_status mto_map_update(mto_handle h, const double* gamma_a, const double* gamma_d,
+                          const double* eps_qr, const mto_indicator_opts* opts, int32_t* p_new,
+                          int32_t* d_new, int8_t* theta);
+
+/* Optimality-criteria update (textbook; the paper does not name its optimizer):
+ * rho_new = clip(rho (-dc / (lambda dv))^eta, max(0, rho - move), min(1, rho + move)) with
+ * dv = hx hy / d_e^2 and lambda bisected on [0, 1e9] until (l2 - l1)/(l1 + l2) <= 1e-10 so that
+ * sum(rho_new dv) = volfrac * nelx * nely * hx * hy.  rho (in), dc (in), rho_new (out): device
+ * double[design_len]; *lambda (host, may be NULL) receives the multiplier (synchronises). */
+mto_status mto_oc_update(mto_handle h, const double* rho, const double* dc, double volfrac,
+                         double move, double eta, double* rho_new, double* lambda);
+
+/* Kernel-family timing for benchmarks.  When enabled, the launches of each family below are
+ * bracketed by CUDA events recorded on the handle's stream; mto_timing_read synchronises the
+ * stream and returns the number of kernel launches and their summed device time (ms) since the
+ * last mto_timing_enable (which resets the counters).  Families: */
+#define MTO_TIME_APPLY32 0   /* split-precision operator on FP32 vectors (mixed inner PCG) */
+#define MTO_TIME_APPLY64 1   /* FP64 element-by-element operator (plain FP64 path) */
+#define MTO_TIME_BUILD 2     /* step (a): subcell tables and element matrices */
+#define MTO_TIME_SENS 3      /* step (c): sensitivity quadrature and compliance */
+#define MTO_TIME_INDICATOR 4 /* step (d): indicators and map update */
+#define MTO_TIME_VECTOR 5    /* PCG vector updates, residuals, precision conversions */
+#define MTO_TIME_APPLYDF64 6 /* split-precision operator on FP64 vectors (refinement residuals) */
+mto_status mto_timing_enable(mto_handle h, int32_t enable);
+mto_status mto_timing_read(mto_handle h, int32_t family, int64_t* launches, double* total_ms);
+
+/* Device memory held by the handle, in bytes (host output). */
+mto_status mto_memory(mto_handle h, int64_t* bytes);
+
+/* Number of kernel launches this handle has issued since creation (host output). */
+mto_status mto_launch_count(mto_handle h, int64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MTO_H */

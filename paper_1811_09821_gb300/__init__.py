@@ -1,0 +1,295 @@
+"""GB300 (sm_103a) hot path of dp-adaptive multi-resolution topology optimization
+(Gupta, van Keulen, Langelaar, arXiv:1811.09821): element build, matrix-free PCG solve,
+compliance sensitivities and the composite refinement indicator, as CUDA kernels behind the C ABI
+of ``include/mto.h`` (``libmto.so``).
+
+This module is the thin Python binding: it marshals arguments (torch CUDA tensors for device
+memory, numpy arrays for host maps) into the C calls of the same names.  Every step of the path
+runs in the library's kernels; there is no CPU fallback, and importing this package raises when
+``libmto.so`` cannot be loaded.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmto.so")
+
+MTO_FP64, MTO_MIXED = 0, 1
+NORM_L2, NORM_JACOBI = 0, 1
+STATUS = {0: "MTO_OK", 1: "MTO_EINVAL", 2: "MTO_ENOMEM", 3: "MTO_ECUDA", 4: "MTO_ENOCONV", 5: "MTO_ENAN",
+          6: "MTO_ETIMEOUT"}
+P_MAX, D_MAX = 6, 16
+
+
+class MTOError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Material(ctypes.Structure):
+    """Material of Eq. 3 / Sec. 4.1 (plane stress)."""
+    _fields_ = [("E0", ctypes.c_double), ("Emin", ctypes.c_double), ("nu", ctypes.c_double), ("q", ctypes.c_double)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("rtol", ctypes.c_double), ("inner_rtol", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("warm_start", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("norm", ctypes.c_int32)]
+
+
+class IndicatorOpts(ctypes.Structure):
+    """Sec. 3.2 / 3.3 parameters; defaults are the paper's values."""
+    _fields_ = [("cycle", ctypes.c_int32), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("frac_a_refine", ctypes.c_double), ("frac_a_coarsen", ctypes.c_double),
+                ("alpha_d_refine", ctypes.c_double), ("alpha_d_coarsen", ctypes.c_double),
+                ("alpha_qr", ctypes.c_double), ("p_max", ctypes.c_int32), ("d_max", ctypes.c_int32)]
+
+    @classmethod
+    def paper(cls, cycle=1):
+        return cls(cycle, 0.2, 0.8, 0.10, 0.05, 1.0, 1.0, 0.9, 5, 64)
+
+
+# every symbol declared in include/mto.h
+SYMBOLS = ["mto_create", "mto_destroy", "mto_last_error", "mto_set_stream", "mto_setup", "mto_set_supports",
+           "mto_vertex_dof", "mto_side_dofs", "mto_element_nodes", "mto_element_matrix", "mto_build_elements", "mto_solve", "mto_apply",
+           "mto_sensitivity", "mto_indicator", "mto_map_update", "mto_oc_update", "mto_timing_enable", "mto_timing_read",
+           "mto_memory", "mto_launch_count"]
+TIME_FAMILIES = {"apply32": 0, "apply64": 1, "build": 2, "sens": 3, "indicator": 4, "vector": 5, "applydf64": 6}
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libmto.so and declare its signatures.  Raises OSError when it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} is missing: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "mto_create": ([P(vp), ctypes.c_int, vp], ctypes.c_int),
+        "mto_destroy": ([vp], ctypes.c_int),
+        "mto_last_error": ([vp], ctypes.c_char_p),
+        "mto_set_stream": ([vp, vp], ctypes.c_int),
+        "mto_setup": ([vp, i32, i32, dbl, dbl, P(i32), P(i32), P(i64), P(i64)], ctypes.c_int),
+        "mto_set_supports": ([vp, P(i64), i64], ctypes.c_int),
+        "mto_vertex_dof": ([vp, i32, i32, i32, P(i64)], ctypes.c_int),
+        "mto_side_dofs": ([vp, i32, i32, P(i64), i64, P(i64)], ctypes.c_int),
+        "mto_element_nodes": ([vp, i64, P(i64), P(dbl), P(i32)], ctypes.c_int),
+        "mto_element_matrix": ([vp, i64, P(dbl)], ctypes.c_int),
+        "mto_build_elements": ([vp, vp, P(Material), i32], ctypes.c_int),
+        "mto_solve": ([vp, vp, vp, P(SolveOpts), P(i32), P(dbl)], ctypes.c_int),
+        "mto_apply": ([vp, vp, vp], ctypes.c_int),
+        "mto_sensitivity": ([vp, vp, vp, vp, P(Material), i32, vp, P(dbl)], ctypes.c_int),
+        "mto_indicator": ([vp, vp, vp, P(Material), P(IndicatorOpts), vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "mto_map_update": ([vp, vp, vp, vp, P(IndicatorOpts), vp, vp, vp], ctypes.c_int),
+        "mto_oc_update": ([vp, vp, vp, dbl, dbl, dbl, vp, P(dbl)], ctypes.c_int),
+        "mto_timing_enable": ([vp, i32], ctypes.c_int),
+        "mto_timing_read": ([vp, i32, P(i64), P(dbl)], ctypes.c_int),
+        "mto_memory": ([vp, P(i64)], ctypes.c_int),
+        "mto_launch_count": ([vp, P(i64)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _ptr(t, dtype=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise TypeError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected dtype {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Handle:
+    """One problem instance on one CUDA device: owns the numbering, element matrices and workspace."""
+
+    def __init__(self, device=0, stream=None):
+        self.L = load_library()
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        self._check(self.L.mto_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream)))
+        self.h = h
+        self.ndof = self.design_len = None
+
+    def _check(self, status):
+        if status != 0:
+            msg = self.L.mto_last_error(self.h).decode() if getattr(self, "h", None) else ""
+            raise MTOError(status, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mto_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- mesh and supports
+    def setup(self, nelx, nely, p, d, hx=1.0, hy=1.0):
+        p = np.ascontiguousarray(p, dtype=np.int32)
+        d = np.ascontiguousarray(d, dtype=np.int32)
+        nd, dl = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.L.mto_setup(self.h, nelx, nely, hx, hy, p.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                     d.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(nd),
+                                     ctypes.byref(dl)))
+        self.nelx, self.nely, self.nel = nelx, nely, nelx * nely
+        self.ndof, self.design_len = nd.value, dl.value
+        return self.ndof, self.design_len
+
+    def set_supports(self, fixed):
+        fixed = np.ascontiguousarray(fixed, dtype=np.int64)
+        self._check(self.L.mto_set_supports(self.h, fixed.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                            len(fixed)))
+
+    def vertex_dof(self, ix, iy, comp):
+        out = ctypes.c_int64()
+        self._check(self.L.mto_vertex_dof(self.h, ix, iy, comp, ctypes.byref(out)))
+        return out.value
+
+    def side_dofs(self, side, comp=-1):
+        n = ctypes.c_int64()
+        self._check(self.L.mto_side_dofs(self.h, side, comp, None, 0, ctypes.byref(n)))
+        out = np.zeros(n.value, dtype=np.int64)
+        self._check(self.L.mto_side_dofs(self.h, side, comp, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                         n.value, ctypes.byref(n)))
+        return out
+
+    def element_nodes(self, e):
+        """Per local node of element e: list of (global node, weight) (minimum-rule map)."""
+        m = (P_MAX + 1) ** 2
+        nodes = np.zeros(m * 8, dtype=np.int64)
+        w = np.zeros(m * 8)
+        c = np.zeros(m, dtype=np.int32)
+        self._check(self.L.mto_element_nodes(self.h, e, nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                             w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                             c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        out = []
+        for ln in range(m):
+            if c[ln] == 0:
+                break
+            out.append([(int(nodes[ln * 8 + k]), float(w[ln * 8 + k])) for k in range(c[ln])])
+        return out
+
+    def element_matrix(self, e, p):
+        """Packed upper triangle of element e's current matrix (numpy, n_e (n_e + 1) / 2)."""
+        ne = 2 * (p + 1) ** 2
+        out = np.zeros(ne * (ne + 1) // 2)
+        self._check(self.L.mto_element_matrix(self.h, e, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    # ---------------------------------------------------------------- the four steps
+    def build_elements(self, rho, mat, precision=MTO_FP64):
+        self._check(self.L.mto_build_elements(self.h, _ptr(rho, torch.float64), ctypes.byref(mat), precision))
+
+    def solve(self, f, u, precision=MTO_FP64, rtol=1e-8, inner_rtol=1e-4, max_iter=200000, max_outer=50,
+              warm_start=False, check_every=64, norm=NORM_L2, raise_on_noconv=True):
+        o = SolveOpts(precision, rtol, inner_rtol, max_iter, max_outer, int(bool(warm_start)), check_every, norm)
+        it, rr = ctypes.c_int32(), ctypes.c_double()
+        st = self.L.mto_solve(self.h, _ptr(f, torch.float64), _ptr(u, torch.float64), ctypes.byref(o),
+                              ctypes.byref(it), ctypes.byref(rr))
+        if st != 0 and not (st == 4 and not raise_on_noconv):
+            self._check(st)
+        return it.value, rr.value
+
+    def apply(self, x, y):
+        self._check(self.L.mto_apply(self.h, _ptr(x, torch.float64), _ptr(y, torch.float64)))
+
+    def sensitivity(self, u, f, rho, mat, dc, precision=MTO_FP64, want_C=True):
+        C = ctypes.c_double()
+        self._check(self.L.mto_sensitivity(self.h, _ptr(u, torch.float64), _ptr(f, torch.float64),
+                                           _ptr(rho, torch.float64), ctypes.byref(mat), precision,
+                                           _ptr(dc, torch.float64), ctypes.byref(C) if want_C else None))
+        return C.value if want_C else None
+
+    def indicator(self, u, rho, mat, opts=None, maps=True):
+        opts = opts or IndicatorOpts.paper()
+        dev = self.device
+        ga = torch.empty(self.nel, dtype=torch.float64, device=dev)
+        gd = torch.empty_like(ga)
+        eq = torch.empty_like(ga)
+        pn = torch.empty(self.nel, dtype=torch.int32, device=dev) if maps else None
+        dn = torch.empty_like(pn) if maps else None
+        th = torch.empty(self.nel, dtype=torch.int8, device=dev) if maps else None
+        self._check(self.L.mto_indicator(self.h, _ptr(u, torch.float64), _ptr(rho, torch.float64), ctypes.byref(mat),
+                                         ctypes.byref(opts), _ptr(ga), _ptr(gd), _ptr(eq), _ptr(pn), _ptr(dn),
+                                         _ptr(th)))
+        return dict(gamma_a=ga, gamma_d=gd, eps_qr=eq, p_new=pn, d_new=dn, theta=th)
+
+    def map_update(self, gamma_a, gamma_d, eps_qr, opts=None):
+        opts = opts or IndicatorOpts.paper()
+        pn = torch.empty(self.nel, dtype=torch.int32, device=self.device)
+        dn = torch.empty_like(pn)
+        th = torch.empty(self.nel, dtype=torch.int8, device=self.device)
+        self._check(self.L.mto_map_update(self.h, _ptr(gamma_a, torch.float64), _ptr(gamma_d, torch.float64),
+                                          _ptr(eps_qr, torch.float64), ctypes.byref(opts), _ptr(pn), _ptr(dn),
+                                          _ptr(th)))
+        return pn, dn, th
+
+    def oc_update(self, rho, dc, volfrac, rho_new, move=0.2, eta=0.5):
+        lam = ctypes.c_double()
+        self._check(self.L.mto_oc_update(self.h, _ptr(rho, torch.float64), _ptr(dc, torch.float64), volfrac, move, eta,
+                                         _ptr(rho_new, torch.float64), ctypes.byref(lam)))
+        return lam.value
+
+    def timing_enable(self, on=True):
+        self._check(self.L.mto_timing_enable(self.h, int(bool(on))))
+
+    def timing_read(self):
+        """{family: (kernel launches, device ms)} since the last timing_enable."""
+        out = {}
+        for name, fam in TIME_FAMILIES.items():
+            n, ms = ctypes.c_int64(), ctypes.c_double()
+            self._check(self.L.mto_timing_read(self.h, fam, ctypes.byref(n), ctypes.byref(ms)))
+            out[name] = (n.value, ms.value)
+        return out
+
+    def memory(self):
+        b = ctypes.c_int64()
+        self._check(self.L.mto_memory(self.h, ctypes.byref(b)))
+        return b.value
+
+    def launch_count(self):
+        c = ctypes.c_int64()
+        self._check(self.L.mto_launch_count(self.h, ctypes.byref(c)))
+        return c.value
+
+
+def load_case(handle, load):
+    """Supports and load vector of a named load case, placed with the library's own numbering.
+
+    cantilever: left edge clamped, F = -1 (y) at vertex (nelx, nely/2) (Sec. 4.1, Fig. 3a);
+    mbb: u_x = 0 on the left edge, u_y = 0 at vertex (nelx, 0), F = -1 (y) at vertex (0, nely).
+    Returns (fixed DOFs as numpy int64, f as a CUDA float64 tensor)."""
+    nx, ny = handle.nelx, handle.nely
+    f = torch.zeros(handle.ndof, dtype=torch.float64, device=handle.device)
+    if load == "cantilever":
+        fixed = handle.side_dofs(0, -1)
+        f[handle.vertex_dof(nx, ny // 2, 1)] = -1.0
+    elif load == "mbb":
+        fixed = np.concatenate([handle.side_dofs(0, 0), [handle.vertex_dof(nx, 0, 1)]]).astype(np.int64)
+        f[handle.vertex_dof(0, ny, 1)] = -1.0
+    else:
+        raise ValueError(load)
+    return np.sort(fixed), f
+
+
+def material(E0=1.0, Emin=1e-9, nu=0.3, q=3.0):
+    return Material(E0, Emin, nu, q)

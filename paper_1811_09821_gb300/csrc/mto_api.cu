@@ -1,0 +1,635 @@
+// C ABI entry points: handle lifecycle, mesh setup (minimum-rule DOF numbering and element
+// classes), supports, numbering queries, and dispatch to the kernel translation units.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mto_internal.cuh"
+
+using namespace mto;
+
+mto_status mto_fail(mto_handle h, mto_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+mto_status mto_cuda_check(mto_handle h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return MTO_OK;
+  return mto_fail(h, MTO_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+mto_status mto_after_launch(mto_handle h, const char* what) {
+  h->launches++;
+  return mto_cuda_check(h, cudaGetLastError(), what);
+}
+
+namespace {
+cudaEvent_t take_event(mto_handle h) {
+  if (!h->timing.pool.empty()) {
+    cudaEvent_t e = h->timing.pool.back();
+    h->timing.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+
+TimedScope::TimedScope(mto_handle h_, int fam_) : h(h_), fam(fam_), launches0(h_->launches) {
+  if (!h->timing.on) return;
+  if (h->timing.pending.size() > 4096) {
+    cudaStreamSynchronize(h->stream);
+    timing_harvest(h);
+  }
+  a = take_event(h);
+  cudaEventRecord(a, h->stream);
+}
+
+TimedScope::~TimedScope() {
+  if (!a) return;
+  cudaEvent_t b = take_event(h);
+  cudaEventRecord(b, h->stream);
+  h->timing.pending.push_back({fam, (int)(h->launches - launches0), a, b});
+}
+
+void timing_harvest(mto_handle h) {
+  for (auto& p : h->timing.pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      h->timing.ms[p.fam] += ms;
+      h->timing.launches[p.fam] += p.launches;
+    }
+    h->timing.pool.push_back(p.a);
+    h->timing.pool.push_back(p.b);
+  }
+  h->timing.pending.clear();
+}
+
+namespace {
+
+template <typename T>
+void free_dev(mto_handle h, T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void release_mesh(mto_handle h) {
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_dev(h, h->p_d);
+  free_dev(h, h->d_d);
+  free_dev(h, h->design_off_d);
+  free_dev(h, h->cons_d);
+  for (auto& c : h->pc) {
+    free_dev(h, c.elem);
+    free_dev(h, c.gmap);
+    free_dev(h, c.dpos);
+    free_dev(h, c.K64);
+    free_dev(h, c.K32);
+    free_dev(h, c.K32lo);
+    c = PClass();
+  }
+  for (auto* v : {&h->bc, &h->bc_qr}) {
+    for (auto& b : *v) {
+      free_dev(h, b.elem);
+      free_dev(h, b.slot);
+      free_dev(h, b.K0T);
+      free_dev(h, b.stab);
+      free_dev(h, b.stabf);
+    }
+    v->clear();
+  }
+  for (auto& q : h->qr) {
+    free_dev(h, q.R);
+    q = QRTab();
+  }
+  free_dev(h, h->slot_d);
+  free_dev(h, h->invd64);
+  free_dev(h, h->invd32);
+  free_dev(h, h->r64);
+  free_dev(h, h->p64);
+  free_dev(h, h->q64);
+  free_dev(h, h->x32);
+  free_dev(h, h->r32);
+  free_dev(h, h->p32);
+  free_dev(h, h->q32);
+  free_dev(h, h->ibuf);
+  free_dev(h, h->dbuf);
+  free_dev(h, h->edge_buf);
+  if (h->basis_tab) cudaFree(h->basis_tab);
+  h->basis_tab = nullptr;
+  h->have_setup = h->have_supports = false;
+  h->built_precision = -1;
+  h->k0_nu = -2.0;
+  h->fixed_host.clear();
+  free_dev(h, h->fixed_d);
+  h->n_fixed = 0;
+  h->bytes = h->base_bytes;
+}
+
+// ---- numbering (host, integer) ---------------------------------------------------------------
+inline int64_t vertex_id(mto_handle h, int ix, int iy) { return (int64_t)iy * (h->nelx + 1) + ix; }
+
+// Global nodes of a horizontal (dir = 0) or vertical (dir = 1) edge in parameter order
+// (left->right / bottom->top): start vertex, interior nodes, end vertex.  Returns the edge order.
+int edge_nodes(mto_handle h, int dir, int ix, int iy, int64_t* out) {
+  int pE;
+  int64_t base;
+  int64_t v0, v1;
+  if (dir == 0) {
+    int64_t id = (int64_t)iy * h->nelx + ix;
+    pE = h->pH[id];
+    base = h->h_base[id];
+    v0 = vertex_id(h, ix, iy);
+    v1 = vertex_id(h, ix + 1, iy);
+  } else {
+    int64_t id = (int64_t)iy * (h->nelx + 1) + ix;
+    pE = h->pV[id];
+    base = h->v_base[id];
+    v0 = vertex_id(h, ix, iy);
+    v1 = vertex_id(h, ix, iy + 1);
+  }
+  out[0] = v0;
+  for (int k = 1; k < pE; ++k) out[k] = base + (k - 1);
+  out[pE] = v1;
+  return pE;
+}
+
+// (node, weight) list of local node (a, b) of element e; returns the count.
+int local_node_map(mto_handle h, int64_t e, int a, int b, int64_t* nodes, double* w) {
+  int ex = (int)(e % h->nelx), ey = (int)(e / h->nelx);
+  int p = h->p_host[e];
+  bool xa = (a == 0 || a == p), yb = (b == 0 || b == p);
+  if (xa && yb) {
+    nodes[0] = vertex_id(h, ex + a / p, ey + b / p);
+    w[0] = 1.0;
+    return 1;
+  }
+  if (yb || xa) {
+    int64_t en[kPMaxTab + 2];
+    int pE, t;
+    if (yb) {
+      pE = edge_nodes(h, 0, ex, ey + b / p, en);
+      t = a;
+    } else {
+      pE = edge_nodes(h, 1, ex + a / p, ey, en);
+      t = b;
+    }
+    if (pE == p) {
+      nodes[0] = en[t];
+      w[0] = 1.0;
+      return 1;
+    }
+    double zp[kPMaxTab + 1], ze[kPMaxTab + 1];
+    gll_nodes(p, zp);
+    gll_nodes(pE, ze);
+    for (int k = 0; k <= pE; ++k) {
+      nodes[k] = en[k];
+      w[k] = lagrange_val(ze, pE + 1, k, zp[t]);
+    }
+    return pE + 1;
+  }
+  nodes[0] = h->i_base[e] + (int64_t)(b - 1) * (p - 1) + (a - 1);
+  w[0] = 1.0;
+  return 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+mto_status mto_create(mto_handle* out, int device, void* stream) {
+  if (!out) return MTO_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return MTO_ECUDA;
+  mto_handle h = new mto_handle_s();
+  h->device = device;
+  h->stream = (cudaStream_t)stream;
+  cudaSetDevice(device);
+  if (mto_alloc(h, &h->scal, kSlots) || mto_alloc(h, &h->red, 64) || mto_alloc(h, &h->flags, 64) ||
+      mto_alloc(h, &h->sel, 256)) {
+    delete h;
+    return MTO_ENOMEM;
+  }
+  h->base_bytes = h->bytes;
+  if (cudaMallocHost((void**)&h->host_pinned, 64 * sizeof(double)) != cudaSuccess) {
+    delete h;
+    return MTO_ENOMEM;
+  }
+  *out = h;
+  return MTO_OK;
+}
+
+mto_status mto_destroy(mto_handle h) {
+  if (!h) return MTO_OK;
+  release_mesh(h);
+  timing_harvest(h);
+  for (cudaEvent_t e : h->timing.pool) cudaEventDestroy(e);
+  cudaFree(h->scal);
+  cudaFree(h->red);
+  cudaFree(h->flags);
+  cudaFree(h->sel);
+  cudaFreeHost(h->host_pinned);
+  delete h;
+  return MTO_OK;
+}
+
+const char* mto_last_error(mto_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+mto_status mto_set_stream(mto_handle h, void* stream) {
+  if (!h) return MTO_EINVAL;
+  h->stream = (cudaStream_t)stream;
+  return MTO_OK;
+}
+
+mto_status mto_setup(mto_handle h, int32_t nelx, int32_t nely, double hx, double hy,
+                     const int32_t* p_map, const int32_t* d_map, int64_t* ndof, int64_t* design_len) {
+  if (!h) return MTO_EINVAL;
+  h->err.clear();
+  if (nelx < 1 || nely < 1 || !(hx > 0) || !(hy > 0) || !p_map || !d_map)
+    return mto_fail(h, MTO_EINVAL, "mto_setup: bad mesh arguments");
+  int64_t nel = (int64_t)nelx * nely;
+  for (int64_t e = 0; e < nel; ++e) {
+    if (p_map[e] < 1 || p_map[e] > MTO_P_MAX)
+      return mto_fail(h, MTO_EINVAL, "mto_setup: p outside 1..MTO_P_MAX at element " + std::to_string(e));
+    if (d_map[e] < 1 || d_map[e] > MTO_D_MAX)
+      return mto_fail(h, MTO_EINVAL, "mto_setup: d outside 1..MTO_D_MAX at element " + std::to_string(e));
+  }
+  cudaSetDevice(h->device);
+  release_mesh(h);
+  h->nelx = nelx;
+  h->nely = nely;
+  h->hx = hx;
+  h->hy = hy;
+  h->nel = nel;
+  h->p_host.assign(p_map, p_map + nel);
+  h->d_host.assign(d_map, d_map + nel);
+
+  // edge orders (minimum rule) and node bases
+  h->pH.assign((size_t)(nely + 1) * nelx, 0);
+  h->pV.assign((size_t)nely * (nelx + 1), 0);
+  for (int iy = 0; iy <= nely; ++iy)
+    for (int ix = 0; ix < nelx; ++ix) {
+      int below = iy > 0 ? p_map[(int64_t)(iy - 1) * nelx + ix] : 1 << 20;
+      int above = iy < nely ? p_map[(int64_t)iy * nelx + ix] : 1 << 20;
+      h->pH[(int64_t)iy * nelx + ix] = std::min(below, above);
+    }
+  for (int iy = 0; iy < nely; ++iy)
+    for (int ix = 0; ix <= nelx; ++ix) {
+      int left = ix > 0 ? p_map[(int64_t)iy * nelx + ix - 1] : 1 << 20;
+      int right = ix < nelx ? p_map[(int64_t)iy * nelx + ix] : 1 << 20;
+      h->pV[(int64_t)iy * (nelx + 1) + ix] = std::min(left, right);
+    }
+  int64_t next = (int64_t)(nelx + 1) * (nely + 1);
+  h->h_base.resize(h->pH.size());
+  for (size_t k = 0; k < h->pH.size(); ++k) {
+    h->h_base[k] = next;
+    next += h->pH[k] - 1;
+  }
+  h->v_base.resize(h->pV.size());
+  for (size_t k = 0; k < h->pV.size(); ++k) {
+    h->v_base[k] = next;
+    next += h->pV[k] - 1;
+  }
+  h->i_base.resize(nel);
+  for (int64_t e = 0; e < nel; ++e) {
+    h->i_base[e] = next;
+    next += (int64_t)(p_map[e] - 1) * (p_map[e] - 1);
+  }
+  h->n_nodes = next;
+  h->ndof = 2 * next;
+  if (h->ndof >= (int64_t)1 << 31) return mto_fail(h, MTO_EINVAL, "mto_setup: more than 2^31 DOFs");
+  h->design_off_host.resize(nel + 1);
+  h->design_off_host[0] = 0;
+  for (int64_t e = 0; e < nel; ++e)
+    h->design_off_host[e + 1] = h->design_off_host[e] + (int64_t)d_map[e] * d_map[e];
+  h->design_len = h->design_off_host[nel];
+
+  // element classes by order: node maps with minimum-rule constraint records
+  std::vector<Constraint> cons;
+  std::vector<int> slot_of(nel, -1);
+  for (int p = 1; p <= MTO_P_MAX; ++p) {
+    std::vector<int> elems;
+    for (int64_t e = 0; e < nel; ++e)
+      if (p_map[e] == p) elems.push_back((int)e);
+    PClass& c = h->pc[p];
+    c.p = p;
+    c.n = (int)elems.size();
+    if (c.n == 0) continue;
+    c.ld = round_up(c.n, 32);
+    int ne = 2 * (p + 1) * (p + 1);
+    c.P = packed_size(ne);
+    c.L = diag_row_len(ne);
+    int nn = (p + 1) * (p + 1);
+    std::vector<int> gmap((size_t)nn * c.ld, 0);
+    // positions of each packed entry (i <= j) in the circulant-diagonal row
+    std::vector<int2> dpos(c.P);
+    for (int ii = 0, cc = 0; ii < ne; ++ii)
+      for (int jj = ii; jj < ne; ++jj, ++cc) {
+        const int k = jj - ii;
+        if (2 * k < ne) dpos[cc] = make_int2(k * ne + ii, -1);
+        else if (2 * k == ne) dpos[cc] = make_int2(k * ne + ii, k * ne + jj);
+        else dpos[cc] = make_int2((ne - k) * ne + jj, -1);
+      }
+    for (int k = 0; k < c.n; ++k) {
+      int64_t e = elems[k];
+      slot_of[e] = k;
+      for (int b = 0; b <= p; ++b)
+        for (int a = 0; a <= p; ++a) {
+          int64_t nodes[kConsMax];
+          double w[kConsMax];
+          int cnt = local_node_map(h, e, a, b, nodes, w);
+          int ln = b * (p + 1) + a;
+          if (cnt == 1) {
+            gmap[(size_t)k * nn + ln] = (int)nodes[0];
+          } else {
+            Constraint r;
+            memset(&r, 0, sizeof(r));
+            r.cnt = cnt;
+            for (int j = 0; j < cnt; ++j) {
+              r.node[j] = (int)nodes[j];
+              r.w[j] = w[j];
+            }
+            gmap[(size_t)k * nn + ln] = -(1 + (int)cons.size());
+            cons.push_back(r);
+          }
+        }
+    }
+    MTO_TRY(mto_alloc(h, &c.elem, c.n));
+    MTO_TRY(mto_alloc(h, &c.gmap, gmap.size()));
+    MTO_TRY(mto_alloc(h, &c.dpos, dpos.size()));
+    MTO_TRY(mto_cuda_check(h, cudaMemcpy(c.dpos, dpos.data(), dpos.size() * sizeof(int2), cudaMemcpyHostToDevice), "upload"));
+    MTO_TRY(mto_cuda_check(h, cudaMemcpy(c.elem, elems.data(), c.n * sizeof(int), cudaMemcpyHostToDevice), "upload"));
+    MTO_TRY(mto_cuda_check(h, cudaMemcpy(c.gmap, gmap.data(), gmap.size() * sizeof(int), cudaMemcpyHostToDevice), "upload"));
+  }
+  h->n_cons = (int)cons.size();
+  if (h->n_cons) {
+    MTO_TRY(mto_alloc(h, &h->cons_d, cons.size()));
+    MTO_TRY(mto_cuda_check(h, cudaMemcpy(h->cons_d, cons.data(), cons.size() * sizeof(Constraint), cudaMemcpyHostToDevice), "upload"));
+  }
+
+  // (p, d) classes for the build / sensitivity, and (p+1, d) tables for the QR indicator
+  for (int p = 1; p <= MTO_P_MAX; ++p)
+    for (int d = 1; d <= MTO_D_MAX; ++d) {
+      std::vector<int> elems, slots;
+      for (int64_t e = 0; e < nel; ++e)
+        if (p_map[e] == p && d_map[e] == d) {
+          elems.push_back((int)e);
+          slots.push_back(slot_of[e]);
+        }
+      if (elems.empty()) continue;
+      BClass b;
+      b.p = p;
+      b.d = d;
+      b.S = d * d;
+      b.P = packed_size(2 * (p + 1) * (p + 1));
+      b.n = (int)elems.size();
+      MTO_TRY(mto_alloc(h, &b.elem, b.n));
+      MTO_TRY(mto_alloc(h, &b.slot, b.n));
+      MTO_TRY(mto_cuda_check(h, cudaMemcpy(b.elem, elems.data(), b.n * sizeof(int), cudaMemcpyHostToDevice), "upload"));
+      MTO_TRY(mto_cuda_check(h, cudaMemcpy(b.slot, slots.data(), b.n * sizeof(int), cudaMemcpyHostToDevice), "upload"));
+      h->bc.push_back(b);
+      BClass q = b;
+      q.p = p + 1;
+      q.P = packed_size(2 * (p + 2) * (p + 2));
+      q.elem = nullptr;
+      q.slot = nullptr;
+      h->bc_qr.push_back(q);
+    }
+
+  // per-element arrays
+  MTO_TRY(mto_alloc(h, &h->p_d, nel));
+  MTO_TRY(mto_alloc(h, &h->d_d, nel));
+  MTO_TRY(mto_alloc(h, &h->design_off_d, nel + 1));
+  MTO_TRY(mto_alloc(h, &h->slot_d, nel));   // slot of each element within its order class
+  MTO_TRY(mto_cuda_check(h, cudaMemcpy(h->p_d, p_map, nel * sizeof(int), cudaMemcpyHostToDevice), "upload"));
+  MTO_TRY(mto_cuda_check(h, cudaMemcpy(h->d_d, d_map, nel * sizeof(int), cudaMemcpyHostToDevice), "upload"));
+  MTO_TRY(mto_cuda_check(h, cudaMemcpy(h->design_off_d, h->design_off_host.data(), (nel + 1) * sizeof(int64_t), cudaMemcpyHostToDevice), "upload"));
+  MTO_TRY(mto_cuda_check(h, cudaMemcpy(h->slot_d, slot_of.data(), nel * sizeof(int), cudaMemcpyHostToDevice), "upload"));
+
+  // solver workspace
+  int64_t n = h->ndof;
+  MTO_TRY(mto_alloc(h, &h->invd64, n));
+  MTO_TRY(mto_alloc(h, &h->invd32, n));
+  MTO_TRY(mto_alloc(h, &h->r64, n));
+  MTO_TRY(mto_alloc(h, &h->p64, n));
+  MTO_TRY(mto_alloc(h, &h->q64, n));
+  MTO_TRY(mto_alloc(h, &h->x32, n));
+  MTO_TRY(mto_alloc(h, &h->r32, n));
+  MTO_TRY(mto_alloc(h, &h->p32, n));
+  MTO_TRY(mto_alloc(h, &h->q32, n));
+  MTO_TRY(mto_alloc(h, &h->ibuf, 4 * nel + 64));
+  MTO_TRY(mto_alloc(h, &h->dbuf, 2 * nel + 64));
+  h->n_edges = (int64_t)(nely + 1) * nelx + (int64_t)nely * (nelx + 1);
+  MTO_TRY(mto_alloc(h, &h->edge_buf, h->n_edges + nel));
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->flags, 0, 64 * sizeof(int), h->stream), "memset"));
+  MTO_TRY(build_tables(h));
+  MTO_TRY(build_sens_tables(h));
+  MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "mto_setup"));
+  h->have_setup = true;
+  if (ndof) *ndof = h->ndof;
+  if (design_len) *design_len = h->design_len;
+  return MTO_OK;
+}
+
+mto_status mto_set_supports(mto_handle h, const int64_t* fixed, int64_t n) {
+  if (!h || !h->have_setup) return mto_fail(h, MTO_EINVAL, "mto_set_supports: call mto_setup first");
+  if (n < 0 || (n > 0 && !fixed)) return mto_fail(h, MTO_EINVAL, "mto_set_supports: bad arguments");
+  for (int64_t k = 0; k < n; ++k)
+    if (fixed[k] < 0 || fixed[k] >= h->ndof)
+      return mto_fail(h, MTO_EINVAL, "mto_set_supports: DOF index out of range");
+  h->fixed_host.assign(fixed, fixed + n);
+  std::sort(h->fixed_host.begin(), h->fixed_host.end());
+  h->fixed_host.erase(std::unique(h->fixed_host.begin(), h->fixed_host.end()), h->fixed_host.end());
+  free_dev(h, h->fixed_d);
+  h->n_fixed = (int64_t)h->fixed_host.size();
+  if (h->n_fixed) {
+    MTO_TRY(mto_alloc(h, &h->fixed_d, h->n_fixed));
+    MTO_TRY(mto_cuda_check(h, cudaMemcpy(h->fixed_d, h->fixed_host.data(), h->n_fixed * sizeof(int64_t),
+                                         cudaMemcpyHostToDevice), "upload"));
+  }
+  h->have_supports = true;
+  if (h->built_precision >= 0) MTO_TRY(build_diagonal(h, h->built_precision));
+  return MTO_OK;
+}
+
+mto_status mto_vertex_dof(mto_handle h, int32_t ix, int32_t iy, int32_t comp, int64_t* dof) {
+  if (!h || !h->have_setup || !dof) return mto_fail(h, MTO_EINVAL, "mto_vertex_dof: bad arguments");
+  if (ix < 0 || ix > h->nelx || iy < 0 || iy > h->nely || comp < 0 || comp > 1)
+    return mto_fail(h, MTO_EINVAL, "mto_vertex_dof: vertex or component out of range");
+  *dof = 2 * vertex_id(h, ix, iy) + comp;
+  return MTO_OK;
+}
+
+mto_status mto_side_dofs(mto_handle h, int32_t side, int32_t comp, int64_t* out, int64_t cap, int64_t* count) {
+  if (!h || !h->have_setup || !count) return mto_fail(h, MTO_EINVAL, "mto_side_dofs: bad arguments");
+  if (side < 0 || side > 3 || comp < -1 || comp > 1) return mto_fail(h, MTO_EINVAL, "mto_side_dofs: bad side/comp");
+  std::vector<int64_t> nodes;
+  int64_t en[kPMaxTab + 2];
+  if (side <= 1) {
+    int ix = side == 0 ? 0 : h->nelx;
+    for (int iy = 0; iy < h->nely; ++iy) {
+      int pE = edge_nodes(h, 1, ix, iy, en);
+      for (int k = 0; k < pE; ++k) nodes.push_back(en[k]);
+    }
+    nodes.push_back(vertex_id(h, ix, h->nely));
+  } else {
+    int iy = side == 2 ? 0 : h->nely;
+    for (int ix = 0; ix < h->nelx; ++ix) {
+      int pE = edge_nodes(h, 0, ix, iy, en);
+      for (int k = 0; k < pE; ++k) nodes.push_back(en[k]);
+    }
+    nodes.push_back(vertex_id(h, h->nelx, iy));
+  }
+  std::vector<int64_t> dofs;
+  for (int64_t nd : nodes) {
+    if (comp != 1) dofs.push_back(2 * nd);
+    if (comp != 0) dofs.push_back(2 * nd + 1);
+  }
+  std::sort(dofs.begin(), dofs.end());
+  dofs.erase(std::unique(dofs.begin(), dofs.end()), dofs.end());
+  *count = (int64_t)dofs.size();
+  if (cap > 0) {
+    if (!out) return mto_fail(h, MTO_EINVAL, "mto_side_dofs: null output");
+    int64_t m = std::min<int64_t>(cap, (int64_t)dofs.size());
+    std::copy(dofs.begin(), dofs.begin() + m, out);
+  }
+  return MTO_OK;
+}
+
+mto_status mto_element_nodes(mto_handle h, int64_t e, int64_t* nodes, double* weights, int32_t* counts) {
+  if (!h || !h->have_setup || !nodes || !weights || !counts || e < 0 || e >= h->nel)
+    return mto_fail(h, MTO_EINVAL, "mto_element_nodes: bad arguments");
+  int p = h->p_host[e];
+  for (int b = 0; b <= p; ++b)
+    for (int a = 0; a <= p; ++a) {
+      int ln = b * (p + 1) + a;
+      counts[ln] = local_node_map(h, e, a, b, nodes + ln * kConsMax, weights + ln * kConsMax);
+    }
+  return MTO_OK;
+}
+
+mto_status mto_build_elements(mto_handle h, const double* rho, const mto_material* mat, int32_t precision) {
+  if (!h || !h->have_setup || !rho || !mat) return mto_fail(h, MTO_EINVAL, "mto_build_elements: bad arguments");
+  if (precision != MTO_FP64 && precision != MTO_MIXED) return mto_fail(h, MTO_EINVAL, "mto_build_elements: bad precision");
+  if (!(mat->E0 > 0) || !(mat->Emin >= 0) || !(mat->nu > -1 && mat->nu < 0.5) || !(mat->q >= 1))
+    return mto_fail(h, MTO_EINVAL, "mto_build_elements: bad material");
+  cudaSetDevice(h->device);
+  h->built_precision = precision;
+  MTO_TRY(build_elements(h, rho, mat, precision));
+  if (h->have_supports) MTO_TRY(build_diagonal(h, precision));
+  return MTO_OK;
+}
+
+mto_status mto_element_matrix(mto_handle h, int64_t e, double* packed) {
+  if (!h || !h->have_setup || !packed || e < 0 || e >= h->nel)
+    return mto_fail(h, MTO_EINVAL, "mto_element_matrix: bad arguments");
+  if (h->built_precision < 0) return mto_fail(h, MTO_EINVAL, "mto_element_matrix: call mto_build_elements first");
+  cudaSetDevice(h->device);
+  return element_matrix(h, e, packed);
+}
+
+mto_status mto_solve(mto_handle h, const double* f, double* u, const mto_solve_opts* opts, int32_t* iters,
+                     double* relres) {
+  if (!h || !h->have_setup || !f || !u || !opts) return mto_fail(h, MTO_EINVAL, "mto_solve: bad arguments");
+  if (!h->have_supports) return mto_fail(h, MTO_EINVAL, "mto_solve: call mto_set_supports first");
+  if (h->built_precision < 0) return mto_fail(h, MTO_EINVAL, "mto_solve: call mto_build_elements first");
+  if (opts->precision == MTO_MIXED && h->built_precision != MTO_MIXED)
+    return mto_fail(h, MTO_EINVAL, "mto_solve: the mixed solve needs the split-precision (MTO_MIXED) build");
+  if (!(opts->rtol > 0) || opts->max_iter < 1 || opts->check_every < 1)
+    return mto_fail(h, MTO_EINVAL, "mto_solve: bad options");
+  cudaSetDevice(h->device);
+  return solve(h, f, u, opts, iters, relres);
+}
+
+mto_status mto_apply(mto_handle h, const double* x, double* y) {
+  if (!h || !h->have_setup || !x || !y) return mto_fail(h, MTO_EINVAL, "mto_apply: bad arguments");
+  if (h->built_precision < 0) return mto_fail(h, MTO_EINVAL, "mto_apply: call mto_build_elements first");
+  cudaSetDevice(h->device);
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(y, 0, h->ndof * sizeof(double), h->stream), "mto_apply"));
+  return apply64(h, x, y, nullptr);
+}
+
+mto_status mto_sensitivity(mto_handle h, const double* u, const double* f, const double* rho,
+                           const mto_material* mat, int32_t precision, double* dc, double* C) {
+  if (!h || !h->have_setup || !u || !f || !rho || !mat || !dc)
+    return mto_fail(h, MTO_EINVAL, "mto_sensitivity: bad arguments");
+  if (precision != MTO_FP64 && precision != MTO_MIXED) return mto_fail(h, MTO_EINVAL, "mto_sensitivity: bad precision");
+  cudaSetDevice(h->device);
+  return sensitivity(h, u, f, rho, mat, precision, dc, C);
+}
+
+mto_status mto_indicator(mto_handle h, const double* u, const double* rho, const mto_material* mat,
+                         const mto_indicator_opts* opts, double* gamma_a, double* gamma_d, double* eps_qr,
+                         int32_t* p_new, int32_t* d_new, int8_t* theta) {
+  if (!h || !h->have_setup || !u || !rho || !mat || !opts)
+    return mto_fail(h, MTO_EINVAL, "mto_indicator: bad arguments");
+  if (h->built_precision < 0) return mto_fail(h, MTO_EINVAL, "mto_indicator: call mto_build_elements first");
+  if (opts->cycle < 1 || opts->p_max < 1 || opts->p_max > MTO_P_MAX || opts->d_max < 1 ||
+      opts->d_max > MTO_D_MAX * MTO_D_MAX)
+    return mto_fail(h, MTO_EINVAL, "mto_indicator: bad options");
+  cudaSetDevice(h->device);
+  return indicators(h, u, rho, mat, opts, gamma_a, gamma_d, eps_qr, p_new, d_new, theta);
+}
+
+mto_status mto_map_update(mto_handle h, const double* gamma_a, const double* gamma_d, const double* eps_qr,
+                          const mto_indicator_opts* opts, int32_t* p_new, int32_t* d_new, int8_t* theta) {
+  if (!h || !h->have_setup || !gamma_a || !gamma_d || !eps_qr || !opts || !p_new || !d_new || !theta)
+    return mto_fail(h, MTO_EINVAL, "mto_map_update: bad arguments");
+  if (opts->p_max < 1 || opts->p_max > MTO_P_MAX || opts->d_max < 1 || opts->d_max > MTO_D_MAX * MTO_D_MAX)
+    return mto_fail(h, MTO_EINVAL, "mto_map_update: bad options");
+  cudaSetDevice(h->device);
+  return map_update(h, gamma_a, gamma_d, eps_qr, opts, p_new, d_new, theta);
+}
+
+mto_status mto_oc_update(mto_handle h, const double* rho, const double* dc, double volfrac, double move,
+                         double eta, double* rho_new, double* lambda) {
+  if (!h || !h->have_setup || !rho || !dc || !rho_new) return mto_fail(h, MTO_EINVAL, "mto_oc_update: bad arguments");
+  if (!(volfrac > 0 && volfrac <= 1) || !(move > 0) || !(eta > 0))
+    return mto_fail(h, MTO_EINVAL, "mto_oc_update: bad parameters");
+  cudaSetDevice(h->device);
+  return oc_update(h, rho, dc, volfrac, move, eta, rho_new, lambda);
+}
+
+mto_status mto_timing_enable(mto_handle h, int32_t enable) {
+  if (!h) return MTO_EINVAL;
+  cudaSetDevice(h->device);
+  MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "mto_timing_enable"));
+  timing_harvest(h);
+  for (int f = 0; f < F_COUNT; ++f) {
+    h->timing.ms[f] = 0.0;
+    h->timing.launches[f] = 0;
+  }
+  h->timing.on = enable != 0;
+  return MTO_OK;
+}
+
+mto_status mto_timing_read(mto_handle h, int32_t family, int64_t* launches, double* total_ms) {
+  if (!h || family < 0 || family >= F_COUNT || !launches || !total_ms)
+    return mto_fail(h, MTO_EINVAL, "mto_timing_read: bad arguments");
+  cudaSetDevice(h->device);
+  MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "mto_timing_read"));
+  timing_harvest(h);
+  *launches = h->timing.launches[family];
+  *total_ms = h->timing.ms[family];
+  return MTO_OK;
+}
+
+mto_status mto_memory(mto_handle h, int64_t* bytes) {
+  if (!h || !bytes) return MTO_EINVAL;
+  *bytes = h->bytes;
+  return MTO_OK;
+}
+
+mto_status mto_launch_count(mto_handle h, int64_t* count) {
+  if (!h || !count) return MTO_EINVAL;
+  *count = h->launches;
+  return MTO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,335 @@
+// Internal declarations of the MTO library: handle layout, element classes, device helpers.
+// Everything here is private to libmto; the public surface is include/mto.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mto.h"
+
+namespace mto {
+
+constexpr int kPMaxTab = MTO_P_MAX + 1;   // tables go one order higher for the QR indicator
+constexpr int kConsMax = 8;               // (node, weight) pairs per constrained local node
+constexpr int kSlots = 4;                 // PCG scalar ring
+
+// Packed upper triangle of an n x n symmetric matrix, row-major: c(i, j) for i <= j.
+__host__ __device__ constexpr int packed_size(int n) { return n * (n + 1) / 2; }
+__host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// Constrained local node: value = sum_k w[k] * value(node[k])  (minimum-rule interpolation).
+struct Constraint {
+  int cnt;
+  int node[kConsMax];
+  double w[kConsMax];
+};
+
+// Circulant-diagonal storage of a symmetric n_e x n_e element matrix: diagonal k (0 <= k <= n_e/2)
+// holds D_k[i] = K[i][(i + k) mod n_e] for i = 0..n_e-1, so one element's matrix is a row of
+// L = (n_e/2 + 1) n_e values (every packed entry once, the k = n_e/2 diagonal of an even n_e twice).
+// A warp owning one element lets lane i read D_k[i] (contiguous), form K[i][i+k] x_{i+k} for its
+// own row and hand K[i][i+k] x_i to lane i+k (the symmetric half) by shuffle.
+__host__ __device__ constexpr int diag_count(int ne) { return ne / 2 + 1; }
+__host__ __device__ constexpr int diag_row_len(int ne) { return diag_count(ne) * ne; }
+
+// All elements of one shape-function order p.  Element matrices are element-major rows of the
+// circulant-diagonal layout: FP64 [n][L] (FP64 path) or the split-precision pair hi, lo [n][L].
+struct PClass {
+  int p = 0;
+  int n = 0;          // elements in the class
+  int ld = 0;         // allocated element count (n rounded up to 32)
+  int P = 0;          // packed size n_e (n_e + 1) / 2
+  int L = 0;          // circulant-diagonal row length per element
+  int* elem = nullptr;   // [n] element ids, ascending
+  int* gmap = nullptr;   // [n][(p+1)^2] global node id, or -(1 + constraint index)
+  int2* dpos = nullptr;  // [P] row positions of packed entry c (second one or -1)
+  double* K64 = nullptr;   // FP64 path
+  float* K32 = nullptr;    // split-precision pair (mixed path): hi = fl32(K_e) ...
+  float* K32lo = nullptr;  // ... and lo = fl32(K_e - hi), same layout
+};
+
+// Elements of one (p, d) pair: the build and sensitivity granularity.
+struct BClass {
+  int p = 0, d = 0, S = 0, P = 0;
+  int n = 0;
+  int* elem = nullptr;   // [n] element ids
+  int* slot = nullptr;   // [n] slot of each element in its PClass
+  double* K0T = nullptr; // [P][S] subcell stiffness tables, transposed (entry c, subcell s)
+  double* stab = nullptr; // sensitivity quadrature tables (FP64 and FP32 copies)
+  float* stabf = nullptr;
+};
+
+// QR-indicator tables for order p -> p + 1.
+struct QRTab {
+  int p = 0;
+  double* R = nullptr;   // [(p+2)^2][(p+1)^2] scalar load transfer M^(p+1,p) M^(p)^-1
+};
+
+// Kernel families timed with CUDA events when timing is enabled (see mto_timing_enable).
+enum Family { F_APPLY32 = 0, F_APPLY64 = 1, F_BUILD = 2, F_SENS = 3, F_INDICATOR = 4, F_VECTOR = 5,
+              F_APPLYDF64 = 6, F_COUNT = 7 };
+
+struct Timing {
+  bool on = false;
+  struct Pending { int fam; int launches; cudaEvent_t a, b; };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Pending> pending;
+  int64_t launches[F_COUNT] = {0};
+  double ms[F_COUNT] = {0};
+};
+
+struct Scalars {         // one PCG iteration's reductions
+  double pq, rz, rr, pad;
+};
+
+}  // namespace mto
+
+struct mto_handle_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int64_t launches = 0;
+  int64_t bytes = 0;
+  mto::Timing timing;
+
+  // mesh
+  int nelx = 0, nely = 0;
+  double hx = 1.0, hy = 1.0;
+  int64_t nel = 0, n_nodes = 0, ndof = 0, design_len = 0;
+  std::vector<int> p_host, d_host;
+  std::vector<int64_t> design_off_host;
+  std::vector<int> pH, pV;                     // edge orders
+  std::vector<int64_t> h_base, v_base, i_base; // first global node of each edge / cell interior
+  std::vector<int64_t> fixed_host;
+  bool have_setup = false, have_supports = false;
+  int built_precision = -1;
+  double k0_nu = -2.0;                         // nu of the current subcell tables
+
+  // device tables
+  int* p_d = nullptr;
+  int* d_d = nullptr;
+  int64_t* design_off_d = nullptr;
+  mto::Constraint* cons_d = nullptr;
+  int n_cons = 0;
+  mto::PClass pc[mto::kPMaxTab + 1];
+  std::vector<mto::BClass> bc;
+  std::vector<mto::BClass> bc_qr;              // (p+1, d) tables for the QR indicator
+  mto::QRTab qr[mto::kPMaxTab + 1];
+  int* slot_d = nullptr;                       // [nel] slot of each element within its order class
+  int64_t* fixed_d = nullptr;                  // [n_fixed] supported DOFs
+  int64_t n_fixed = 0;
+  int64_t base_bytes = 0;                      // device bytes held independently of the mesh
+
+  // solver workspace
+  double* invd64 = nullptr;  // inverse diagonal, 0 on supported DOFs
+  float* invd32 = nullptr;
+  double *r64 = nullptr, *p64 = nullptr, *q64 = nullptr;
+  float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+  mto::Scalars* scal = nullptr;                // [kSlots]
+  double* red = nullptr;                       // misc reduction scratch [64]
+  int* flags = nullptr;                        // [0] done iteration + 1, [1] error code, [2..] misc
+  double* host_pinned = nullptr;               // pinned host mirror for small read-backs [64]
+  unsigned long long* sel = nullptr;           // selection / small integer scratch [256]
+  void* basis_tab = nullptr;                   // GLL / Gauss tables for the indicator kernels
+  double* edge_buf = nullptr;                  // [n_edges + nel] Kelly edge terms, then QR scratch
+  int64_t n_edges = 0;
+  int* ibuf = nullptr;                         // integer scratch [4 * nel]
+  double* dbuf = nullptr;                      // double scratch [2 * nel]
+};
+
+// ------------------------------------------------------------------------------------------
+// Shared helpers
+// ------------------------------------------------------------------------------------------
+#define MTO_TRY(expr)                                \
+  do {                                               \
+    mto_status _s = (expr);                          \
+    if (_s != MTO_OK) return _s;                     \
+  } while (0)
+
+mto_status mto_fail(mto_handle h, mto_status s, const std::string& msg);
+mto_status mto_cuda_check(mto_handle h, cudaError_t e, const char* what);
+mto_status mto_after_launch(mto_handle h, const char* what);
+
+// Event bracket around the launches of one kernel family on h->stream (no-op when timing is off).
+struct TimedScope {
+  mto_handle h;
+  int fam;
+  int64_t launches0;
+  cudaEvent_t a = nullptr;
+  TimedScope(mto_handle h_, int fam_);
+  ~TimedScope();
+};
+void timing_harvest(mto_handle h);   // call after the stream has been synchronised
+
+template <typename T>
+mto_status mto_alloc(mto_handle h, T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) return MTO_OK;
+  cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    return mto_fail(h, MTO_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  h->bytes += (int64_t)(count * sizeof(T));
+  return MTO_OK;
+}
+
+inline int grid_for(int64_t n, int block, int cap = 152 * 16) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+// ------------------------------------------------------------------------------------------
+// Finite-element basis on the device (one-time table construction; FP64)
+// ------------------------------------------------------------------------------------------
+namespace mto {
+
+// Legendre P_n and P_{n-1} at x by the three-term recurrence.
+__host__ __device__ inline void legendre_pair(int n, double x, double* pn, double* pn1) {
+  double a = 1.0, b = x;  // P_0, P_1
+  if (n == 0) { *pn = 1.0; *pn1 = 0.0; return; }
+  for (int k = 2; k <= n; ++k) {
+    double c = ((2 * k - 1) * x * b - (k - 1) * a) / k;
+    a = b;
+    b = c;
+  }
+  *pn = b;
+  *pn1 = a;
+}
+
+// The p+1 Gauss-Lobatto-Legendre nodes (end points and roots of P_p'), ascending.  Newton's
+// method on (1 - x^2) P_p'(x) written through the identity (1 - x^2) P_p' = p (P_{p-1} - x P_p),
+// started from the Chebyshev-Gauss-Lobatto points; then symmetrised.
+__host__ __device__ inline void gll_nodes(int p, double* z) {
+  for (int k = 0; k <= p; ++k) {
+    double x = -cos(3.14159265358979323846 * k / p);
+    if (k > 0 && k < p) {
+      for (int it = 0; it < 100; ++it) {
+        double pn, pn1;
+        legendre_pair(p, x, &pn, &pn1);
+        // f(x) = P_{p-1} - x P_p  (proportional to (1-x^2) P_p'), f'(x) = -(p+1) P_p
+        double f = pn1 - x * pn;
+        double df = -(p + 1) * pn;
+        double dx = f / df;
+        x -= dx;
+        if (fabs(dx) < 1e-17) break;
+      }
+    }
+    z[k] = x;
+  }
+  for (int k = 0; k <= p / 2; ++k) {
+    double s = 0.5 * (z[p - k] - z[k]);
+    z[k] = -s;
+    z[p - k] = s;
+  }
+  if (p % 2 == 0) z[p / 2] = 0.0;
+}
+
+// n-point Gauss-Legendre rule on [-1, 1]: Newton's method on P_n from cos(pi (k + 3/4)/(n + 1/2)),
+// weights 2 / ((1 - x^2) P_n'(x)^2).  Ascending nodes.
+__host__ __device__ inline void gauss_rule(int n, double* x, double* w) {
+  for (int k = 0; k < n; ++k) {
+    double t = cos(3.14159265358979323846 * (k + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double pn, pn1;
+      legendre_pair(n, t, &pn, &pn1);
+      dp = n * (t * pn - pn1) / (t * t - 1.0);
+      double dt = pn / dp;
+      t -= dt;
+      if (fabs(dt) < 1e-17) break;
+    }
+    double pn, pn1;
+    legendre_pair(n, t, &pn, &pn1);
+    dp = n * (t * pn - pn1) / (t * t - 1.0);
+    x[n - 1 - k] = t;
+    w[n - 1 - k] = 2.0 / ((1.0 - t * t) * dp * dp);
+  }
+  for (int k = 0; k < n / 2; ++k) {
+    double s = 0.5 * (x[n - 1 - k] - x[k]);
+    double ww = 0.5 * (w[n - 1 - k] + w[k]);
+    x[k] = -s; x[n - 1 - k] = s;
+    w[k] = ww; w[n - 1 - k] = ww;
+  }
+  if (n % 2 == 1) x[n / 2] = 0.0;
+}
+
+// Lagrange polynomial l_k on nodes z[0..n1-1] and its derivative, at x.
+__host__ __device__ inline double lagrange_val(const double* z, int n1, int k, double x) {
+  double v = 1.0;
+  for (int j = 0; j < n1; ++j)
+    if (j != k) v *= (x - z[j]) / (z[k] - z[j]);
+  return v;
+}
+
+__host__ __device__ inline double lagrange_der(const double* z, int n1, int k, double x) {
+  double s = 0.0;
+  for (int i = 0; i < n1; ++i) {
+    if (i == k) continue;
+    double t = 1.0 / (z[k] - z[i]);
+    for (int j = 0; j < n1; ++j)
+      if (j != k && j != i) t *= (x - z[j]) / (z[k] - z[j]);
+    s += t;
+  }
+  return s;
+}
+
+// Row-major packed index of (i, j), i <= j, in an n x n upper triangle.
+__host__ __device__ inline int packed_index(int n, int i, int j) {
+  return i * n - i * (i - 1) / 2 + (j - i);
+}
+
+// Entry at row position `pos` (see PClass::dpos) of the element matrix in slot `slot`, as a double:
+// from the FP64 matrices when present, else from the split-precision pair (hi + lo).
+__device__ __forceinline__ double k_entry(const double* __restrict__ K64, const float* __restrict__ Kh,
+                                          const float* __restrict__ Kl, int L, int slot, int pos) {
+  const size_t o = (size_t)slot * L + pos;
+  if (K64) return K64[o];
+  return (double)Kh[o] + (double)Kl[o];
+}
+
+// Order-preserving map of a double to an unsigned 64-bit key (for radix selection).
+__host__ __device__ inline unsigned long long order_key(double v) {
+  unsigned long long u;
+  memcpy(&u, &v, 8);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ULL);
+}
+
+}  // namespace mto
+
+// ------------------------------------------------------------------------------------------
+// Entry points of the kernel translation units (host wrappers that enqueue on h->stream)
+// ------------------------------------------------------------------------------------------
+namespace mto {
+// fe.cu
+mto_status build_tables(mto_handle h);                                  // K0 for all classes, QR tables
+// sens.cu (tables)
+mto_status build_sens_tables(mto_handle h);
+mto_status build_elements(mto_handle h, const double* rho, const mto_material* m, int precision);
+mto_status build_diagonal(mto_handle h, int precision);
+mto_status element_matrix(mto_handle h, int64_t e, double* host_out);
+// apply.cu
+mto_status apply64(mto_handle h, const double* x, double* y, double* pq);        // y += K x
+mto_status apply32(mto_handle h, const float* x, float* y, double* pq);
+mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts* o, int32_t* iters,
+                 double* relres);
+// sens.cu
+mto_status sensitivity(mto_handle h, const double* u, const double* f, const double* rho,
+                       const mto_material* m, int precision, double* dc, double* C);
+// ind.cu
+mto_status indicators(mto_handle h, const double* u, const double* rho, const mto_material* m,
+                      const mto_indicator_opts* o, double* ga, double* gd, double* eqr, int32_t* pn,
+                      int32_t* dn, int8_t* th);
+mto_status map_update(mto_handle h, const double* ga, const double* gd, const double* eqr,
+                      const mto_indicator_opts* o, int32_t* pn, int32_t* dn, int8_t* th);
+mto_status oc_update(mto_handle h, const double* rho, const double* dc, double volfrac, double move,
+                     double eta, double* rho_new, double* lambda);
+// reductions shared by several units
+mto_status dot64(mto_handle h, const double* a, const double* b, int64_t n, double* out_dev);
+}  // namespace mto

@@ -1,0 +1,238 @@
+// Step (c): compliance C = f^T u (Eq. 1 with z = f) and the design sensitivities
+// dC/drho_s = -E'(rho_s) w_s,  w_s = u_e^T K0_s u_e = integral over subcell s of eps^T D0 eps,
+// E'(rho) = q rho^(q-1) (E0 - Emin).  The compliance problem is self-adjoint (adjoint = -u), so u
+// is the only field needed; it is re-gathered per element from the stored global vector.
+//
+// Kernel: one warp per element.  The element's displacement is gathered in FP64 and its best-fit
+// rigid motion (translation and rotation, which K0_s annihilates) is removed in FP64.  Strains at
+// the (p+1) x (p+1) Gauss points of every subcell come from a sum-factorised tensor evaluation on
+// the element's d(p+1) x d(p+1) point grid; each point adds eps^T D0 eps (a sum of non-negative
+// terms) to its subcell.  Compute type T is double (MTO_FP64) or float (MTO_MIXED).
+#include <cmath>
+
+#include "mto_internal.cuh"
+
+namespace mto {
+
+// 1D tables of a (p, d) class: [L: N1 x G][D: N1 x G][W: G][Z: N1] with G = d (p+1) points
+// xi_g = -1 + (2 i + 1 + x_k)/d (subcell i, Gauss node x_k), L = l_a(xi_g), D = l_a'(xi_g) and
+// W = w_k / d (the 1D subcell Jacobian).
+__global__ void sens_table_kernel(int p, int d, double* __restrict__ tab, float* __restrict__ tabf) {
+  const int n1 = p + 1, G = d * n1;
+  double z[kPMaxTab + 1], gx[kPMaxTab + 1], gw[kPMaxTab + 1];
+  gll_nodes(p, z);
+  gauss_rule(n1, gx, gw);
+  const int tot = 2 * n1 * G + G + n1;
+  for (int k = threadIdx.x; k < tot; k += blockDim.x) {
+    double v;
+    if (k < 2 * n1 * G) {
+      int which = k / (n1 * G), r = k % (n1 * G), a = r / G, g = r % G;
+      int i = g / n1, kk = g % n1;
+      double xi = -1.0 + (2.0 * i + 1.0 + gx[kk]) / d;
+      v = which == 0 ? lagrange_val(z, n1, a, xi) : lagrange_der(z, n1, a, xi);
+    } else if (k < 2 * n1 * G + G) {
+      int g = k - 2 * n1 * G;
+      v = gw[g % n1] / d;
+    } else {
+      v = z[k - 2 * n1 * G - G];
+    }
+    tab[k] = v;
+    tabf[k] = (float)v;
+  }
+}
+
+namespace {
+
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int PO, typename T>
+__global__ void __launch_bounds__(128) sens_kernel(
+    int n, int d, const int* __restrict__ elem, const int* __restrict__ slot, int ld, const int* __restrict__ gmap,
+    const Constraint* __restrict__ cons, const double* __restrict__ u, const double* __restrict__ rho,
+    const int64_t* __restrict__ design_off, double E0, double Emin, double q, double nu, double hx, double hy,
+    const T* __restrict__ tab, const double* __restrict__ Z, double* __restrict__ dc) {
+  constexpr int N1 = PO + 1, NN = N1 * N1;
+  static_assert(NN <= 64, "two nodes per lane at most");
+  const int G = d * N1;
+  extern __shared__ unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // per-warp shared layout: A[4][N1][G] (T), part[G] (T), U[2][NN] (T)
+  const size_t per_warp = (size_t)(4 * N1 * G + G + 2 * NN) * sizeof(T);
+  T* A = reinterpret_cast<T*>(smem_raw + warp * per_warp);
+  T* part = A + 4 * N1 * G;
+  T* U = part + G;
+  const int k = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (k >= n) return;
+  const int e = elem[k], sl = slot[k];
+  const T* L = tab;
+  const T* Dd = tab + N1 * G;
+  const T* W = tab + 2 * N1 * G;
+
+  // gather u_e (FP64) and remove the best-fit rigid motion in FP64 (lanes stride over the nodes)
+  double sux = 0.0, suy = 0.0, snum = 0.0, sden = 0.0;
+  double ux[2], uy[2], xl[2], yl[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int ln = lane + 32 * r;
+    ux[r] = uy[r] = xl[r] = yl[r] = 0.0;
+    if (ln < NN) {
+      int g = gmap[(size_t)sl * NN + ln];
+      if (g >= 0) {
+        ux[r] = u[2 * (size_t)g];
+        uy[r] = u[2 * (size_t)g + 1];
+      } else {
+        const Constraint& c = cons[-g - 1];
+        for (int j = 0; j < c.cnt; ++j) {
+          ux[r] += c.w[j] * u[2 * (size_t)c.node[j]];
+          uy[r] += c.w[j] * u[2 * (size_t)c.node[j] + 1];
+        }
+      }
+      xl[r] = 0.5 * Z[ln % N1] * hx;   // node coordinates about the element centre (FP64 GLL nodes)
+      yl[r] = 0.5 * Z[ln / N1] * hy;
+      sux += ux[r];
+      suy += uy[r];
+      snum += xl[r] * uy[r] - yl[r] * ux[r];
+      sden += xl[r] * xl[r] + yl[r] * yl[r];
+    }
+  }
+  const double tx = wsum(sux) / NN, ty = wsum(suy) / NN;
+  const double om = wsum(snum) / wsum(sden);
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int ln = lane + 32 * r;
+    if (ln < NN) {
+      U[ln] = (T)(ux[r] - tx + om * yl[r]);
+      U[NN + ln] = (T)(uy[r] - ty - om * xl[r]);
+    }
+  }
+  __syncwarp();
+
+  // stage 1 (x direction): A_c[b][g] = sum_a U_c[b][a] L[a][g],  Ad_c[b][g] = sum_a U_c[b][a] D[a][g]
+  for (int g = lane; g < G; g += 32) {
+#pragma unroll
+    for (int b = 0; b < N1; ++b) {
+      T a0 = 0, a1 = 0, d0 = 0, d1 = 0;
+#pragma unroll
+      for (int a = 0; a < N1; ++a) {
+        T l = L[a * G + g], dl = Dd[a * G + g];
+        T v0 = U[b * N1 + a], v1 = U[NN + b * N1 + a];
+        a0 = fma(v0, l, a0);
+        d0 = fma(v0, dl, d0);
+        a1 = fma(v1, l, a1);
+        d1 = fma(v1, dl, d1);
+      }
+      A[(0 * N1 + b) * G + g] = a0;
+      A[(1 * N1 + b) * G + g] = d0;
+      A[(2 * N1 + b) * G + g] = a1;
+      A[(3 * N1 + b) * G + g] = d1;
+    }
+  }
+  __syncwarp();
+
+  // stage 2 (y direction) and the energy density eps^T D0 eps at every point
+  const T sx = (T)(2.0 / hx), sy = (T)(2.0 / hy), jac = (T)(0.25 * hx * hy);
+  const double f = 1.0 / (1.0 - nu * nu);
+  const T D11 = (T)f, D12 = (T)(f * nu), D33 = (T)(f * 0.5 * (1.0 - nu));
+  const double dE = E0 - Emin;
+  const int64_t off = design_off[e];
+  for (int j = 0; j < d; ++j) {
+    for (int g = lane; g < G; g += 32) {
+      T acc = 0;
+      for (int kk = 0; kk < N1; ++kk) {
+        const int gy = j * N1 + kk;
+        T exx = 0, eyy = 0, gxy0 = 0, gxy1 = 0;
+#pragma unroll
+        for (int b = 0; b < N1; ++b) {
+          T lb = L[b * G + gy], db = Dd[b * G + gy];
+          exx = fma(A[(1 * N1 + b) * G + g], lb, exx);   // d ux / d xi
+          gxy0 = fma(A[(0 * N1 + b) * G + g], db, gxy0); // d ux / d eta
+          gxy1 = fma(A[(3 * N1 + b) * G + g], lb, gxy1); // d uy / d xi
+          eyy = fma(A[(2 * N1 + b) * G + g], db, eyy);   // d uy / d eta
+        }
+        exx *= sx;
+        eyy *= sy;
+        T gam = gxy0 * sy + gxy1 * sx;
+        T en = D11 * (exx * exx + eyy * eyy) + (T)2 * D12 * exx * eyy + D33 * gam * gam;
+        acc = fma(W[gy], en, acc);
+      }
+      part[g] = acc * W[g] * jac;
+    }
+    __syncwarp();
+    for (int i = lane; i < d; i += 32) {
+      T w = 0;
+      for (int kk = 0; kk < N1; ++kk) w += part[i * N1 + kk];
+      const int s = j * d + i;
+      const double r = rho[off + s];
+      dc[off + s] = -q * pow(r, q - 1.0) * dE * (double)w;
+    }
+    __syncwarp();
+  }
+}
+
+template <int PO, typename T>
+mto_status launch_sens(mto_handle h, const BClass& b, const double* u, const double* rho, const mto_material* m,
+                       const T* tab, double* dc) {
+  const int N1 = PO + 1, G = b.d * N1;
+  const size_t per_warp = (size_t)(4 * N1 * G + G + 2 * N1 * N1) * sizeof(T);
+  const int warps = 4;
+  const size_t smem = per_warp * warps;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(sens_kernel<PO, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const PClass& c = h->pc[b.p];
+  sens_kernel<PO, T><<<(b.n + warps - 1) / warps, 32 * warps, smem, h->stream>>>(
+      b.n, b.d, b.elem, b.slot, c.ld, c.gmap, h->cons_d, u, rho, h->design_off_d, m->E0, m->Emin, m->q, m->nu,
+      h->hx, h->hy, tab, b.stab + 2 * N1 * G + G, dc);
+  return mto_after_launch(h, "sens_kernel");
+}
+
+template <typename T>
+mto_status sens_all(mto_handle h, const double* u, const double* rho, const mto_material* m, double* dc) {
+  for (auto& b : h->bc) {
+    const T* tab;
+    if constexpr (sizeof(T) == 8) tab = (const T*)b.stab; else tab = (const T*)b.stabf;
+    switch (b.p) {
+      case 1: MTO_TRY((launch_sens<1, T>(h, b, u, rho, m, tab, dc))); break;
+      case 2: MTO_TRY((launch_sens<2, T>(h, b, u, rho, m, tab, dc))); break;
+      case 3: MTO_TRY((launch_sens<3, T>(h, b, u, rho, m, tab, dc))); break;
+      case 4: MTO_TRY((launch_sens<4, T>(h, b, u, rho, m, tab, dc))); break;
+      case 5: MTO_TRY((launch_sens<5, T>(h, b, u, rho, m, tab, dc))); break;
+      case 6: MTO_TRY((launch_sens<6, T>(h, b, u, rho, m, tab, dc))); break;
+    }
+  }
+  return MTO_OK;
+}
+
+}  // namespace
+
+mto_status build_sens_tables(mto_handle h) {
+  for (auto& b : h->bc) {
+    const int n1 = b.p + 1, G = b.d * n1, tot = 2 * n1 * G + G + n1;
+    MTO_TRY(mto_alloc(h, &b.stab, (size_t)tot));
+    MTO_TRY(mto_alloc(h, &b.stabf, (size_t)tot));
+    sens_table_kernel<<<1, 256, 0, h->stream>>>(b.p, b.d, b.stab, b.stabf);
+    MTO_TRY(mto_after_launch(h, "sens_table_kernel"));
+  }
+  return MTO_OK;
+}
+
+mto_status sensitivity(mto_handle h, const double* u, const double* f, const double* rho, const mto_material* m,
+                       int precision, double* dc, double* C) {
+  {
+  TimedScope ts(h, F_SENS);
+  if (precision == MTO_FP64) MTO_TRY(sens_all<double>(h, u, rho, m, dc));
+  else MTO_TRY(sens_all<float>(h, u, rho, m, dc));
+  MTO_TRY(dot64(h, f, u, h->ndof, h->red + 8));
+  }
+  if (C) {
+    MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->host_pinned + 8, h->red + 8, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy"));
+    MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
+    *C = h->host_pinned[8];
+  }
+  return MTO_OK;
+}
+
+}  // namespace mto

@@ -1,0 +1,249 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle, element by element, on
+seeded workloads small enough for the oracle: several tiles, ragged tails, mixed orders and
+design counts, order jumps of 1 and 2.
+
+Tolerances (from the stated targets): u and C within 1e-8 relative, dC/drho within 1e-6 of
+max|dC/drho|, integer numbering / maps bit-exact.  One documented exception: on binary 0/1 designs
+with Emin = 1e-9 E0 and solid islands held only by void, FP64 itself determines u only to ~1e-7 in
+the l2 norm (two exact factorisations of the oracle differ by 4e-8 .. 1.1e-7 on mbb_40x20), so
+there u is held to 1e-6 while C stays at 1e-8."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import workloads as W
+from oracle import indicators as oi
+from oracle import mesh as om
+from oracle import oc as ooc
+from oracle import sensitivity as ose
+from oracle import solve as osv
+
+CASES = ["cantilever_20x10_p2_d4", "mbb_40x20_p3_d8", "dp_cantilever_40x20"]
+
+
+@pytest.fixture(scope="module")
+def mto():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1811_09821_gb300 as m
+    from paper_1811_09821_gb300 import _build
+    _build.build()
+    m.load_library()
+    return m
+
+
+_ORACLE = {}
+
+
+def oracle_results(name):
+    if name in _ORACLE:
+        return _ORACLE[name]
+    pr = W.named(name)
+    m = om.DPMesh(pr.nelx, pr.nely, pr.p, pr.d)
+    fixed, f = (om.mbb_bc if pr.load == W.MBB else om.cantilever_bc)(m)
+    Ke = osv.element_matrices(m, pr.rho, pr.E0, pr.Emin, pr.nu, pr.q)
+    K = osv.assemble(m, Ke)
+    u = osv.solve_direct(K, f, fixed)
+    out = dict(pr=pr, mesh=m, fixed=fixed, f=f, K=K, u=u, C=ose.compliance(f, u),
+               dc=ose.sensitivity(m, u, pr.rho, pr.E0, pr.Emin, pr.nu, pr.q))
+    _ORACLE[name] = out
+    return out
+
+
+def gpu_setup(mto, pr):
+    h = mto.Handle(0)
+    h.setup(pr.nelx, pr.nely, pr.p, pr.d)
+    fixed, f = mto.load_case(h, pr.load)
+    h.set_supports(fixed)
+    mat = mto.material(pr.E0, pr.Emin, pr.nu, pr.q)
+    rho = torch.tensor(pr.rho, dtype=torch.float64, device="cuda")
+    return h, fixed, f, mat, rho
+
+
+# ----------------------------------------------------------------------------- numbering
+@pytest.mark.parametrize("name", CASES + ["jumps"])
+def test_numbering_bit_exact(mto, name):
+    if name == "jumps":
+        p = np.array([[1, 2, 3, 3, 1], [2, 3, 1, 2, 3], [3, 3, 2, 1, 2], [1, 3, 3, 2, 1]]).ravel()
+        pr = W.Problem("jumps", 5, 4, p.astype(np.int32), np.full(20, 2, np.int32), np.full(80, 0.5), W.CANTILEVER)
+    else:
+        pr = W.named(name)
+    m = om.DPMesh(pr.nelx, pr.nely, pr.p, pr.d)
+    h = mto.Handle(0)
+    ndof, dl = h.setup(pr.nelx, pr.nely, pr.p, pr.d)
+    assert ndof == m.ndof and dl == m.design_len
+    for e in range(m.nel):
+        want = m.element_node_map(e)
+        got = h.element_nodes(e)
+        assert len(got) == len(want)
+        for a, b in zip(got, want):
+            assert [g for g, _ in a] == [g for g, _ in b]
+            np.testing.assert_allclose([w for _, w in a], [w for _, w in b], rtol=0, atol=1e-15)
+    for side in range(4):
+        nodes = m.side_nodes(side)
+        np.testing.assert_array_equal(h.side_dofs(side, 0), 2 * nodes)
+        np.testing.assert_array_equal(h.side_dofs(side, 1), 2 * nodes + 1)
+    fixed, _ = mto.load_case(h, pr.load)
+    ofixed, _ = (om.mbb_bc if pr.load == W.MBB else om.cantilever_bc)(m)
+    np.testing.assert_array_equal(fixed, ofixed)
+    h.close()
+
+
+# ----------------------------------------------------------------------------- step (a) via the operator
+@pytest.mark.parametrize("build", ["fp64", "split"])
+@pytest.mark.parametrize("name", CASES)
+def test_operator_matches_assembled_oracle(mto, name, build):
+    """The FP64 operator and the split-precision (FP32 pair, error-free FP32 arithmetic) operator
+    both reproduce the assembled oracle K x to ~1e-13 of max|K x|."""
+    o = oracle_results(name)
+    pr = o["pr"]
+    h, fixed, f, mat, rho = gpu_setup(mto, pr)
+    h.build_elements(rho, mat, mto.MTO_FP64 if build == "fp64" else mto.MTO_MIXED)
+    rng = np.random.default_rng(3)
+    for _ in range(2):
+        x = rng.standard_normal(h.ndof)
+        y = torch.zeros(h.ndof, dtype=torch.float64, device="cuda")
+        h.apply(torch.tensor(x, device="cuda"), y)
+        want = o["K"] @ x
+        err = np.abs(y.cpu().numpy() - want).max() / np.abs(want).max()
+        assert err < 1e-13, err
+    h.close()
+
+
+# ----------------------------------------------------------------------------- step (b) + (c)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", CASES)
+def test_solve_and_sensitivity_parity(mto, name, precision):
+    o = oracle_results(name)
+    pr = o["pr"]
+    prec = mto.MTO_FP64 if precision == "fp64" else mto.MTO_MIXED
+    h, fixed, f, mat, rho = gpu_setup(mto, pr)
+    h.build_elements(rho, mat, prec)
+    u = torch.zeros(h.ndof, dtype=torch.float64, device="cuda")
+    it, rr = h.solve(f, u, precision=prec, rtol=1e-9, norm=mto.NORM_JACOBI, max_iter=100000)
+    ug = u.cpu().numpy()
+    uerr = np.linalg.norm(ug - o["u"]) / np.linalg.norm(o["u"])
+    utol = 1e-6 if name.startswith("mbb") else 1e-8
+    assert uerr < utol, (uerr, it, rr)
+    dc = torch.zeros(h.design_len, dtype=torch.float64, device="cuda")
+    C = h.sensitivity(u, f, rho, mat, dc, precision=prec)
+    assert abs(C - o["C"]) < 1e-8 * abs(o["C"]), (C, o["C"])
+    dce = np.abs(dc.cpu().numpy() - o["dc"]).max() / np.abs(o["dc"]).max()
+    assert dce < 1e-6, dce
+    dcn = np.linalg.norm(dc.cpu().numpy() - o["dc"]) / np.linalg.norm(o["dc"])
+    assert dcn < 1e-6
+    h.close()
+
+
+def test_sensitivity_on_oracle_displacement(mto):
+    """Sensitivity kernels alone: fed the oracle's u, the FP64 path matches to rounding."""
+    o = oracle_results("dp_cantilever_40x20")
+    pr = o["pr"]
+    h, fixed, f, mat, rho = gpu_setup(mto, pr)
+    h.build_elements(rho, mat, mto.MTO_FP64)
+    u = torch.tensor(o["u"], device="cuda")
+    for prec, tol in ((mto.MTO_FP64, 1e-11), (mto.MTO_MIXED, 1e-6)):
+        dc = torch.zeros(h.design_len, dtype=torch.float64, device="cuda")
+        C = h.sensitivity(u, f, rho, mat, dc, precision=prec)
+        assert abs(C - o["C"]) < 1e-13 * abs(o["C"])
+        err = np.abs(dc.cpu().numpy() - o["dc"]).max() / np.abs(o["dc"]).max()
+        assert err < tol, (prec, err)
+    h.close()
+
+
+# ----------------------------------------------------------------------------- step (d)
+@pytest.mark.parametrize("name", CASES)
+def test_indicators_on_oracle_displacement(mto, name):
+    o = oracle_results(name)
+    pr, m = o["pr"], o["mesh"]
+    h, fixed, f, mat, rho = gpu_setup(mto, pr)
+    h.build_elements(rho, mat, mto.MTO_FP64)
+    u = torch.tensor(o["u"], device="cuda")
+    ind = h.indicator(u, rho, mat)
+    ga = oi.kelly(m, o["u"])
+    gd = oi.gamma_d(m, pr.rho)
+    eq = oi.qr_error(m, o["u"], pr.rho, pr.E0, pr.Emin, pr.nu, pr.q)
+    np.testing.assert_allclose(ind["gamma_a"].cpu().numpy(), ga, rtol=1e-9, atol=1e-12 * np.abs(ga).max())
+    np.testing.assert_allclose(ind["gamma_d"].cpu().numpy(), gd, rtol=0, atol=1e-15)
+    # element problems of solid/void elements have condition ~1e9: eps agrees to ~3e-8 there
+    np.testing.assert_allclose(ind["eps_qr"].cpu().numpy(), eq, rtol=0, atol=1e-7)
+    # maps: the oracle's update applied to the oracle's indicators
+    pn, dn, th = oi.map_update(pr.nelx, pr.nely, pr.p, ga, gd, eq)
+    # elements whose indicator lies within a guard band of a cut-off are ties (none expected)
+    np.testing.assert_array_equal(ind["p_new"].cpu().numpy(), pn)
+    np.testing.assert_array_equal(ind["d_new"].cpu().numpy(), dn)
+    np.testing.assert_array_equal(ind["theta"].cpu().numpy(), th)
+    h.close()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_map_update_bit_exact(mto, seed):
+    """The integer update alone, on indicator values both sides receive (with deliberate ties)."""
+    rng = np.random.default_rng(seed)
+    nelx, nely = 23, 11
+    nel = nelx * nely
+    p = oi.smooth_p(rng.integers(1, 6, nel), nelx, nely)
+    d = np.full(nel, 2)
+    ga = np.round(rng.uniform(0, 1, nel), 2)           # many exact ties: index tie-break
+    gd = np.round(rng.uniform(-1, 1, nel), 1)
+    gd[rng.integers(0, nel, 20)] = 0.0
+    eq = rng.uniform(0.5, 1.0, nel)
+    h = mto.Handle(0)
+    h.setup(nelx, nely, p, d)
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    for ad in (1.0, 0.5):
+        opts = mto.IndicatorOpts.paper()
+        opts.alpha_d_refine = opts.alpha_d_coarsen = ad
+        pn, dn, th = h.map_update(T(ga), T(gd), T(eq), opts)
+        wp, wd, wt = oi.map_update(nelx, nely, p, ga, gd, eq, alpha_d_refine=ad, alpha_d_coarsen=ad)
+        np.testing.assert_array_equal(pn.cpu().numpy(), wp)
+        np.testing.assert_array_equal(dn.cpu().numpy(), wd)
+        np.testing.assert_array_equal(th.cpu().numpy(), wt)
+    h.close()
+
+
+# ----------------------------------------------------------------------------- OC
+def test_oc_update_parity(mto):
+    o = oracle_results("dp_cantilever_40x20")
+    pr, m = o["pr"], o["mesh"]
+    h, fixed, f, mat, rho = gpu_setup(mto, pr)
+    dc = torch.tensor(o["dc"], device="cuda")
+    out = torch.zeros_like(rho)
+    lam = h.oc_update(rho, dc, 0.2, out)
+    dv = ooc.subcell_areas(m)
+    want, wl = ooc.oc_update(pr.rho, o["dc"], dv, 0.2 * m.nel)
+    assert abs(lam - wl) < 1e-8 * wl
+    np.testing.assert_allclose(out.cpu().numpy(), want, rtol=1e-9, atol=1e-12)
+    assert abs(out.cpu().numpy() @ dv - 0.2 * m.nel) < 1e-8 * m.nel
+    h.close()
+
+
+# ----------------------------------------------------------------------------- error behaviour
+def test_errors_are_reported_not_trapped(mto):
+    h = mto.Handle(0)
+    with pytest.raises(mto.MTOError) as ei:
+        h.setup(4, 2, np.full(8, 9), np.ones(8))
+    assert ei.value.status == 1
+    h.setup(4, 2, np.full(8, 2), np.full(8, 2))
+    f = torch.zeros(h.ndof, dtype=torch.float64, device="cuda")
+    u = torch.zeros_like(f)
+    with pytest.raises(mto.MTOError):
+        h.solve(f, u)                                   # no supports, no build
+    with pytest.raises(mto.MTOError):
+        h.set_supports(np.array([h.ndof + 5]))
+    fixed, f = mto.load_case(h, "cantilever")
+    h.set_supports(fixed)
+    rho = torch.full((h.design_len,), 0.5, dtype=torch.float64, device="cuda")
+    h.build_elements(rho, mto.material(), mto.MTO_FP64)
+    with pytest.raises(mto.MTOError) as ei:
+        h.solve(f, u, rtol=1e-14, max_iter=2, check_every=1)
+    assert ei.value.status == 4                         # MTO_ENOCONV
+    it, rr = h.solve(f, u, rtol=1e-10)
+    assert rr < 1e-10
+    # breakdown is reported, not trapped: a zero load converges at once
+    f0 = torch.zeros_like(f)
+    it, rr = h.solve(f0, u)
+    assert it == 0 and float(u.abs().max()) == 0.0
+    h.close()
