@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--precond", default="schwarz", choices=["schwarz", "jacobi"])
+    ap.add_argument("--solve", default="mixed", choices=["mixed", "split64"],
+                    help="mixed: FP32-vector inner CG in FP64 refinement; split64: one CG with FP64 vectors")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
@@ -194,10 +197,14 @@ def run_gpu(args, rank, world, local_rank):
     dc = torch.zeros(dlen, dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
 
+    pc = mto.PREC_SCHWARZ if args.precond == "schwarz" else mto.PREC_JACOBI
+
     def step(prec):
         h.build_elements(rho, mat, prec)
-        it, rr = h.solve(f, u, precision=prec, rtol=args.rtol, max_iter=400000, check_every=64)
-        C = h.sensitivity(u, f, rho, mat, dc, precision=prec, want_C=False)
+        sprec = prec if (prec == mto.MTO_FP64 or args.solve == "mixed") else mto.MTO_FP64
+        it, rr = h.solve(f, u, precision=sprec, rtol=args.rtol, max_iter=400000, check_every=32, precond=pc,
+                         inner_max=4000)
+        h.sensitivity(u, f, rho, mat, dc, precision=prec, want_C=False)
         h.indicator(u, rho, mat)
         return it, rr
 
@@ -257,10 +264,7 @@ def run_gpu(args, rank, world, local_rank):
         t0 = time.perf_counter()
         rho.copy_(rho_h, non_blocking=True)
         f.copy_(f_h, non_blocking=True)
-        h.build_elements(rho, mat, mto.MTO_MIXED)
-        h.solve(f, u, precision=mto.MTO_MIXED, rtol=args.rtol, max_iter=400000, check_every=64)
-        h.sensitivity(u, f, rho, mat, dc, precision=mto.MTO_MIXED, want_C=False)
-        h.indicator(u, rho, mat)
+        step(mto.MTO_MIXED)
         u_h.copy_(u, non_blocking=True)
         dc_h.copy_(dc, non_blocking=True)
         torch.cuda.synchronize(dev)
@@ -268,13 +272,15 @@ def run_gpu(args, rank, world, local_rank):
 
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    n_apply, apply_ms = mixed["families"]["apply32"]
-    # algorithmic bytes of one inner operator launch: the split-precision pair of the packed K_e
-    # (2 x 4 bytes per entry, 528 entries for Q3) and the node map per element, one read of x and
-    # one write of y (FP32) per DOF
+    fam = "apply32" if args.solve == "mixed" else "applydf64"
+    n_apply, apply_ms = mixed["families"][fam]
+    # algorithmic bytes of one operator launch: the split-precision pair of the element matrix in
+    # its circulant-diagonal row ((n_e/2 + 1) n_e entries, 2 x 4 bytes; 544 for Q3) and the node map
+    # per element, one read of x and one write of y per DOF (4 bytes FP32, 8 bytes FP64 vectors)
+    vb = 4 if args.solve == "mixed" else 8
     nn = [(int(p) + 1) ** 2 for p in pr.p]
-    kbytes = sum(8 * ((2 * n) * (2 * n + 1) // 2) + 4 * n for n in nn)
-    bytes_per_launch = kbytes + 2 * 4 * ndof
+    kbytes = sum(8 * ((2 * n) // 2 + 1) * (2 * n) + 4 * n for n in nn)
+    bytes_per_launch = kbytes + 2 * vb * ndof
     ncls = len(set(int(p) for p in pr.p))
     avg_ms = apply_ms / max(n_apply, 1) * ncls     # one apply = ncls class launches
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9 if n_apply else None
@@ -294,14 +300,15 @@ def run_gpu(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": args.workload, "nelx": pr.nelx, "nely": pr.nely, "p": int(pr.p[0]),
                    "d": int(pr.d[0]), "free_dofs": nfree, "design_values": dlen, "rtol": args.rtol,
-                   "residual_norm": "l2", "l2_flush": "512 MB write between timed steps",
+                   "residual_norm": "l2", "precond": args.precond, "solve": args.solve,
+                   "l2_flush": "512 MB write between timed steps",
                    "parallelism": f"replicas x{world}"},
         "mdof_pcg_iter_per_s": nfree * mixed["iters"] / (mixed["ms"] * 1e-3) / 1e6,
         "pcg_iters_per_step": mixed["iters"] / steps,
         "relres": mixed["relres"],
         "families_ms": {k: round(v[1] / steps, 4) for k, v in mixed["families"].items()},
         "gpu_launches": mixed["launches"],
-        "roofline": {"bound": "hbm", "kernel": "apply_df_kernel<3,float> (split-precision EbE operator)",
+        "roofline": {"bound": "hbm", "kernel": f"ebe_kernel<3,split,{'float' if vb == 4 else 'double'}> (element operator)",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "traffic": None,
                      "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_ms * 1e3,

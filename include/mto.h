@@ -78,7 +78,13 @@ typedef struct {
  *  check_every PCG iterations between host convergence checks (>= 1).
  *  norm        residual norm of the stopping tests: MTO_NORM_L2 (||r||_2 / ||f||_2) or
  *              MTO_NORM_JACOBI (sqrt(r^T D^-1 r / f^T D^-1 f), D = diag(K)); the scaled norm also
- *              weighs the rows of nearly void regions (stiffness ~ Emin), which the l2 norm ignores. */
+ *              weighs the rows of nearly void regions (stiffness ~ Emin), which the l2 norm ignores.
+ *  precond     MTO_PREC_JACOBI (point Jacobi) or MTO_PREC_SCHWARZ (element-block additive Schwarz:
+ *              per element the inverse of K_e plus the neighbours' share of the assembled diagonal,
+ *              which captures the near-null modes of solid/void elements).
+ *  inner_max   MTO_MIXED only: cap on the iterations of one inner solve (<= 0: none).
+ * CG iterations run in chunks of check_every (rounded up to a multiple of 4), each a CUDA graph;
+ * the reported count stops at convergence, but a chunk already launched completes (cheaply). */
 typedef struct {
   int32_t precision;
   double rtol;
@@ -88,7 +94,12 @@ typedef struct {
   int32_t warm_start;
   int32_t check_every;
   int32_t norm;
+  int32_t precond;
+  int32_t inner_max;
 } mto_solve_opts;
+
+#define MTO_PREC_JACOBI 0
+#define MTO_PREC_SCHWARZ 1
 
 #define MTO_NORM_L2 0
 #define MTO_NORM_JACOBI 1
@@ -169,6 +180,15 @@ mto_status mto_build_elements(mto_handle h, const double* rho, const mto_materia
  * from the split pair the value is hi + lo.  Allocates a small device buffer; synchronises. */
 mto_status mto_element_matrix(mto_handle h, int64_t e, double* packed);
 
+/* Which kernel forms the element matrices in mto_build_elements:
+ * MTO_BUILD_TENSOR: classes with d <= 8 run as one exact sliced GEMM per class on the tensor
+ *   cores (tcgen05, BF16 slices, FP32 TMEM accumulators, ~48-bit result); larger d fall back to
+ *   the FP64 CUDA-core kernel.
+ * MTO_BUILD_SIMT (default): the FP64 CUDA-core kernel for every class. */
+#define MTO_BUILD_TENSOR 0
+#define MTO_BUILD_SIMT 1
+mto_status mto_set_build_path(mto_handle h, int32_t path);
+
 /* Step (b): solve K u = f on the free DOFs (u = 0 on supports) with the options above, using the
  * matrices of the last mto_build_elements.  f: device double[ndof]; u: device double[ndof]
  * (initial guess when opts->warm_start, overwritten with the solution).  *iters receives the
@@ -226,6 +246,7 @@ mto_status mto_oc_update(mto_handle h, const double* rho, const double* dc, doub
 #define MTO_TIME_INDICATOR 4 /* step (d): indicators and map update */
 #define MTO_TIME_VECTOR 5    /* PCG vector updates, residuals, precision conversions */
 #define MTO_TIME_APPLYDF64 6 /* split-precision operator on FP64 vectors (refinement residuals) */
+#define MTO_TIME_PRECOND 7   /* element-block preconditioner applications and set-up */
 mto_status mto_timing_enable(mto_handle h, int32_t enable);
 mto_status mto_timing_read(mto_handle h, int32_t family, int64_t* launches, double* total_ms);
 

@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libmto.so")
 
 MTO_FP64, MTO_MIXED = 0, 1
 NORM_L2, NORM_JACOBI = 0, 1
+BUILD_TENSOR, BUILD_SIMT = 0, 1
+PREC_JACOBI, PREC_SCHWARZ = 0, 1
 STATUS = {0: "MTO_OK", 1: "MTO_EINVAL", 2: "MTO_ENOMEM", 3: "MTO_ECUDA", 4: "MTO_ENOCONV", 5: "MTO_ENAN",
           6: "MTO_ETIMEOUT"}
 P_MAX, D_MAX = 6, 16
@@ -38,7 +40,8 @@ class Material(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("rtol", ctypes.c_double), ("inner_rtol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("warm_start", ctypes.c_int32),
-                ("check_every", ctypes.c_int32), ("norm", ctypes.c_int32)]
+                ("check_every", ctypes.c_int32), ("norm", ctypes.c_int32), ("precond", ctypes.c_int32),
+                ("inner_max", ctypes.c_int32)]
 
 
 class IndicatorOpts(ctypes.Structure):
@@ -57,8 +60,10 @@ class IndicatorOpts(ctypes.Structure):
 SYMBOLS = ["mto_create", "mto_destroy", "mto_last_error", "mto_set_stream", "mto_setup", "mto_set_supports",
            "mto_vertex_dof", "mto_side_dofs", "mto_element_nodes", "mto_element_matrix", "mto_build_elements", "mto_solve", "mto_apply",
            "mto_sensitivity", "mto_indicator", "mto_map_update", "mto_oc_update", "mto_timing_enable", "mto_timing_read",
+           "mto_set_build_path",
            "mto_memory", "mto_launch_count"]
-TIME_FAMILIES = {"apply32": 0, "apply64": 1, "build": 2, "sens": 3, "indicator": 4, "vector": 5, "applydf64": 6}
+TIME_FAMILIES = {"apply32": 0, "apply64": 1, "build": 2, "sens": 3, "indicator": 4, "vector": 5, "applydf64": 6,
+                 "precond": 7}
 
 _lib = None
 
@@ -92,6 +97,7 @@ def load_library(path=LIB_PATH):
         "mto_map_update": ([vp, vp, vp, vp, P(IndicatorOpts), vp, vp, vp], ctypes.c_int),
         "mto_oc_update": ([vp, vp, vp, dbl, dbl, dbl, vp, P(dbl)], ctypes.c_int),
         "mto_timing_enable": ([vp, i32], ctypes.c_int),
+        "mto_set_build_path": ([vp, i32], ctypes.c_int),
         "mto_timing_read": ([vp, i32, P(i64), P(dbl)], ctypes.c_int),
         "mto_memory": ([vp, P(i64)], ctypes.c_int),
         "mto_launch_count": ([vp, P(i64)], ctypes.c_int),
@@ -200,8 +206,10 @@ class Handle:
         self._check(self.L.mto_build_elements(self.h, _ptr(rho, torch.float64), ctypes.byref(mat), precision))
 
     def solve(self, f, u, precision=MTO_FP64, rtol=1e-8, inner_rtol=1e-4, max_iter=200000, max_outer=50,
-              warm_start=False, check_every=64, norm=NORM_L2, raise_on_noconv=True):
-        o = SolveOpts(precision, rtol, inner_rtol, max_iter, max_outer, int(bool(warm_start)), check_every, norm)
+              warm_start=False, check_every=64, norm=NORM_L2, precond=PREC_SCHWARZ, inner_max=0,
+              raise_on_noconv=True):
+        o = SolveOpts(precision, rtol, inner_rtol, max_iter, max_outer, int(bool(warm_start)), check_every, norm,
+                      precond, inner_max)
         it, rr = ctypes.c_int32(), ctypes.c_double()
         st = self.L.mto_solve(self.h, _ptr(f, torch.float64), _ptr(u, torch.float64), ctypes.byref(o),
                               ctypes.byref(it), ctypes.byref(rr))
@@ -248,6 +256,9 @@ class Handle:
         self._check(self.L.mto_oc_update(self.h, _ptr(rho, torch.float64), _ptr(dc, torch.float64), volfrac, move, eta,
                                          _ptr(rho_new, torch.float64), ctypes.byref(lam)))
         return lam.value
+
+    def set_build_path(self, path):
+        self._check(self.L.mto_set_build_path(self.h, path))
 
     def timing_enable(self, on=True):
         self._check(self.L.mto_timing_enable(self.h, int(bool(on))))

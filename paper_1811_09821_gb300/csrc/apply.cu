@@ -81,17 +81,79 @@ __device__ __forceinline__ void df_acc(float& sh, float& sl, float pp, float pe)
 // so each stored entry serves both triangles.  kDF = false: FP64 matrices and arithmetic (plain
 // FP64 path).  kDF = true: the split-precision pair on the FP32 pipes with error-free products and
 // sums (~48-bit accurate), vectors TX = double (refinement residuals) or float (inner iterations).
-// Also returns x^T y (= sum_e x_e^T K_e x_e) into *pq so the CG curvature needs no extra pass.
+// A reduction output of one launch: every block stores its partial, the last block to finish
+// (counted with an atomic) sums the partials in index order (deterministic) into *res and
+// re-arms the counter.  Consumers read res[0 .. nres) (one scalar per launch).
+struct Red {
+  double* part;   // [gridDim.x]
+  unsigned* cnt;
+  double* res;
+};
+
+__device__ __forceinline__ void reduce_out(double v, const Red& rd) {
+  __shared__ int last;
+  v = block_sum(v);
+  if (threadIdx.x == 0) {
+    rd.part[blockIdx.x] = v;
+    __threadfence();
+    const unsigned t = atomicAdd(rd.cnt, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double s = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += __ldcg(rd.part + i);
+    s = block_sum(s);
+    if (threadIdx.x == 0) {
+      *rd.res = s;
+      *rd.cnt = 0u;
+    }
+  }
+}
+
+// sum of a few launch results, same order in every thread
+__device__ __forceinline__ double sum_res(const double* __restrict__ res, int n) {
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += __ldcg(res + i);
+  return s;
+}
+
+// Each launch reduces x^T y (= sum_e x_e^T K_e x_e) into one scalar, so CG gets its curvature
+// without an extra pass and without same-address atomics on the data.  With a convergence test
+// `cv` the whole launch returns once the residual norm of the previous vector update meets it,
+// after block 0 records the iteration count in *done.
+struct ConvTest {
+  const double* res;   // residual norm^2 results (nullptr: no test)
+  int n;
+  const double* ref;   // reference norm^2
+  double tol2;
+  const int* base;     // chunk base iteration (device)
+  int local;           // iteration within the chunk
+  int* done;
+  int* err;
+};
+
 template <int PO, bool kDF, typename TX>
 __global__ void __launch_bounds__(256) ebe_kernel(const double* __restrict__ K64, const float* __restrict__ Kh,
                                                   const float* __restrict__ Kl, int L, int n,
                                                   const int* __restrict__ gmap, const Constraint* __restrict__ cons,
-                                                  const TX* __restrict__ x, TX* __restrict__ y,
-                                                  double* __restrict__ pq, const int* __restrict__ done) {
+                                                  const TX* __restrict__ x, TX* __restrict__ y, Red red,
+                                                  const int* __restrict__ done, ConvTest cv) {
   constexpr int N1 = PO + 1, NN = N1 * N1, NE = 2 * NN, ND = NE / 2 + 1;
   constexpr int W = WarpShape<NE>::W, G = WarpShape<NE>::G, M = WarpShape<NE>::M;
   constexpr bool kSplitX = kDF && sizeof(TX) == 8;
   if (done && *done) return;
+  if (cv.res) {
+    const double rr = sum_res(cv.res, cv.n);
+    if (!(rr > cv.tol2 * *cv.ref)) {   // converged, or a NaN residual
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (!(rr == rr)) *cv.err = MTO_ENAN;
+        *cv.done = *cv.base + cv.local + 1;
+      }
+      return;
+    }
+  }
   const int lane = threadIdx.x & 31;
   const int li = lane % W, gb = lane - li, gid = lane / W;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -189,150 +251,210 @@ __global__ void __launch_bounds__(256) ebe_kernel(const double* __restrict__ K64
         const Constraint& c = cons[-g - 1];
         for (int q = 0; q < c.cnt; ++q) atomicAdd(y + 2 * (size_t)c.node[q] + (i & 1), (TX)(c.w[q] * yv));
       }
-      if (pq) dot += xd[m] * yv;
+      if (red.part) dot += xd[m] * yv;
     }
   }
-  if (pq) {
-    double s = block_sum(dot);
-    if (threadIdx.x == 0) atomicAdd(pq, s);
+  if (red.part) reduce_out(dot, red);
+}
+
+}  // namespace
+
+// Blocks of one element-operator launch for an order class (fixed per class size).
+template <int PO>
+int ebe_blocks_p(int n) {
+  constexpr int NE = 2 * (PO + 1) * (PO + 1);
+  constexpr int G = WarpShape<NE>::G;
+  const int warps = (n + G - 1) / G;
+  return grid_for((int64_t)warps * 32, 256, 152 * 8);
+}
+
+int ebe_blocks(int p, int n) {
+  switch (p) {
+    case 1: return ebe_blocks_p<1>(n);
+    case 2: return ebe_blocks_p<2>(n);
+    case 3: return ebe_blocks_p<3>(n);
+    case 4: return ebe_blocks_p<4>(n);
+    case 5: return ebe_blocks_p<5>(n);
+    default: return ebe_blocks_p<6>(n);
   }
 }
 
+namespace {
+
 template <int PO, bool kDF, typename TX>
-void launch_ebe(mto_handle h, const PClass& c, const TX* x, TX* y, double* pq, const int* done) {
-  constexpr int NE = 2 * (PO + 1) * (PO + 1);
-  constexpr int G = WarpShape<NE>::G;
-  const int warps = (c.n + G - 1) / G;
-  const int blocks = grid_for((int64_t)warps * 32, 256, 152 * 8);
-  ebe_kernel<PO, kDF, TX><<<blocks, 256, 0, h->stream>>>(kDF ? nullptr : c.K64, c.K32, c.K32lo, c.L, c.n, c.gmap,
-                                                          h->cons_d, x, y, pq, done);
+void launch_ebe(mto_handle h, const PClass& c, const double* M64, const float* Mh, const float* Ml, const TX* x,
+                TX* y, Red red, const int* done, const ConvTest& cv) {
+  ebe_kernel<PO, kDF, TX><<<ebe_blocks_p<PO>(c.n), 256, 0, h->stream>>>(M64, Mh, Ml, c.L, c.n, c.gmap, h->cons_d, x,
+                                                                        y, red, done, cv);
 }
 
-// The assembled operator: FP64 element matrices on the FP64 pipes (plain FP64 path), or the
-// split-precision pair on the FP32 pipes (mixed path) with FP64 (residual) or FP32 (inner) vectors.
+// reduction slot k of the CG buffers (launch j writes part + j * kPartStride, res[j], cnt[j])
+Red red_slot(mto_handle h, int k, int j) {
+  if (k < 0) return Red{nullptr, nullptr, nullptr};
+  return Red{h->cg_part + (size_t)k * h->cg_stride + (size_t)j * h->cg_class_stride, h->cg_cnt + 8 * k + j,
+             h->cg_res + 8 * k + j};
+}
+
+// y += sum_e P_e^T A_e P_e x over all order classes, where A_e is the element stiffness (which = 0)
+// or the element-block preconditioner (which = 1).  FP64 matrices on the FP64 pipes (plain FP64
+// path) or the split-precision pair on the FP32 pipes (mixed path) with FP64 or FP32 vectors.
+// x^T y goes to reduction slot `slot` (one result per class launch; -1: not wanted); *nres
+// receives the number of class launches.
 template <typename T>
-mto_status apply_all(mto_handle h, const T* x, T* y, double* pq, const int* done) {
+mto_status apply_all(mto_handle h, int which, const T* x, T* y, int slot, const int* done, ConvTest cv,
+                     int* nres = nullptr) {
   const bool df = h->built_precision == MTO_MIXED;
-  TimedScope ts(h, df ? (sizeof(T) == 8 ? F_APPLYDF64 : F_APPLY32) : F_APPLY64);
+  const int fam = which == 1 ? F_PRECOND : (df ? (sizeof(T) == 8 ? F_APPLYDF64 : F_APPLY32) : F_APPLY64);
+  TimedScope ts(h, fam);
+  int ci = 0;
   for (int p = 1; p <= MTO_P_MAX; ++p) {
     const PClass& c = h->pc[p];
     if (c.n == 0) continue;
+    const double* M64 = which ? c.B64 : c.K64;
+    const float* Mh = which ? c.B32 : c.K32;
+    const float* Ml = which ? c.B32lo : c.K32lo;
+    const Red pp = red_slot(h, slot, ci);
     if (df) {
-      if (!c.K32 || !c.K32lo) return mto_fail(h, MTO_EINVAL, "split-precision element matrices are not built");
+      if (!Mh || !Ml) return mto_fail(h, MTO_EINVAL, "split-precision element matrices are not built");
       switch (p) {
-        case 1: launch_ebe<1, true, T>(h, c, x, y, pq, done); break;
-        case 2: launch_ebe<2, true, T>(h, c, x, y, pq, done); break;
-        case 3: launch_ebe<3, true, T>(h, c, x, y, pq, done); break;
-        case 4: launch_ebe<4, true, T>(h, c, x, y, pq, done); break;
-        case 5: launch_ebe<5, true, T>(h, c, x, y, pq, done); break;
-        case 6: launch_ebe<6, true, T>(h, c, x, y, pq, done); break;
+        case 1: launch_ebe<1, true, T>(h, c, M64, Mh, Ml, x, y, pp, done, cv); break;
+        case 2: launch_ebe<2, true, T>(h, c, M64, Mh, Ml, x, y, pp, done, cv); break;
+        case 3: launch_ebe<3, true, T>(h, c, M64, Mh, Ml, x, y, pp, done, cv); break;
+        case 4: launch_ebe<4, true, T>(h, c, M64, Mh, Ml, x, y, pp, done, cv); break;
+        case 5: launch_ebe<5, true, T>(h, c, M64, Mh, Ml, x, y, pp, done, cv); break;
+        case 6: launch_ebe<6, true, T>(h, c, M64, Mh, Ml, x, y, pp, done, cv); break;
       }
     } else {
       if constexpr (sizeof(T) == 8) {
-        if (!c.K64) return mto_fail(h, MTO_EINVAL, "FP64 element matrices are not built");
+        if (!M64) return mto_fail(h, MTO_EINVAL, "FP64 element matrices are not built");
         switch (p) {
-          case 1: launch_ebe<1, false, T>(h, c, x, y, pq, done); break;
-          case 2: launch_ebe<2, false, T>(h, c, x, y, pq, done); break;
-          case 3: launch_ebe<3, false, T>(h, c, x, y, pq, done); break;
-          case 4: launch_ebe<4, false, T>(h, c, x, y, pq, done); break;
-          case 5: launch_ebe<5, false, T>(h, c, x, y, pq, done); break;
-          case 6: launch_ebe<6, false, T>(h, c, x, y, pq, done); break;
+          case 1: launch_ebe<1, false, T>(h, c, M64, Mh, Ml, x, y, pp, done, cv); break;
+          case 2: launch_ebe<2, false, T>(h, c, M64, Mh, Ml, x, y, pp, done, cv); break;
+          case 3: launch_ebe<3, false, T>(h, c, M64, Mh, Ml, x, y, pp, done, cv); break;
+          case 4: launch_ebe<4, false, T>(h, c, M64, Mh, Ml, x, y, pp, done, cv); break;
+          case 5: launch_ebe<5, false, T>(h, c, M64, Mh, Ml, x, y, pp, done, cv); break;
+          case 6: launch_ebe<6, false, T>(h, c, M64, Mh, Ml, x, y, pp, done, cv); break;
         }
       } else {
         return mto_fail(h, MTO_EINVAL, "FP32 vectors need the split-precision build");
       }
     }
+    ++ci;
     MTO_TRY(mto_after_launch(h, "ebe_kernel"));
   }
+  if (nres) *nres = ci;
   return MTO_OK;
 }
 
-// ---------------------------------------------------------------------------------- PCG kernels
-// Iteration k uses scalar slot k & 3 for its reductions; the previous iteration's r^T z is in
-// slot (k + 3) & 3.  Slot (k + 2) & 3 is cleared here for iteration k + 2 (no kernel of
-// iterations k and k + 1 reads it).
 
-// x += alpha p; r -= alpha q (free DOFs, invd != 0), q = 0; accumulate r^T D^-1 r and r^T r.
-template <typename T>
-__global__ void __launch_bounds__(256) cg_update_kernel(int64_t n, T* __restrict__ x, T* __restrict__ r,
-                                                        const T* __restrict__ p, T* __restrict__ q,
-                                                        const T* __restrict__ invd, Scalars* __restrict__ S,
-                                                        int k, const int* __restrict__ done) {
+// ---------------------------------------------------------------------------------- CG
+// Preconditioned CG (Hestenes-Stiefel form).  Per iteration: the operator launch q = K p, which
+// also yields p^T K p; a fused vector kernel (alpha, x, r, q = 0, Jacobi z and r^T z, r^T r,
+// r^T D^-1 r); the element-block preconditioner z = M^-1 r (Schwarz only, also yielding r^T z);
+// and the direction kernel (convergence test, beta, p = z + beta p).  The curvature p^T K p is
+// accumulated directly (never formed by subtraction), which matters at the 1e9 stiffness contrast
+// of these problems.  Every reduction is finished by the last block of its launch in a fixed order
+// (deterministic); consumers add the few launch results of a slot in class order.  Slots alternate
+// by iteration parity: kGam = r^T z, kDel = p^T K p, kRR = r^T r, kRD = r^T D^-1 r.
+constexpr int kGam = 0, kDel = 2, kRR = 4, kRD = 6;
+
+template <typename T, bool kJacobi>
+__global__ void __launch_bounds__(256) cg_vector_kernel(
+    int64_t n, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, T* __restrict__ q, T* __restrict__ z,
+    const T* __restrict__ invd, const double* __restrict__ gin, int ng, const double* __restrict__ pin, int np,
+    Red gout, Red rrout, Red rdout, const int* __restrict__ base, int local, int* __restrict__ done,
+    int* __restrict__ err) {
   if (*done) return;
-  const double alpha = S[(k + 3) & 3].rz / S[k & 3].pq;
+  const double rz = sum_res(gin, ng);
+  const double pq = sum_res(pin, np);
+  const double alpha = rz / pq;
+  if (!(pq > 0.0) || !isfinite(alpha)) {
+    // rz = 0: the residual vanished (exact solution); otherwise a breakdown
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (rz != 0.0) *err = MTO_ENAN;
+      *done = *base + local + 1;
+    }
+    return;
+  }
   const T a = (T)alpha;
-  double rz = 0.0, rr = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    T inv = invd[i];
-    T qi = q[i];
-    q[i] = 0;
+  double g = 0.0, rr = 0.0, rd = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const T inv = invd[j];
+    const T qj = q[j];
+    q[j] = (T)0;
+    if (!kJacobi) z[j] = (T)0;
     if (inv != (T)0) {
-      x[i] = fma(a, p[i], x[i]);
-      T ri = fma(-a, qi, r[i]);
-      r[i] = ri;
-      double rd = (double)ri;
-      rz += rd * rd * (double)inv;
-      rr += rd * rd;
+      x[j] = fma(a, p[j], x[j]);
+      const T rj = fma(-a, qj, r[j]);
+      r[j] = rj;
+      const double rjd = (double)rj;
+      if (kJacobi) g += rjd * rjd * (double)inv;
+      rr += rjd * rjd;
+      rd += rjd * rjd * (double)inv;
     }
   }
-  rz = block_sum(rz);
-  if (threadIdx.x == 0) atomicAdd(&S[k & 3].rz, rz);
-  rr = block_sum(rr);
-  if (threadIdx.x == 0) atomicAdd(&S[k & 3].rr, rr);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    Scalars z = {0.0, 0.0, 0.0, 0.0};
-    S[(k + 2) & 3] = z;
-  }
+  if (kJacobi) reduce_out(g, gout);
+  reduce_out(rr, rrout);
+  reduce_out(rd, rdout);
 }
 
-// p = D^-1 r + beta p; convergence / breakdown test on slot k (block 0): r^T r (use_rz = 0) or
-// r^T D^-1 r (use_rz = 1) against tol2 * (*ref).
-template <typename T>
-__global__ void __launch_bounds__(256) cg_direction_kernel(int64_t n, const T* __restrict__ r, T* __restrict__ p,
-                                                           const T* __restrict__ invd, Scalars* __restrict__ S,
-                                                           int k, const double* __restrict__ ref, double tol2,
-                                                           int use_rz, int* __restrict__ done, int* __restrict__ err) {
-  if (*done) return;
-  const double beta = S[k & 3].rz / S[(k + 3) & 3].rz;
+// convergence test on the new residual, then beta = (r^T z)_new / (r^T z)_old and p = z + beta p
+// (Jacobi: z = D^-1 r on the fly)
+template <typename T, bool kJacobi>
+__global__ void __launch_bounds__(256) cg_direction_kernel(
+    int64_t n, const T* __restrict__ r, const T* __restrict__ z, T* __restrict__ p, const T* __restrict__ invd,
+    const double* __restrict__ gnew, const double* __restrict__ gold, int ng, ConvTest cv) {
+  if (*cv.done) return;
+  const double crit = sum_res(cv.res, cv.n);
+  if (!(crit > cv.tol2 * *cv.ref)) {   // converged, or a NaN residual
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (!(crit == crit)) *cv.err = MTO_ENAN;
+      *cv.done = *cv.base + cv.local + 1;
+    }
+    return;
+  }
+  const double beta = sum_res(gnew, ng) / sum_res(gold, ng);
   const T b = (T)beta;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = fma(b, p[i], invd[i] * r[i]);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    double rr = S[k & 3].rr;
-    double pq = S[k & 3].pq;
-    double crit = use_rz ? S[k & 3].rz : rr;
-    if (!isfinite(rr) || !isfinite(S[k & 3].rz) || !(pq > 0.0)) {
-      if (!(rr == 0.0)) *err = MTO_ENAN;
-      *done = k + 1;
-    } else if (crit <= tol2 * (*ref)) {
-      *done = k + 1;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const T zj = kJacobi ? invd[j] * r[j] : z[j];
+    p[j] = fma(b, p[j], zj);
+  }
+}
+
+// start of a CG run from the residual r (zero on supports): q = 0 and, for Jacobi, p = D^-1 r with
+// r^T z; for Schwarz z = 0 (the preconditioner launch fills it), p set afterwards
+template <typename T, bool kJacobi>
+__global__ void __launch_bounds__(256) cg_init_kernel(int64_t n, const T* __restrict__ r, T* __restrict__ p,
+                                                      T* __restrict__ q, T* __restrict__ z,
+                                                      const T* __restrict__ invd, Red gout) {
+  double g = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    q[j] = (T)0;
+    if (kJacobi) {
+      const T pj = invd[j] * r[j];
+      p[j] = pj;
+      g += (double)r[j] * (double)pj;
+    } else {
+      z[j] = (T)0;
     }
   }
+  if (kJacobi) reduce_out(g, gout);
 }
 
-// p = D^-1 r; slot 3 <- (r^T D^-1 r, r^T r) (the "iteration -1" values); clears slots 0 and 1.
 template <typename T>
-__global__ void __launch_bounds__(256) cg_init_kernel(int64_t n, const T* __restrict__ r, T* __restrict__ p,
-                                                      const T* __restrict__ invd, Scalars* __restrict__ S) {
-  double rz = 0.0, rr = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    T ri = r[i];
-    p[i] = invd[i] * ri;
-    double rd = (double)ri;
-    rz += rd * rd * (double)invd[i];
-    rr += rd * rd;
-  }
-  rz = block_sum(rz);
-  if (threadIdx.x == 0) atomicAdd(&S[3].rz, rz);
-  rr = block_sum(rr);
-  if (threadIdx.x == 0) atomicAdd(&S[3].rr, rr);
+__global__ void __launch_bounds__(256) copy_kernel(int64_t n, const T* __restrict__ a, T* __restrict__ b) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    b[j] = a[j];
 }
 
-// r = f - Ku on free DOFs, 0 on supports; out[0] += r^T r, out[1] += f^T f, out[2] += r^T D^-1 r,
-// out[3] += f^T D^-1 f (free DOFs)
+__global__ void advance_kernel(int* base, int by) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *base += by;
+}
+
+// r = f - Ku on free DOFs, 0 on supports; per-block partials of r^T r, f^T f, r^T D^-1 r, f^T D^-1 f
 __global__ void __launch_bounds__(256) residual_kernel(int64_t n, const double* __restrict__ f,
                                                        const double* __restrict__ Ku, const double* __restrict__ invd,
-                                                       double* __restrict__ r, double* __restrict__ out) {
+                                                       double* __restrict__ r, double* __restrict__ part) {
   double rr = 0.0, ff = 0.0, rd = 0.0, fd = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double v = 0.0;
@@ -347,23 +469,33 @@ __global__ void __launch_bounds__(256) residual_kernel(int64_t n, const double* 
     rr += v * v;
   }
   rr = block_sum(rr);
-  if (threadIdx.x == 0) atomicAdd(&out[0], rr);
   ff = block_sum(ff);
-  if (threadIdx.x == 0) atomicAdd(&out[1], ff);
   rd = block_sum(rd);
-  if (threadIdx.x == 0) atomicAdd(&out[2], rd);
   fd = block_sum(fd);
-  if (threadIdx.x == 0) atomicAdd(&out[3], fd);
+  if (threadIdx.x == 0) {
+    part[4 * blockIdx.x + 0] = rr;
+    part[4 * blockIdx.x + 1] = ff;
+    part[4 * blockIdx.x + 2] = rd;
+    part[4 * blockIdx.x + 3] = fd;
+  }
 }
 
-// r32 = (float)(r * scale), x32 = 0, q32 = 0
+// one block: out[k] = sum_b part[4 b + k] (fixed order)
+__global__ void sum4_kernel(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  for (int k = 0; k < 4; ++k) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[4 * b + k];
+    v = block_sum(v);
+    if (threadIdx.x == 0) out[k] = v;
+  }
+}
+
+// r32 = (float)(r * scale)
 __global__ void __launch_bounds__(256) demote_kernel(int64_t n, const double* __restrict__ r, double scale,
-                                                     float* __restrict__ r32, float* __restrict__ x32,
-                                                     float* __restrict__ q32) {
+                                                     float* __restrict__ r32, float* __restrict__ x32) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     r32[i] = (float)(r[i] * scale);
     x32[i] = 0.0f;
-    q32[i] = 0.0f;
   }
 }
 
@@ -380,24 +512,183 @@ __global__ void __launch_bounds__(256) mask_kernel(int64_t n, const double* __re
 }
 
 __global__ void __launch_bounds__(256) dot_kernel(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
-                                                  double* __restrict__ out) {
+                                                  double* __restrict__ part) {
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     s += a[i] * b[i];
   s = block_sum(s);
-  if (threadIdx.x == 0) atomicAdd(out, s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// FP64 residual r = f - K u (masked) and its squared norms into h->red[0..3] (l2: r, f; Jacobi:
-// r, f); returns host copies of the pair selected by `norm`.
+__global__ void sum1_kernel(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[b];
+  v = block_sum(v);
+  if (threadIdx.x == 0) *out = v;
+}
+
+constexpr int kVecBlocks = 152 * 4;   // grid of the vector kernels (fixed: partial counts)
+
+template <typename T>
+struct CGVecs {
+  T *x, *r, *p, *q, *z;
+  const T* invd;
+};
+
+template <typename T>
+CGVecs<T> cg_vecs(mto_handle h, T* x, T* r);
+template <>
+CGVecs<double> cg_vecs<double>(mto_handle h, double* x, double* r) {
+  return {x, r, h->p64, h->w64, h->u64, h->invd64};
+}
+template <>
+CGVecs<float> cg_vecs<float>(mto_handle h, float* x, float* r) {
+  return {x, r, h->p32, h->w32, h->u32, h->invd32};
+}
+
+// result j of reduction slot k
+inline const double* res_slot(mto_handle h, int k) { return h->cg_res + 8 * k; }
+
+// The launches of CG iteration `local` of a chunk (nc = number of order classes).
+template <typename T>
+mto_status cg_iteration(mto_handle h, const CGVecs<T>& v, bool schwarz, int nrm, const double* ref, double tol2,
+                        int local, int nc) {
+  const int64_t n = h->ndof;
+  const int par = local & 1, nxt = par ^ 1;
+  const int ng = schwarz ? nc : 1;
+  ConvTest none{};
+  MTO_TRY(apply_all<T>(h, 0, v.p, v.q, kDel + par, h->flags, none));
+  {
+    TimedScope ts(h, F_VECTOR);
+    if (schwarz)
+      cg_vector_kernel<T, false><<<kVecBlocks, 256, 0, h->stream>>>(
+          n, v.x, v.r, v.p, v.q, v.z, v.invd, res_slot(h, kGam + par), ng, res_slot(h, kDel + par), nc,
+          red_slot(h, -1, 0), red_slot(h, kRR + nxt, 0), red_slot(h, kRD + nxt, 0), h->cg_base, local, h->flags,
+          h->flags + 1);
+    else
+      cg_vector_kernel<T, true><<<kVecBlocks, 256, 0, h->stream>>>(
+          n, v.x, v.r, v.p, v.q, v.z, v.invd, res_slot(h, kGam + par), ng, res_slot(h, kDel + par), nc,
+          red_slot(h, kGam + nxt, 0), red_slot(h, kRR + nxt, 0), red_slot(h, kRD + nxt, 0), h->cg_base, local,
+          h->flags, h->flags + 1);
+    MTO_TRY(mto_after_launch(h, "cg_vector_kernel"));
+  }
+  if (schwarz) MTO_TRY(apply_all<T>(h, 1, v.r, v.z, kGam + nxt, h->flags, none));
+  {
+    TimedScope ts(h, F_VECTOR);
+    ConvTest cv{res_slot(h, nrm ? kRD + nxt : kRR + nxt), 1, ref, tol2, h->cg_base, local, h->flags, h->flags + 1};
+    if (schwarz)
+      cg_direction_kernel<T, false><<<kVecBlocks, 256, 0, h->stream>>>(
+          n, v.r, v.z, v.p, v.invd, res_slot(h, kGam + nxt), res_slot(h, kGam + par), ng, cv);
+    else
+      cg_direction_kernel<T, true><<<kVecBlocks, 256, 0, h->stream>>>(
+          n, v.r, v.z, v.p, v.invd, res_slot(h, kGam + nxt), res_slot(h, kGam + par), ng, cv);
+    MTO_TRY(mto_after_launch(h, "cg_direction_kernel"));
+  }
+  return MTO_OK;
+}
+
+// CG on (x, r) of type T: r is the residual of x (free DOFs, zero on supports).  Stops when the
+// residual norm^2 (l2 or Jacobi) <= tol2 * (*ref) or after max_it iterations.  Iterations run in
+// chunks of `chunk` (even), each captured once as a CUDA graph and replayed.
+template <typename T>
+mto_status run_cg(mto_handle h, T* x, T* r, bool schwarz, int nrm, const double* ref, double tol2, int max_it,
+                  int chunk, int* iters) {
+  const int64_t n = h->ndof;
+  CGVecs<T> v = cg_vecs<T>(h, x, r);
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->flags, 0, 2 * sizeof(int), h->stream), "memset"));
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->cg_base, 0, sizeof(int), h->stream), "memset"));
+  // a launch that ended the run early may have left a block count behind
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->cg_cnt, 0, 64 * sizeof(unsigned), h->stream), "memset"));
+  ConvTest none{};
+  int nc = 0;
+  for (int p = 1; p <= MTO_P_MAX; ++p)
+    if (h->pc[p].n) ++nc;
+  {
+    TimedScope ts(h, F_VECTOR);
+    if (schwarz)
+      cg_init_kernel<T, false><<<kVecBlocks, 256, 0, h->stream>>>(n, v.r, v.p, v.q, v.z, v.invd, red_slot(h, -1, 0));
+    else
+      cg_init_kernel<T, true><<<kVecBlocks, 256, 0, h->stream>>>(n, v.r, v.p, v.q, v.z, v.invd,
+                                                                 red_slot(h, kGam, 0));
+    MTO_TRY(mto_after_launch(h, "cg_init_kernel"));
+  }
+  if (schwarz) {
+    MTO_TRY(apply_all<T>(h, 1, v.r, v.z, kGam, nullptr, none));
+    TimedScope ts(h, F_VECTOR);
+    copy_kernel<T><<<kVecBlocks, 256, 0, h->stream>>>(n, v.z, v.p);
+    MTO_TRY(mto_after_launch(h, "copy_kernel"));
+  }
+
+  const bool use_graph = h->use_graphs;
+  GraphEntry* ge = nullptr;
+  if (use_graph) {
+    GraphKey key{sizeof(T), (const void*)x, (const void*)r, schwarz, nrm, ref, tol2, chunk, h->timing.on,
+                 h->built_precision};
+    ge = find_graph(h, key);
+    if (!ge) {
+      ge = new_graph(h, key);
+      const int64_t l0 = h->launches;
+      MTO_TRY(mto_cuda_check(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal),
+                             "cudaStreamBeginCapture"));
+      h->timing.capture_list = &ge->events;
+      mto_status st = MTO_OK;
+      for (int l = 0; l < chunk && st == MTO_OK; ++l)
+        st = cg_iteration<T>(h, v, schwarz, nrm, ref, tol2, l, nc);
+      if (st == MTO_OK) {
+        advance_kernel<<<1, 32, 0, h->stream>>>(h->cg_base, chunk);
+        st = mto_after_launch(h, "advance_kernel");
+      }
+      h->timing.capture_list = nullptr;
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+      ge->launches_per_replay = h->launches - l0;
+      h->launches = l0;   // nothing ran during capture
+      if (st != MTO_OK) return st;
+      MTO_TRY(mto_cuda_check(h, e, "cudaStreamEndCapture"));
+      MTO_TRY(mto_cuda_check(h, cudaGraphInstantiate(&ge->exec, g, 0), "cudaGraphInstantiate"));
+      cudaGraphDestroy(g);
+    }
+  }
+  int k = 0, done = 0, err = 0;
+  while (k < max_it) {
+    if (use_graph) {
+      MTO_TRY(mto_cuda_check(h, cudaGraphLaunch(ge->exec, h->stream), "cudaGraphLaunch"));
+      h->launches += ge->launches_per_replay;
+      k += chunk;
+    } else {
+      for (int l = 0; l < chunk; ++l) MTO_TRY(cg_iteration<T>(h, v, schwarz, nrm, ref, tol2, l, nc));
+      advance_kernel<<<1, 32, 0, h->stream>>>(h->cg_base, chunk);
+      MTO_TRY(mto_after_launch(h, "advance_kernel"));
+      k += chunk;
+    }
+    MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->host_flags, h->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                                              h->stream), "copy"));
+    MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
+    if (use_graph) graph_timing_harvest(h, ge);
+    timing_harvest(h);
+    done = h->host_flags[0];
+    err = h->host_flags[1];
+    if (done) break;
+  }
+  *iters = done ? done : k;
+  if (err) return mto_fail(h, MTO_ENAN, "CG breakdown: non-finite or non-positive curvature");
+  return MTO_OK;
+}
+
+// FP64 residual r = f - K u (masked) and its squared norms: h->red[0..3] = (r, f l2; r, f Jacobi).
 mto_status true_residual(mto_handle h, const double* f, const double* u, int norm, double* rr, double* ff) {
-  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->q64, 0, sizeof(double) * h->ndof, h->stream), "memset"));
-  MTO_TRY(apply_all<double>(h, u, h->q64, nullptr, nullptr));
-  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->red, 0, 4 * sizeof(double), h->stream), "memset"));
-  TimedScope ts(h, F_VECTOR);
-  residual_kernel<<<grid_for(h->ndof, 256, 152 * 4), 256, 0, h->stream>>>(h->ndof, f, h->q64, h->invd64, h->r64, h->red);
-  MTO_TRY(mto_after_launch(h, "residual_kernel"));
-  MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->host_pinned, h->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy"));
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->s64, 0, sizeof(double) * h->ndof, h->stream), "memset"));
+  ConvTest none{};
+  MTO_TRY(apply_all<double>(h, 0, u, h->s64, -1, nullptr, none));
+  {
+    TimedScope ts(h, F_VECTOR);
+    residual_kernel<<<kVecBlocks, 256, 0, h->stream>>>(h->ndof, f, h->s64, h->invd64, h->r64, h->cg_part);
+    MTO_TRY(mto_after_launch(h, "residual_kernel"));
+    sum4_kernel<<<1, 256, 0, h->stream>>>(h->cg_part, kVecBlocks, h->red);
+    MTO_TRY(mto_after_launch(h, "sum4_kernel"));
+  }
+  MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->host_pinned, h->red, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                                            h->stream), "copy"));
   MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
   timing_harvest(h);
   *rr = h->host_pinned[norm ? 2 : 0];
@@ -405,79 +696,37 @@ mto_status true_residual(mto_handle h, const double* f, const double* u, int nor
   return MTO_OK;
 }
 
-// Preconditioned CG on (x, r, p, q) of type T: r is the current residual of x (free DOFs,
-// zero on supports), q is zero.  Stops when r^T r <= tol2 * (*ref) or after max_it iterations.
-template <typename T>
-mto_status run_pcg(mto_handle h, T* x, T* r, T* p, T* q, const T* invd, const double* ref, double tol2,
-                   int use_rz, int max_it, int check_every, int* iters) {
-  const int64_t n = h->ndof;
-  const int blk = 256, grd = grid_for(n, blk, 152 * 4);
-  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->scal, 0, sizeof(Scalars) * kSlots, h->stream), "memset"));
-  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->flags, 0, 2 * sizeof(int), h->stream), "memset"));
-  cg_init_kernel<T><<<grd, blk, 0, h->stream>>>(n, r, p, invd, h->scal);
-  MTO_TRY(mto_after_launch(h, "cg_init_kernel"));
-  int k = 0;
-  int done = 0, err = 0;
-  while (k < max_it) {
-    int chunk = check_every < max_it - k ? check_every : max_it - k;
-    for (int j = 0; j < chunk; ++j, ++k) {
-      MTO_TRY(apply_all<T>(h, p, q, &h->scal[k & 3].pq, h->flags));
-      TimedScope ts(h, F_VECTOR);
-      cg_update_kernel<T><<<grd, blk, 0, h->stream>>>(n, x, r, p, q, invd, h->scal, k, h->flags);
-      MTO_TRY(mto_after_launch(h, "cg_update_kernel"));
-      cg_direction_kernel<T><<<grd, blk, 0, h->stream>>>(n, r, p, invd, h->scal, k, ref, tol2, use_rz,
-                                                         h->flags, h->flags + 1);
-      MTO_TRY(mto_after_launch(h, "cg_direction_kernel"));
-    }
-    MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->host_pinned, h->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream), "copy"));
-    MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
-    timing_harvest(h);
-    const int* fl = reinterpret_cast<const int*>(h->host_pinned);
-    done = fl[0];
-    err = fl[1];
-    if (done) break;
-  }
-  *iters = done ? done : k;
-  if (err) return mto_fail(h, MTO_ENAN, "PCG breakdown: non-finite or non-positive curvature");
-  // leave q zero for the next use (the update kernel clears it; an early exit may not have)
-  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(q, 0, sizeof(T) * n, h->stream), "memset"));
-  return MTO_OK;
-}
-
-// squared l2 norm of the last true residual (host copy)
-double rr0_l2(mto_handle h) { return h->host_pinned[0]; }
-
 }  // namespace
 
-mto_status apply64(mto_handle h, const double* x, double* y, double* pq) {
-  return apply_all<double>(h, x, y, pq, nullptr);
-}
-
-mto_status apply32(mto_handle h, const float* x, float* y, double* pq) {
-  return apply_all<float>(h, x, y, pq, nullptr);
+mto_status apply64(mto_handle h, const double* x, double* y) {
+  ConvTest none{};
+  return apply_all<double>(h, 0, x, y, -1, nullptr, none);
 }
 
 mto_status dot64(mto_handle h, const double* a, const double* b, int64_t n, double* out_dev) {
-  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(out_dev, 0, sizeof(double), h->stream), "memset"));
-  dot_kernel<<<grid_for(n, 256, 152 * 4), 256, 0, h->stream>>>(n, a, b, out_dev);
-  return mto_after_launch(h, "dot_kernel");
+  dot_kernel<<<kVecBlocks, 256, 0, h->stream>>>(n, a, b, h->cg_part);
+  MTO_TRY(mto_after_launch(h, "dot_kernel"));
+  sum1_kernel<<<1, 256, 0, h->stream>>>(h->cg_part, kVecBlocks, out_dev);
+  return mto_after_launch(h, "sum1_kernel");
 }
 
 mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts* o, int32_t* iters_out,
                  double* relres_out) {
   const int64_t n = h->ndof;
   const int grd = grid_for(n, 256, 152 * 4);
+  const bool schwarz = o->precond == MTO_PREC_SCHWARZ;
+  if (schwarz && !h->schwarz_valid) MTO_TRY(build_schwarz(h));
   if (!o->warm_start) MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(u, 0, sizeof(double) * n, h->stream), "memset"));
   else {
     mask_kernel<<<grd, 256, 0, h->stream>>>(n, h->invd64, u);
     MTO_TRY(mto_after_launch(h, "mask_kernel"));
   }
-  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->q32, 0, sizeof(float) * n, h->stream), "memset"));
+  const int chunk = o->check_every < 2 ? 2 : (o->check_every + 1) / 2 * 2;
   int total = 0;
   double rr = 0.0, ff = 0.0;
-  const int max_outer = o->precision == MTO_MIXED ? (o->max_outer > 0 ? o->max_outer : 50) : 20;
-  mto_status st = MTO_ENOCONV;
+  const int max_outer = o->max_outer > 0 ? o->max_outer : 50;
   const int nrm = o->norm == MTO_NORM_JACOBI ? 1 : 0;
+  mto_status st = MTO_ENOCONV;
   for (int outer = 0; outer <= max_outer; ++outer) {
     MTO_TRY(true_residual(h, f, u, nrm, &rr, &ff));
     if (!std::isfinite(rr)) {
@@ -492,25 +741,29 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
     int it = 0;
     if (o->precision == MTO_FP64) {
       // h->red[1] (h->red[3]) holds f^T f (f^T D^-1 f): CG runs until the residual norm meets rtol
-      MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->q64, 0, sizeof(double) * n, h->stream), "memset"));
-      MTO_TRY(run_pcg<double>(h, u, h->r64, h->p64, h->q64, h->invd64, h->red + (nrm ? 3 : 1), o->rtol * o->rtol,
-                              nrm, o->max_iter - total, o->check_every, &it));
+      MTO_TRY(run_cg<double>(h, u, h->r64, schwarz, nrm, h->red + (nrm ? 3 : 1), o->rtol * o->rtol,
+                             o->max_iter - total, chunk, &it));
     } else {
-      const double scale = 1.0 / std::sqrt(rr0_l2(h));
-      TimedScope ts(h, F_VECTOR);
-      demote_kernel<<<grd, 256, 0, h->stream>>>(n, h->r64, scale, h->r32, h->x32, h->q32);
-      MTO_TRY(mto_after_launch(h, "demote_kernel"));
-      // the inner residual starts at (scaled) norm 1 in l2, and at r^T D^-1 r / ||r||^2 in the
-      // Jacobi norm: h->red[4] = the reference of the inner test
-      const double ref = nrm ? h->host_pinned[2] / rr0_l2(h) : 1.0;
-      h->host_pinned[32] = ref;
-      MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->red + 4, h->host_pinned + 32, sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy"));
-      double itol = o->inner_rtol > 0 ? o->inner_rtol : 1e-4;
-      MTO_TRY(run_pcg<float>(h, h->x32, h->r32, h->p32, h->q32, h->invd32, h->red + 4, itol * itol,
-                             nrm, o->max_iter - total, o->check_every, &it));
-      TimedScope ts2(h, F_VECTOR);
-      promote_kernel<<<grd, 256, 0, h->stream>>>(n, h->x32, 1.0 / scale, u);
-      MTO_TRY(mto_after_launch(h, "promote_kernel"));
+      const double rr2 = h->host_pinned[0];                 // l2 norm^2 of the FP64 residual
+      const double scale = 1.0 / std::sqrt(rr2);
+      {
+        TimedScope ts(h, F_VECTOR);
+        demote_kernel<<<grd, 256, 0, h->stream>>>(n, h->r64, scale, h->r32, h->x32);
+        MTO_TRY(mto_after_launch(h, "demote_kernel"));
+      }
+      // the inner residual starts at l2 norm 1, Jacobi norm^2 r^T D^-1 r / ||r||^2
+      h->host_pinned[32] = nrm ? h->host_pinned[2] / rr2 : 1.0;
+      MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->red + 4, h->host_pinned + 32, sizeof(double),
+                                                cudaMemcpyHostToDevice, h->stream), "copy"));
+      const double itol = o->inner_rtol > 0 ? o->inner_rtol : 1e-4;
+      const int cap = o->inner_max > 0 ? o->inner_max : 1 << 30;
+      const int budget = o->max_iter - total < cap ? o->max_iter - total : cap;
+      MTO_TRY(run_cg<float>(h, h->x32, h->r32, schwarz, nrm, h->red + 4, itol * itol, budget, chunk, &it));
+      {
+        TimedScope ts(h, F_VECTOR);
+        promote_kernel<<<grd, 256, 0, h->stream>>>(n, h->x32, 1.0 / scale, u);
+        MTO_TRY(mto_after_launch(h, "promote_kernel"));
+      }
     }
     total += it;
   }

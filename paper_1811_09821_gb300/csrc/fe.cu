@@ -252,7 +252,146 @@ void launch_diag(mto_handle h, const PClass& c, double* diag) {
                                                                       df ? nullptr : c.K64, c.K32, c.K32lo, diag);
 }
 
+// Element-block (additive Schwarz) preconditioner M^-1 = sum_e P_e^T B_e P_e with
+// B_e = (K_e + Delta_e)^-1 on the element's local DOFs.  Delta_e adds, at each unconstrained local
+// DOF, the rest of the assembled diagonal (the neighbours' share; a hanging DOF of a p-jump edge
+// takes the weighted diagonal sum_k w_k^2 D(g_k) of the global DOFs it interpolates), so
+// K_e + Delta_e is SPD and
+// holds the element's near-null modes exactly (those of solid/void elements, whose stiffness can
+// be 1e-10 of the element's largest, which point Jacobi cannot see).  Supported DOFs are
+// decoupled (unit row and column): B_e maps their zero residual to zero.  One warp per element:
+// FP64 in-place Gauss-Jordan inversion of the SPD block in shared memory, symmetrised, written in
+// the circulant-diagonal layout (FP64, or the split-precision pair).
+template <int PO>
+__global__ void schwarz_kernel(int n, int L, const int2* __restrict__ dpos, const int* __restrict__ gmap,
+                               const Constraint* __restrict__ cons,
+                               const double* __restrict__ K64, const float* __restrict__ Kh,
+                               const float* __restrict__ Kl, const double* __restrict__ diag,
+                               const double* __restrict__ invd, double* __restrict__ B64, float* __restrict__ Bh,
+                               float* __restrict__ Bl) {
+  constexpr int N1 = PO + 1, NN = N1 * N1, NE = 2 * NN, LDA = NE + 1, P = NE * (NE + 1) / 2;
+  extern __shared__ double sm[];
+  const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* A = sm + (size_t)warp * NE * LDA;
+  int* fx = reinterpret_cast<int*>(sm + (size_t)wpb * NE * LDA) + warp * NE;
+  for (int e = blockIdx.x * wpb + warp; e < n; e += gridDim.x * wpb) {
+    for (int idx = lane; idx < NE * NE; idx += 32) {
+      const int i = idx / NE, j = idx - (idx / NE) * NE;
+      const int a = i < j ? i : j, b = i < j ? j : i;
+      A[i * LDA + j] = k_entry(K64, Kh, Kl, L, e, dpos[packed_index(NE, a, b)].x);
+    }
+    __syncwarp();
+    for (int i = lane; i < NE; i += 32) {
+      const int g = gmap[(size_t)e * NN + (i >> 1)];
+      int fixed = 0;
+      if (g >= 0) {
+        const size_t gd = 2 * (size_t)g + (i & 1);
+        if (invd[gd] == 0.0) fixed = 1;
+        else A[i * LDA + i] += fmax(diag[gd] - A[i * LDA + i], 0.0);
+      } else {
+        // a hanging local DOF interpolates free global DOFs: it takes their weighted diagonal
+        const Constraint& c = cons[-g - 1];
+        double dh = 0.0;
+        for (int k = 0; k < c.cnt; ++k) {
+          const size_t gd = 2 * (size_t)c.node[k] + (i & 1);
+          if (invd[gd] != 0.0) dh += c.w[k] * c.w[k] * diag[gd];
+        }
+        A[i * LDA + i] += fmax(dh - A[i * LDA + i], 0.0);
+      }
+      fx[i] = fixed;
+    }
+    __syncwarp();
+    for (int i = lane; i < NE; i += 32)
+      for (int j = 0; j < NE; ++j)
+        if (fx[i] || fx[j]) A[i * LDA + j] = (i == j) ? 1.0 : 0.0;
+    __syncwarp();
+    // in-place Gauss-Jordan inversion (SPD: no pivoting)
+    for (int k = 0; k < NE; ++k) {
+      const double pinv = 1.0 / A[k * LDA + k];
+      __syncwarp();
+      for (int j = lane; j < NE; j += 32)
+        if (j != k) A[k * LDA + j] *= pinv;
+      __syncwarp();
+      for (int i = lane; i < NE; i += 32) {
+        if (i == k) continue;
+        const double f = A[i * LDA + k];
+        for (int j = 0; j < NE; ++j)
+          if (j != k) A[i * LDA + j] -= f * A[k * LDA + j];
+        A[i * LDA + k] = -f * pinv;
+      }
+      __syncwarp();
+      if (lane == 0) A[k * LDA + k] = pinv;
+      __syncwarp();
+    }
+    for (int c = lane; c < P; c += 32) {
+      int i = 0, rem = c;
+      while (rem >= NE - i) {
+        rem -= NE - i;
+        ++i;
+      }
+      const int j = i + rem;
+      const double v = 0.5 * (A[i * LDA + j] + A[j * LDA + i]);
+      const int2 ps = dpos[c];
+      const size_t o1 = (size_t)e * L + ps.x, o2 = (size_t)e * L + ps.y;
+      if (B64) {
+        B64[o1] = v;
+        if (ps.y >= 0) B64[o2] = v;
+      } else {
+        const float hi = (float)v, lo = (float)(v - (double)hi);
+        Bh[o1] = hi;
+        Bl[o1] = lo;
+        if (ps.y >= 0) {
+          Bh[o2] = hi;
+          Bl[o2] = lo;
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int PO>
+mto_status launch_schwarz(mto_handle h, PClass& c) {
+  constexpr int NE = 2 * (PO + 1) * (PO + 1);
+  const int wpb = NE <= 32 ? 8 : (NE <= 50 ? 4 : 2);
+  const size_t smem = (size_t)wpb * NE * (NE + 1) * sizeof(double) + (size_t)wpb * NE * sizeof(int);
+  if (smem > 48 * 1024)
+    MTO_TRY(mto_cuda_check(h, cudaFuncSetAttribute(schwarz_kernel<PO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem), "cudaFuncSetAttribute"));
+  const bool df = h->built_precision == MTO_MIXED;
+  const int blocks = grid_for(c.n, wpb, 152 * 8);
+  schwarz_kernel<PO><<<blocks, 32 * wpb, smem, h->stream>>>(c.n, c.L, c.dpos, c.gmap, h->cons_d,
+                                                            df ? nullptr : c.K64, c.K32,
+                                                            c.K32lo, h->diag64, h->invd64, df ? nullptr : c.B64,
+                                                            c.B32, c.B32lo);
+  return mto_after_launch(h, "schwarz_kernel");
+}
+
 }  // namespace
+
+mto_status build_schwarz(mto_handle h) {
+  TimedScope ts(h, F_PRECOND);
+  const bool df = h->built_precision == MTO_MIXED;
+  for (int p = 1; p <= MTO_P_MAX; ++p) {
+    PClass& c = h->pc[p];
+    if (c.n == 0) continue;
+    if (!df && !c.B64) MTO_TRY(mto_alloc(h, &c.B64, (size_t)c.L * c.n));
+    if (df && !c.B32) {
+      MTO_TRY(mto_alloc(h, &c.B32, (size_t)c.L * c.n));
+      MTO_TRY(mto_alloc(h, &c.B32lo, (size_t)c.L * c.n));
+    }
+    switch (p) {
+      case 1: MTO_TRY(launch_schwarz<1>(h, c)); break;
+      case 2: MTO_TRY(launch_schwarz<2>(h, c)); break;
+      case 3: MTO_TRY(launch_schwarz<3>(h, c)); break;
+      case 4: MTO_TRY(launch_schwarz<4>(h, c)); break;
+      case 5: MTO_TRY(launch_schwarz<5>(h, c)); break;
+      case 6: MTO_TRY(launch_schwarz<6>(h, c)); break;
+    }
+  }
+  h->schwarz_valid = true;
+  return MTO_OK;
+}
 
 mto_status element_matrix(mto_handle h, int64_t e, double* host_out) {
   const int p = h->p_host[e];
@@ -301,6 +440,7 @@ mto_status build_elements(mto_handle h, const double* rho, const mto_material* m
         k0_kernel<<<(n + 127) / 128, 128, 0, h->stream>>>(b.p, b.d, m->nu, h->hx, h->hy, b.K0T);
         MTO_TRY(mto_after_launch(h, "k0_kernel"));
       }
+    MTO_TRY(tc_tables(h));
     h->k0_nu = m->nu;
   }
   for (int p = 1; p <= MTO_P_MAX; ++p) {
@@ -314,6 +454,10 @@ mto_status build_elements(mto_handle h, const double* rho, const mto_material* m
   }
   for (auto& b : h->bc) {
     PClass& c = h->pc[b.p];
+    if (h->build_path == MTO_BUILD_TENSOR && b.S <= 64) {
+      MTO_TRY(tc_build_class(h, b, rho, m, precision));
+      continue;
+    }
     size_t smem = sizeof(double) * 32 * (b.S | 1);
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(build_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -329,7 +473,7 @@ mto_status build_elements(mto_handle h, const double* rho, const mto_material* m
 mto_status build_diagonal(mto_handle h, int precision) {
   (void)precision;
   TimedScope ts(h, F_BUILD);
-  double* diag = h->r64;  // scratch
+  double* diag = h->diag64;
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(diag, 0, sizeof(double) * h->ndof, h->stream), "memset"));
   for (int p = 1; p <= MTO_P_MAX; ++p) {
     const PClass& c = h->pc[p];

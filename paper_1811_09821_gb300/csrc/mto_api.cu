@@ -18,7 +18,19 @@ mto_status mto_fail(mto_handle h, mto_status s, const std::string& msg) {
 
 mto_status mto_cuda_check(mto_handle h, cudaError_t e, const char* what) {
   if (e == cudaSuccess) return MTO_OK;
+  cudaGetLastError();   // do not leave a recoverable error behind for the next launch check
   return mto_fail(h, MTO_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+StreamJoin::StreamJoin(mto_handle h_) : h(h_) {
+  cudaSetDevice(h->device);
+  cudaEventRecord(h->ev_in, h->user_stream);
+  cudaStreamWaitEvent(h->stream, h->ev_in, 0);
+}
+
+StreamJoin::~StreamJoin() {
+  cudaEventRecord(h->ev_out, h->stream);
+  cudaStreamWaitEvent(h->user_stream, h->ev_out, 0);
 }
 
 mto_status mto_after_launch(mto_handle h, const char* what) {
@@ -41,19 +53,70 @@ cudaEvent_t take_event(mto_handle h) {
 
 TimedScope::TimedScope(mto_handle h_, int fam_) : h(h_), fam(fam_), launches0(h_->launches) {
   if (!h->timing.on) return;
-  if (h->timing.pending.size() > 4096) {
+  if (!h->timing.capture_list && h->timing.pending.size() > 4096) {
     cudaStreamSynchronize(h->stream);
     timing_harvest(h);
   }
   a = take_event(h);
-  cudaEventRecord(a, h->stream);
+  if (h->timing.capture_list) cudaEventRecordWithFlags(a, h->stream, cudaEventRecordExternal);
+  else cudaEventRecord(a, h->stream);
 }
 
 TimedScope::~TimedScope() {
   if (!a) return;
   cudaEvent_t b = take_event(h);
-  cudaEventRecord(b, h->stream);
-  h->timing.pending.push_back({fam, (int)(h->launches - launches0), a, b});
+  if (h->timing.capture_list) cudaEventRecordWithFlags(b, h->stream, cudaEventRecordExternal);
+  else cudaEventRecord(b, h->stream);
+  Timing::Pending pd{fam, (int)(h->launches - launches0), a, b};
+  if (h->timing.capture_list) h->timing.capture_list->push_back(pd);
+  else h->timing.pending.push_back(pd);
+}
+
+void graph_timing_harvest(mto_handle h, GraphEntry* g) {
+  for (auto& p : g->events) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      h->timing.ms[p.fam] += ms;
+      h->timing.launches[p.fam] += p.launches;
+    } else {
+      cudaGetLastError();
+    }
+  }
+}
+
+GraphEntry* find_graph(mto_handle h, const GraphKey& k) {
+  for (auto* g : h->graphs)
+    if (g->key == k) return g;
+  return nullptr;
+}
+
+GraphEntry* new_graph(mto_handle h, const GraphKey& k) {
+  if (h->graphs.size() >= 8) {
+    GraphEntry* old = h->graphs.front();
+    if (old->exec) cudaGraphExecDestroy(old->exec);
+    for (auto& p : old->events) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    delete old;
+    h->graphs.erase(h->graphs.begin());
+  }
+  GraphEntry* g = new GraphEntry();
+  g->key = k;
+  h->graphs.push_back(g);
+  return g;
+}
+
+void clear_graphs(mto_handle h) {
+  for (auto* g : h->graphs) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    for (auto& p : g->events) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    delete g;
+  }
+  h->graphs.clear();
 }
 
 void timing_harvest(mto_handle h) {
@@ -62,6 +125,8 @@ void timing_harvest(mto_handle h) {
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       h->timing.ms[p.fam] += ms;
       h->timing.launches[p.fam] += p.launches;
+    } else {
+      cudaGetLastError();
     }
     h->timing.pool.push_back(p.a);
     h->timing.pool.push_back(p.b);
@@ -80,6 +145,7 @@ void free_dev(mto_handle h, T*& p) {
 void release_mesh(mto_handle h) {
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
+  clear_graphs(h);
   free_dev(h, h->p_d);
   free_dev(h, h->d_d);
   free_dev(h, h->design_off_d);
@@ -88,9 +154,13 @@ void release_mesh(mto_handle h) {
     free_dev(h, c.elem);
     free_dev(h, c.gmap);
     free_dev(h, c.dpos);
+    free_dev(h, c.posc);
     free_dev(h, c.K64);
     free_dev(h, c.K32);
     free_dev(h, c.K32lo);
+    free_dev(h, c.B64);
+    free_dev(h, c.B32);
+    free_dev(h, c.B32lo);
     c = PClass();
   }
   for (auto* v : {&h->bc, &h->bc_qr}) {
@@ -100,6 +170,8 @@ void release_mesh(mto_handle h) {
       free_dev(h, b.K0T);
       free_dev(h, b.stab);
       free_dev(h, b.stabf);
+      free_dev(h, b.tcB);
+      free_dev(h, b.tcTau);
     }
     v->clear();
   }
@@ -108,15 +180,10 @@ void release_mesh(mto_handle h) {
     q = QRTab();
   }
   free_dev(h, h->slot_d);
-  free_dev(h, h->invd64);
-  free_dev(h, h->invd32);
-  free_dev(h, h->r64);
-  free_dev(h, h->p64);
-  free_dev(h, h->q64);
-  free_dev(h, h->x32);
-  free_dev(h, h->r32);
-  free_dev(h, h->p32);
-  free_dev(h, h->q32);
+  for (double** v : {&h->diag64, &h->invd64, &h->r64, &h->p64, &h->s64, &h->u64, &h->w64, &h->cg_part})
+    free_dev(h, *v);
+  for (float** v : {&h->invd32, &h->x32, &h->r32, &h->p32, &h->s32, &h->u32, &h->w32}) free_dev(h, *v);
+  h->schwarz_valid = false;
   free_dev(h, h->ibuf);
   free_dev(h, h->dbuf);
   free_dev(h, h->edge_buf);
@@ -209,15 +276,22 @@ mto_status mto_create(mto_handle* out, int device, void* stream) {
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return MTO_ECUDA;
   mto_handle h = new mto_handle_s();
   h->device = device;
-  h->stream = (cudaStream_t)stream;
+  h->user_stream = (cudaStream_t)stream;
   cudaSetDevice(device);
-  if (mto_alloc(h, &h->scal, kSlots) || mto_alloc(h, &h->red, 64) || mto_alloc(h, &h->flags, 64) ||
-      mto_alloc(h, &h->sel, 256)) {
+  if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    delete h;
+    return MTO_ECUDA;
+  }
+  if (mto_alloc(h, &h->red, 64) || mto_alloc(h, &h->flags, 64) || mto_alloc(h, &h->sel, 256) ||
+      mto_alloc(h, &h->cg_res, 64) || mto_alloc(h, &h->cg_cnt, 64) || mto_alloc(h, &h->cg_base, 4)) {
     delete h;
     return MTO_ENOMEM;
   }
   h->base_bytes = h->bytes;
-  if (cudaMallocHost((void**)&h->host_pinned, 64 * sizeof(double)) != cudaSuccess) {
+  if (cudaMallocHost((void**)&h->host_pinned, 64 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void**)&h->host_flags, 16 * sizeof(int)) != cudaSuccess) {
     delete h;
     return MTO_ENOMEM;
   }
@@ -230,7 +304,14 @@ mto_status mto_destroy(mto_handle h) {
   release_mesh(h);
   timing_harvest(h);
   for (cudaEvent_t e : h->timing.pool) cudaEventDestroy(e);
-  cudaFree(h->scal);
+  cudaFree(h->cg_res);
+  cudaFree(h->cg_cnt);
+  cudaFree(h->cg_base);
+  cudaFreeHost(h->host_flags);
+  cudaStreamSynchronize(h->stream);
+  cudaStreamDestroy(h->stream);
+  cudaEventDestroy(h->ev_in);
+  cudaEventDestroy(h->ev_out);
   cudaFree(h->red);
   cudaFree(h->flags);
   cudaFree(h->sel);
@@ -243,12 +324,14 @@ const char* mto_last_error(mto_handle h) { return h ? h->err.c_str() : "null han
 
 mto_status mto_set_stream(mto_handle h, void* stream) {
   if (!h) return MTO_EINVAL;
-  h->stream = (cudaStream_t)stream;
+  h->user_stream = (cudaStream_t)stream;
   return MTO_OK;
 }
 
 mto_status mto_setup(mto_handle h, int32_t nelx, int32_t nely, double hx, double hy,
                      const int32_t* p_map, const int32_t* d_map, int64_t* ndof, int64_t* design_len) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
   if (!h) return MTO_EINVAL;
   h->err.clear();
   if (nelx < 1 || nely < 1 || !(hx > 0) || !(hy > 0) || !p_map || !d_map)
@@ -362,6 +445,13 @@ mto_status mto_setup(mto_handle h, int32_t nelx, int32_t nely, double hx, double
     }
     MTO_TRY(mto_alloc(h, &c.elem, c.n));
     MTO_TRY(mto_alloc(h, &c.gmap, gmap.size()));
+    std::vector<int> posc(c.L, 0);
+    for (int cc = 0; cc < c.P; ++cc) {
+      posc[dpos[cc].x] = cc;
+      if (dpos[cc].y >= 0) posc[dpos[cc].y] = cc;
+    }
+    MTO_TRY(mto_alloc(h, &c.posc, posc.size()));
+    MTO_TRY(mto_cuda_check(h, cudaMemcpy(c.posc, posc.data(), posc.size() * sizeof(int), cudaMemcpyHostToDevice), "upload"));
     MTO_TRY(mto_alloc(h, &c.dpos, dpos.size()));
     MTO_TRY(mto_cuda_check(h, cudaMemcpy(c.dpos, dpos.data(), dpos.size() * sizeof(int2), cudaMemcpyHostToDevice), "upload"));
     MTO_TRY(mto_cuda_check(h, cudaMemcpy(c.elem, elems.data(), c.n * sizeof(int), cudaMemcpyHostToDevice), "upload"));
@@ -414,15 +504,17 @@ mto_status mto_setup(mto_handle h, int32_t nelx, int32_t nely, double hx, double
 
   // solver workspace
   int64_t n = h->ndof;
-  MTO_TRY(mto_alloc(h, &h->invd64, n));
-  MTO_TRY(mto_alloc(h, &h->invd32, n));
-  MTO_TRY(mto_alloc(h, &h->r64, n));
-  MTO_TRY(mto_alloc(h, &h->p64, n));
-  MTO_TRY(mto_alloc(h, &h->q64, n));
-  MTO_TRY(mto_alloc(h, &h->x32, n));
-  MTO_TRY(mto_alloc(h, &h->r32, n));
-  MTO_TRY(mto_alloc(h, &h->p32, n));
-  MTO_TRY(mto_alloc(h, &h->q32, n));
+  for (double** v : {&h->diag64, &h->invd64, &h->r64, &h->p64, &h->s64, &h->u64, &h->w64}) MTO_TRY(mto_alloc(h, v, n));
+  for (float** v : {&h->invd32, &h->x32, &h->r32, &h->p32, &h->s32, &h->u32, &h->w32}) MTO_TRY(mto_alloc(h, v, n));
+  // CG block partials: per launch the largest grid of a vector kernel (4 partials per block in the
+  // residual kernel) or of one class's operator launch
+  int64_t maxgrid = 152 * 4 * 4;
+  for (int p = 1; p <= MTO_P_MAX; ++p)
+    if (h->pc[p].n && ebe_blocks(p, h->pc[p].n) > maxgrid) maxgrid = ebe_blocks(p, h->pc[p].n);
+  h->cg_class_stride = maxgrid;
+  h->cg_stride = 8 * maxgrid;
+  MTO_TRY(mto_alloc(h, &h->cg_part, (size_t)8 * h->cg_stride));
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->cg_cnt, 0, 64 * sizeof(unsigned), h->stream), "memset"));
   MTO_TRY(mto_alloc(h, &h->ibuf, 4 * nel + 64));
   MTO_TRY(mto_alloc(h, &h->dbuf, 2 * nel + 64));
   h->n_edges = (int64_t)(nely + 1) * nelx + (int64_t)nely * (nelx + 1);
@@ -438,6 +530,8 @@ mto_status mto_setup(mto_handle h, int32_t nelx, int32_t nely, double hx, double
 }
 
 mto_status mto_set_supports(mto_handle h, const int64_t* fixed, int64_t n) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
   if (!h || !h->have_setup) return mto_fail(h, MTO_EINVAL, "mto_set_supports: call mto_setup first");
   if (n < 0 || (n > 0 && !fixed)) return mto_fail(h, MTO_EINVAL, "mto_set_supports: bad arguments");
   for (int64_t k = 0; k < n; ++k)
@@ -454,6 +548,7 @@ mto_status mto_set_supports(mto_handle h, const int64_t* fixed, int64_t n) {
                                          cudaMemcpyHostToDevice), "upload"));
   }
   h->have_supports = true;
+  h->schwarz_valid = false;
   if (h->built_precision >= 0) MTO_TRY(build_diagonal(h, h->built_precision));
   return MTO_OK;
 }
@@ -515,18 +610,23 @@ mto_status mto_element_nodes(mto_handle h, int64_t e, int64_t* nodes, double* we
 }
 
 mto_status mto_build_elements(mto_handle h, const double* rho, const mto_material* mat, int32_t precision) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
   if (!h || !h->have_setup || !rho || !mat) return mto_fail(h, MTO_EINVAL, "mto_build_elements: bad arguments");
   if (precision != MTO_FP64 && precision != MTO_MIXED) return mto_fail(h, MTO_EINVAL, "mto_build_elements: bad precision");
   if (!(mat->E0 > 0) || !(mat->Emin >= 0) || !(mat->nu > -1 && mat->nu < 0.5) || !(mat->q >= 1))
     return mto_fail(h, MTO_EINVAL, "mto_build_elements: bad material");
   cudaSetDevice(h->device);
   h->built_precision = precision;
+  h->schwarz_valid = false;
   MTO_TRY(build_elements(h, rho, mat, precision));
   if (h->have_supports) MTO_TRY(build_diagonal(h, precision));
   return MTO_OK;
 }
 
 mto_status mto_element_matrix(mto_handle h, int64_t e, double* packed) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
   if (!h || !h->have_setup || !packed || e < 0 || e >= h->nel)
     return mto_fail(h, MTO_EINVAL, "mto_element_matrix: bad arguments");
   if (h->built_precision < 0) return mto_fail(h, MTO_EINVAL, "mto_element_matrix: call mto_build_elements first");
@@ -536,27 +636,34 @@ mto_status mto_element_matrix(mto_handle h, int64_t e, double* packed) {
 
 mto_status mto_solve(mto_handle h, const double* f, double* u, const mto_solve_opts* opts, int32_t* iters,
                      double* relres) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
   if (!h || !h->have_setup || !f || !u || !opts) return mto_fail(h, MTO_EINVAL, "mto_solve: bad arguments");
   if (!h->have_supports) return mto_fail(h, MTO_EINVAL, "mto_solve: call mto_set_supports first");
   if (h->built_precision < 0) return mto_fail(h, MTO_EINVAL, "mto_solve: call mto_build_elements first");
   if (opts->precision == MTO_MIXED && h->built_precision != MTO_MIXED)
     return mto_fail(h, MTO_EINVAL, "mto_solve: the mixed solve needs the split-precision (MTO_MIXED) build");
-  if (!(opts->rtol > 0) || opts->max_iter < 1 || opts->check_every < 1)
+  if (!(opts->rtol > 0) || opts->max_iter < 1 || opts->check_every < 1 ||
+      (opts->precond != MTO_PREC_JACOBI && opts->precond != MTO_PREC_SCHWARZ))
     return mto_fail(h, MTO_EINVAL, "mto_solve: bad options");
   cudaSetDevice(h->device);
   return solve(h, f, u, opts, iters, relres);
 }
 
 mto_status mto_apply(mto_handle h, const double* x, double* y) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
   if (!h || !h->have_setup || !x || !y) return mto_fail(h, MTO_EINVAL, "mto_apply: bad arguments");
   if (h->built_precision < 0) return mto_fail(h, MTO_EINVAL, "mto_apply: call mto_build_elements first");
   cudaSetDevice(h->device);
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(y, 0, h->ndof * sizeof(double), h->stream), "mto_apply"));
-  return apply64(h, x, y, nullptr);
+  return apply64(h, x, y);
 }
 
 mto_status mto_sensitivity(mto_handle h, const double* u, const double* f, const double* rho,
                            const mto_material* mat, int32_t precision, double* dc, double* C) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
   if (!h || !h->have_setup || !u || !f || !rho || !mat || !dc)
     return mto_fail(h, MTO_EINVAL, "mto_sensitivity: bad arguments");
   if (precision != MTO_FP64 && precision != MTO_MIXED) return mto_fail(h, MTO_EINVAL, "mto_sensitivity: bad precision");
@@ -567,6 +674,8 @@ mto_status mto_sensitivity(mto_handle h, const double* u, const double* f, const
 mto_status mto_indicator(mto_handle h, const double* u, const double* rho, const mto_material* mat,
                          const mto_indicator_opts* opts, double* gamma_a, double* gamma_d, double* eps_qr,
                          int32_t* p_new, int32_t* d_new, int8_t* theta) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
   if (!h || !h->have_setup || !u || !rho || !mat || !opts)
     return mto_fail(h, MTO_EINVAL, "mto_indicator: bad arguments");
   if (h->built_precision < 0) return mto_fail(h, MTO_EINVAL, "mto_indicator: call mto_build_elements first");
@@ -579,6 +688,8 @@ mto_status mto_indicator(mto_handle h, const double* u, const double* rho, const
 
 mto_status mto_map_update(mto_handle h, const double* gamma_a, const double* gamma_d, const double* eps_qr,
                           const mto_indicator_opts* opts, int32_t* p_new, int32_t* d_new, int8_t* theta) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
   if (!h || !h->have_setup || !gamma_a || !gamma_d || !eps_qr || !opts || !p_new || !d_new || !theta)
     return mto_fail(h, MTO_EINVAL, "mto_map_update: bad arguments");
   if (opts->p_max < 1 || opts->p_max > MTO_P_MAX || opts->d_max < 1 || opts->d_max > MTO_D_MAX * MTO_D_MAX)
@@ -589,6 +700,8 @@ mto_status mto_map_update(mto_handle h, const double* gamma_a, const double* gam
 
 mto_status mto_oc_update(mto_handle h, const double* rho, const double* dc, double volfrac, double move,
                          double eta, double* rho_new, double* lambda) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
   if (!h || !h->have_setup || !rho || !dc || !rho_new) return mto_fail(h, MTO_EINVAL, "mto_oc_update: bad arguments");
   if (!(volfrac > 0 && volfrac <= 1) || !(move > 0) || !(eta > 0))
     return mto_fail(h, MTO_EINVAL, "mto_oc_update: bad parameters");
@@ -617,6 +730,13 @@ mto_status mto_timing_read(mto_handle h, int32_t family, int64_t* launches, doub
   timing_harvest(h);
   *launches = h->timing.launches[family];
   *total_ms = h->timing.ms[family];
+  return MTO_OK;
+}
+
+mto_status mto_set_build_path(mto_handle h, int32_t path) {
+  if (!h || (path != MTO_BUILD_TENSOR && path != MTO_BUILD_SIMT))
+    return mto_fail(h, MTO_EINVAL, "mto_set_build_path: bad path");
+  h->build_path = path;
   return MTO_OK;
 }
 

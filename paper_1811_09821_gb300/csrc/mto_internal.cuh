@@ -47,9 +47,13 @@ struct PClass {
   int* elem = nullptr;   // [n] element ids, ascending
   int* gmap = nullptr;   // [n][(p+1)^2] global node id, or -(1 + constraint index)
   int2* dpos = nullptr;  // [P] row positions of packed entry c (second one or -1)
+  int* posc = nullptr;   // [L] packed entry stored at each row position
   double* K64 = nullptr;   // FP64 path
   float* K32 = nullptr;    // split-precision pair (mixed path): hi = fl32(K_e) ...
   float* K32lo = nullptr;  // ... and lo = fl32(K_e - hi), same layout
+  double* B64 = nullptr;   // element-block preconditioner (K_e + Delta_e)^-1, same layouts
+  float* B32 = nullptr;
+  float* B32lo = nullptr;
 };
 
 // Elements of one (p, d) pair: the build and sensitivity granularity.
@@ -61,6 +65,8 @@ struct BClass {
   double* K0T = nullptr; // [P][S] subcell stiffness tables, transposed (entry c, subcell s)
   double* stab = nullptr; // sensitivity quadrature tables (FP64 and FP32 copies)
   float* stabf = nullptr;
+  unsigned short* tcB = nullptr;  // tensor-core build: BF16 slices of K0 per N tile
+  float* tcTau = nullptr;         // and the power-of-two column scales
 };
 
 // QR-indicator tables for order p -> p + 1.
@@ -71,26 +77,52 @@ struct QRTab {
 
 // Kernel families timed with CUDA events when timing is enabled (see mto_timing_enable).
 enum Family { F_APPLY32 = 0, F_APPLY64 = 1, F_BUILD = 2, F_SENS = 3, F_INDICATOR = 4, F_VECTOR = 5,
-              F_APPLYDF64 = 6, F_COUNT = 7 };
+              F_APPLYDF64 = 6, F_PRECOND = 7, F_COUNT = 8 };
 
 struct Timing {
   bool on = false;
   struct Pending { int fam; int launches; cudaEvent_t a, b; };
   std::vector<cudaEvent_t> pool;
   std::vector<Pending> pending;
+  std::vector<Pending>* capture_list = nullptr;   // event pairs of a graph being captured
   int64_t launches[F_COUNT] = {0};
   double ms[F_COUNT] = {0};
 };
 
-struct Scalars {         // one PCG iteration's reductions
-  double pq, rz, rr, pad;
+// A captured chunk of CG iterations, replayed until convergence.
+struct GraphKey {
+  size_t tsize;
+  const void* x;
+  const void* r;
+  bool schwarz;
+  int nrm;
+  const double* ref;
+  double tol2;
+  int chunk;
+  bool timing;
+  int prec;
+  bool operator==(const GraphKey& o) const {
+    return tsize == o.tsize && x == o.x && r == o.r && schwarz == o.schwarz && nrm == o.nrm && ref == o.ref &&
+           tol2 == o.tol2 && chunk == o.chunk && timing == o.timing && prec == o.prec;
+  }
 };
+
+struct GraphEntry {
+  GraphKey key;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<Timing::Pending> events;   // event pairs recorded on every replay
+  int64_t launches_per_replay = 0;
+  int64_t captured_launches = 0;
+};
+
 
 }  // namespace mto
 
 struct mto_handle_s {
   int device = 0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;        // the handle's own non-blocking stream (all device work)
+  cudaStream_t user_stream = nullptr;   // the caller's stream, ordered with `stream` by events
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   std::string err;
   int64_t launches = 0;
   int64_t bytes = 0;
@@ -125,13 +157,26 @@ struct mto_handle_s {
   int64_t base_bytes = 0;                      // device bytes held independently of the mesh
 
   // solver workspace
+  double* diag64 = nullptr;  // assembled diagonal
   double* invd64 = nullptr;  // inverse diagonal, 0 on supported DOFs
   float* invd32 = nullptr;
-  double *r64 = nullptr, *p64 = nullptr, *q64 = nullptr;
-  float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
-  mto::Scalars* scal = nullptr;                // [kSlots]
+  double *r64 = nullptr, *p64 = nullptr, *s64 = nullptr, *u64 = nullptr, *w64 = nullptr;
+  float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *s32 = nullptr, *u32 = nullptr, *w32 = nullptr;
+  // CG reductions: 8 slots (r^T z, p^T K p, r^T r, r^T D^-1 r, each by iteration parity) of up to
+  // 8 launches; launch j of slot k stores block partials at cg_part + k*cg_stride + j*cg_class_stride,
+  // its result at cg_res[8k + j], and counts finished blocks in cg_cnt[8k + j] (zero between launches)
+  double* cg_part = nullptr;
+  int64_t cg_class_stride = 0, cg_stride = 0;
+  double* cg_res = nullptr;                    // [64]
+  unsigned* cg_cnt = nullptr;                  // [64]
+  int* cg_base = nullptr;                      // first iteration of the running chunk
+  bool schwarz_valid = false;
+  int build_path = MTO_BUILD_SIMT;
+  bool use_graphs = true;
+  std::vector<mto::GraphEntry*> graphs;
   double* red = nullptr;                       // misc reduction scratch [64]
-  int* flags = nullptr;                        // [0] done iteration + 1, [1] error code, [2..] misc
+  int* flags = nullptr;                        // [0] iterations when done, [1] error code, [2..] misc
+  int* host_flags = nullptr;                   // pinned host mirror of flags[0..1]
   double* host_pinned = nullptr;               // pinned host mirror for small read-backs [64]
   unsigned long long* sel = nullptr;           // selection / small integer scratch [256]
   void* basis_tab = nullptr;                   // GLL / Gauss tables for the indicator kernels
@@ -154,6 +199,13 @@ mto_status mto_fail(mto_handle h, mto_status s, const std::string& msg);
 mto_status mto_cuda_check(mto_handle h, cudaError_t e, const char* what);
 mto_status mto_after_launch(mto_handle h, const char* what);
 
+// Orders an entry point's work after the caller's stream and the caller's stream after it.
+struct StreamJoin {
+  mto_handle h;
+  explicit StreamJoin(mto_handle h_);
+  ~StreamJoin();
+};
+
 // Event bracket around the launches of one kernel family on h->stream (no-op when timing is off).
 struct TimedScope {
   mto_handle h;
@@ -164,6 +216,10 @@ struct TimedScope {
   ~TimedScope();
 };
 void timing_harvest(mto_handle h);   // call after the stream has been synchronised
+void graph_timing_harvest(mto_handle h, mto::GraphEntry* g);
+mto::GraphEntry* find_graph(mto_handle h, const mto::GraphKey& k);
+mto::GraphEntry* new_graph(mto_handle h, const mto::GraphKey& k);
+void clear_graphs(mto_handle h);
 
 template <typename T>
 mto_status mto_alloc(mto_handle h, T** ptr, size_t count) {
@@ -314,9 +370,13 @@ mto_status build_sens_tables(mto_handle h);
 mto_status build_elements(mto_handle h, const double* rho, const mto_material* m, int precision);
 mto_status build_diagonal(mto_handle h, int precision);
 mto_status element_matrix(mto_handle h, int64_t e, double* host_out);
+mto_status build_schwarz(mto_handle h);                                 // element-block preconditioner
+// tc.cu
+mto_status tc_tables(mto_handle h);
+mto_status tc_build_class(mto_handle h, const BClass& b, const double* rho, const mto_material* m, int precision);
+int ebe_blocks(int p, int n);                                           // grid of one operator launch
 // apply.cu
-mto_status apply64(mto_handle h, const double* x, double* y, double* pq);        // y += K x
-mto_status apply32(mto_handle h, const float* x, float* y, double* pq);
+mto_status apply64(mto_handle h, const double* x, double* y);        // y += K x (FP64 vectors)
 mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts* o, int32_t* iters,
                  double* relres);
 // sens.cu

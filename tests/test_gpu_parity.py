@@ -112,6 +112,26 @@ def test_operator_matches_assembled_oracle(mto, name, build):
     h.close()
 
 
+@pytest.mark.parametrize("name", CASES)
+def test_tensor_core_build_matches_simt(mto, name):
+    """The sliced tcgen05 build (d <= 8) and the FP64 CUDA-core build give the same element
+    matrices to ~1e-14 of each element's largest entry, in both storage precisions."""
+    o = oracle_results(name)
+    pr, m = o["pr"], o["mesh"]
+    h, fixed, f, mat, rho = gpu_setup(mto, pr)
+    rng = np.random.default_rng(5)
+    sample = rng.choice(m.nel, min(m.nel, 48), replace=False)
+    for build in (mto.MTO_FP64, mto.MTO_MIXED):
+        got = {}
+        for path in (mto.BUILD_TENSOR, mto.BUILD_SIMT):
+            h.set_build_path(path)
+            h.build_elements(rho, mat, build)
+            got[path] = [h.element_matrix(int(e), int(m.p[e])) for e in sample]
+        for a, b in zip(got[mto.BUILD_TENSOR], got[mto.BUILD_SIMT]):
+            assert np.abs(a - b).max() <= 2e-14 * np.abs(b).max()
+    h.close()
+
+
 # ----------------------------------------------------------------------------- step (b) + (c)
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("name", CASES)
