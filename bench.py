@@ -42,9 +42,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--rtol", type=float, default=1e-8)
-    ap.add_argument("--precond", default="schwarz", choices=["schwarz", "jacobi"])
-    ap.add_argument("--solve", default="mixed", choices=["mixed", "split64"],
-                    help="mixed: FP32-vector inner CG in FP64 refinement; split64: one CG with FP64 vectors")
+    ap.add_argument("--precond", default="mg", choices=["schwarz", "jacobi", "mg"])
+    ap.add_argument("--mg-degree", type=int, default=4, help="Chebyshev degree of the multigrid smoothing")
+    ap.add_argument("--solve", default="mixed", choices=["mixed", "mixed32"],
+                    help="mixed: FP64 refinement around inner PCG on the split-precision operator with FP64 "
+                         "vectors; mixed32: the same with FP32 inner vectors")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
@@ -195,17 +197,20 @@ def run_gpu(args, rank, world, local_rank):
     rho = torch.tensor(pr.rho, dtype=torch.float64, device=dev)
     u = torch.zeros(ndof, dtype=torch.float64, device=dev)
     dc = torch.zeros(dlen, dtype=torch.float64, device=dev)
+    rho_new = torch.zeros(dlen, dtype=torch.float64, device=dev)
+    vol = float(np.mean(pr.rho))
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
 
-    pc = mto.PREC_SCHWARZ if args.precond == "schwarz" else mto.PREC_JACOBI
+    pc = {"schwarz": mto.PREC_SCHWARZ, "jacobi": mto.PREC_JACOBI, "mg": mto.PREC_MG}[args.precond]
 
     def step(prec):
         h.build_elements(rho, mat, prec)
-        sprec = prec if (prec == mto.MTO_FP64 or args.solve == "mixed") else mto.MTO_FP64
+        sprec = mto.MTO_FP64 if prec == mto.MTO_FP64 else (mto.MTO_MIXED if args.solve == "mixed" else mto.MTO_MIXED32)
         it, rr = h.solve(f, u, precision=sprec, rtol=args.rtol, max_iter=400000, check_every=32, precond=pc,
-                         inner_max=4000)
+                         mg_degree=args.mg_degree)
         h.sensitivity(u, f, rho, mat, dc, precision=prec, want_C=False)
         h.indicator(u, rho, mat)
+        h.oc_update(rho, dc, vol, rho_new, want_lambda=False)
         return it, rr
 
     def timed(prec, steps, warmup):
@@ -272,12 +277,12 @@ def run_gpu(args, rank, world, local_rank):
 
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    fam = "apply32" if args.solve == "mixed" else "applydf64"
+    fam = "apply32" if args.solve == "mixed32" else "applydf64"
     n_apply, apply_ms = mixed["families"][fam]
     # algorithmic bytes of one operator launch: the split-precision pair of the element matrix in
     # its circulant-diagonal row ((n_e/2 + 1) n_e entries, 2 x 4 bytes; 544 for Q3) and the node map
     # per element, one read of x and one write of y per DOF (4 bytes FP32, 8 bytes FP64 vectors)
-    vb = 4 if args.solve == "mixed" else 8
+    vb = 4 if args.solve == "mixed32" else 8
     nn = [(int(p) + 1) ** 2 for p in pr.p]
     kbytes = sum(8 * ((2 * n) // 2 + 1) * (2 * n) + 4 * n for n in nn)
     bytes_per_launch = kbytes + 2 * vb * ndof
@@ -296,7 +301,8 @@ def run_gpu(args, rank, world, local_rank):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 inner PCG + f64 refinement/dots/compliance; f64 build, sensitivity in f32 after f64 rigid removal",
+        "dtype": ("f32x2 split operator (f32 pipes) in inner PCG, f64 vectors/refinement/dots/compliance"
+                  if args.solve == "mixed" else "f32 inner PCG + f64 refinement/dots/compliance"),
         "data": "synthetic",
         "config": {"workload": args.workload, "nelx": pr.nelx, "nely": pr.nely, "p": int(pr.p[0]),
                    "d": int(pr.d[0]), "free_dofs": nfree, "design_values": dlen, "rtol": args.rtol,

@@ -56,7 +56,7 @@ typedef enum {
   MTO_ETIMEOUT = 6   /* a bounded device wait expired */
 } mto_status;
 
-typedef enum { MTO_FP64 = 0, MTO_MIXED = 1 } mto_precision;
+typedef enum { MTO_FP64 = 0, MTO_MIXED = 1, MTO_MIXED32 = 2 } mto_precision;
 
 /* Material of Eq. 3 and Sec. 4.1 (E0 = 1, nu = 0.3, q = 3, Emin = 1e-9 E0 in the paper).
  * Plane stress. */
@@ -65,24 +65,34 @@ typedef struct {
 } mto_material;
 
 /* Solver options.
- *  precision   MTO_FP64: one Jacobi-PCG with FP64 vectors on the built operator.
- *              MTO_MIXED (needs the MTO_MIXED build): inner Jacobi-PCG with FP32 vectors inside an
- *              FP64 iterative refinement whose residual r = f - K u uses FP64 vectors; the operator
- *              is the split-precision pair on the FP32 pipes in both.  Dot products are
- *              accumulated in FP64 in every mode.
+ *  precision   MTO_FP64: one PCG with FP64 vectors on the FP64 element matrices (FP64 pipes).
+ *              MTO_MIXED (needs the MTO_MIXED build): FP64 iterative refinement.  Each step forms
+ *              the residual r = f - K u with the FP64 matrices and FP64 vectors, then solves
+ *              K d = r by an inner PCG that applies the split-precision pair on the FP32 pipes
+ *              (error-free products and sums, ~48-bit accurate) with FP64 vectors, to inner_rtol
+ *              relative to r, and sets u += d.
+ *              MTO_MIXED32 (needs the MTO_MIXED build): the same refinement with FP32 vectors in
+ *              the inner PCG (converges only on well-conditioned problems; Jacobi or Schwarz).
+ *              Dot products are accumulated in FP64 in every mode.
  *  rtol        stop when ||f - K u||_2 <= rtol ||f||_2 (free DOFs, FP64 residual).
- *  inner_rtol  MTO_MIXED only: relative residual reduction asked of each inner FP32 solve.
+ *  inner_rtol  mixed solves: relative residual reduction asked of each inner solve (<= 0: 1e-6).
  *  max_iter    limit on the total number of (inner) PCG iterations.
- *  max_outer   MTO_MIXED only: limit on refinement steps.
+ *  max_outer   limit on refinement steps (<= 0: 50; the FP64 solve restarts from its FP64
+ *              residual when the recursive CG residual met rtol before the true one).
  *  warm_start  nonzero: u on entry is the initial guess (else zero).
  *  check_every PCG iterations between host convergence checks (>= 1).
  *  norm        residual norm of the stopping tests: MTO_NORM_L2 (||r||_2 / ||f||_2) or
  *              MTO_NORM_JACOBI (sqrt(r^T D^-1 r / f^T D^-1 f), D = diag(K)); the scaled norm also
  *              weighs the rows of nearly void regions (stiffness ~ Emin), which the l2 norm ignores.
- *  precond     MTO_PREC_JACOBI (point Jacobi) or MTO_PREC_SCHWARZ (element-block additive Schwarz:
+ *  precond     MTO_PREC_JACOBI (point Jacobi), MTO_PREC_SCHWARZ (element-block additive Schwarz:
  *              per element the inverse of K_e plus the neighbours' share of the assembled diagonal,
- *              which captures the near-null modes of solid/void elements).
- *  inner_max   MTO_MIXED only: cap on the iterations of one inner solve (<= 0: none).
+ *              which captures the near-null modes of solid/void elements) or MTO_PREC_MG (one
+ *              V-cycle of element-based Galerkin multigrid: the order p -> bilinear Q1 on the same
+ *              mesh, then 2x2 agglomeration of Q1 elements, Chebyshev-Jacobi smoothing, dense
+ *              inverse on the coarsest grid; FP64 vectors only (not MTO_MIXED32); mesh sides must
+ *              halve down to a coarsest grid of at most 2048 DOFs, else MTO_EINVAL).
+ *  inner_max   mixed solves: cap on the iterations of one inner solve (<= 0: none).
+ *  mg_degree   MTO_PREC_MG only: Chebyshev degree of each pre- and post-smoothing (<= 0: 4).
  * CG iterations run in chunks of check_every (rounded up to a multiple of 4), each a CUDA graph;
  * the reported count stops at convergence, but a chunk already launched completes (cheaply). */
 typedef struct {
@@ -96,10 +106,12 @@ typedef struct {
   int32_t norm;
   int32_t precond;
   int32_t inner_max;
+  int32_t mg_degree;
 } mto_solve_opts;
 
 #define MTO_PREC_JACOBI 0
 #define MTO_PREC_SCHWARZ 1
+#define MTO_PREC_MG 2
 
 #define MTO_NORM_L2 0
 #define MTO_NORM_JACOBI 1
@@ -168,16 +180,17 @@ mto_status mto_element_nodes(mto_handle h, int64_t e, int64_t* nodes, double* we
 
 /* Step (a): element stiffness matrices K_e = sum_s E(rho_s) K0_s (Eqs. 2-3 with the composite
  * integration of App. B) for every element, plus the Jacobi diagonal of the assembled operator.
- * rho: device double[design_len] (packed).  precision MTO_FP64 stores FP64 matrices, applied on
- * the FP64 pipes (the plain FP64 path).  MTO_MIXED stores each matrix as a split-precision FP32
- * pair (hi = fl32(K_e), lo = fl32(K_e - hi), ~48 bits), applied on the FP32 pipes with error-free
- * products and sums.  Matrices stay in the handle (packed upper triangles, element-interleaved).
- * Asynchronous. */
+ * rho: device double[design_len] (packed).  Both precisions store the FP64 matrices (the plain
+ * FP64 path, refinement residuals, indicators); MTO_MIXED also stores each matrix as a
+ * split-precision FP32 pair (hi = fl32(K_e), lo = fl32(K_e - hi), ~48 bits), applied on the FP32
+ * pipes with error-free products and sums by the inner iterations of the mixed solves.  Matrices
+ * stay in the handle, one row of the circulant-diagonal layout per element (D_k[i] = K[i][i+k mod
+ * n_e], k = 0 .. n_e/2), element-major per order class.  Asynchronous. */
 mto_status mto_build_elements(mto_handle h, const double* rho, const mto_material* mat, int32_t precision);
 
 /* Inspection (tests, tools): the current matrix of element e as its packed upper triangle
- * (row-major, i <= j, local DOF 2*node + component), n_e (n_e + 1) / 2 doubles into host memory;
- * from the split pair the value is hi + lo.  Allocates a small device buffer; synchronises. */
+ * (row-major, i <= j, local DOF 2*node + component), n_e (n_e + 1) / 2 doubles into host memory,
+ * from the FP64 matrices.  Allocates a small device buffer; synchronises. */
 mto_status mto_element_matrix(mto_handle h, int64_t e, double* packed);
 
 /* Which kernel forms the element matrices in mto_build_elements:

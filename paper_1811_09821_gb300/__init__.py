@@ -17,10 +17,10 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmto.so")
 
-MTO_FP64, MTO_MIXED = 0, 1
+MTO_FP64, MTO_MIXED, MTO_MIXED32 = 0, 1, 2
 NORM_L2, NORM_JACOBI = 0, 1
 BUILD_TENSOR, BUILD_SIMT = 0, 1
-PREC_JACOBI, PREC_SCHWARZ = 0, 1
+PREC_JACOBI, PREC_SCHWARZ, PREC_MG = 0, 1, 2
 STATUS = {0: "MTO_OK", 1: "MTO_EINVAL", 2: "MTO_ENOMEM", 3: "MTO_ECUDA", 4: "MTO_ENOCONV", 5: "MTO_ENAN",
           6: "MTO_ETIMEOUT"}
 P_MAX, D_MAX = 6, 16
@@ -41,7 +41,7 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("rtol", ctypes.c_double), ("inner_rtol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("warm_start", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("norm", ctypes.c_int32), ("precond", ctypes.c_int32),
-                ("inner_max", ctypes.c_int32)]
+                ("inner_max", ctypes.c_int32), ("mg_degree", ctypes.c_int32)]
 
 
 class IndicatorOpts(ctypes.Structure):
@@ -205,11 +205,11 @@ class Handle:
     def build_elements(self, rho, mat, precision=MTO_FP64):
         self._check(self.L.mto_build_elements(self.h, _ptr(rho, torch.float64), ctypes.byref(mat), precision))
 
-    def solve(self, f, u, precision=MTO_FP64, rtol=1e-8, inner_rtol=1e-4, max_iter=200000, max_outer=50,
+    def solve(self, f, u, precision=MTO_FP64, rtol=1e-8, inner_rtol=0.0, max_iter=200000, max_outer=50,
               warm_start=False, check_every=64, norm=NORM_L2, precond=PREC_SCHWARZ, inner_max=0,
-              raise_on_noconv=True):
+              mg_degree=0, raise_on_noconv=True):
         o = SolveOpts(precision, rtol, inner_rtol, max_iter, max_outer, int(bool(warm_start)), check_every, norm,
-                      precond, inner_max)
+                      precond, inner_max, mg_degree)
         it, rr = ctypes.c_int32(), ctypes.c_double()
         st = self.L.mto_solve(self.h, _ptr(f, torch.float64), _ptr(u, torch.float64), ctypes.byref(o),
                               ctypes.byref(it), ctypes.byref(rr))
@@ -251,11 +251,11 @@ class Handle:
                                           _ptr(th)))
         return pn, dn, th
 
-    def oc_update(self, rho, dc, volfrac, rho_new, move=0.2, eta=0.5):
+    def oc_update(self, rho, dc, volfrac, rho_new, move=0.2, eta=0.5, want_lambda=True):
         lam = ctypes.c_double()
         self._check(self.L.mto_oc_update(self.h, _ptr(rho, torch.float64), _ptr(dc, torch.float64), volfrac, move, eta,
-                                         _ptr(rho_new, torch.float64), ctypes.byref(lam)))
-        return lam.value
+                                         _ptr(rho_new, torch.float64), ctypes.byref(lam) if want_lambda else None))
+        return lam.value if want_lambda else None
 
     def set_build_path(self, path):
         self._check(self.L.mto_set_build_path(self.h, path))

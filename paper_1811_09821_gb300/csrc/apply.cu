@@ -297,13 +297,14 @@ Red red_slot(mto_handle h, int k, int j) {
 
 // y += sum_e P_e^T A_e P_e x over all order classes, where A_e is the element stiffness (which = 0)
 // or the element-block preconditioner (which = 1).  FP64 matrices on the FP64 pipes (plain FP64
-// path) or the split-precision pair on the FP32 pipes (mixed path) with FP64 or FP32 vectors.
-// x^T y goes to reduction slot `slot` (one result per class launch; -1: not wanted); *nres
-// receives the number of class launches.
+// path, refinement residuals) or the split-precision pair on the FP32 pipes (inner iterations of
+// the mixed solves) with FP64 or FP32 vectors.  x^T y goes to reduction slot `slot` (one result
+// per class launch; -1: not wanted); *nres receives the number of class launches.
 template <typename T>
 mto_status apply_all(mto_handle h, int which, const T* x, T* y, int slot, const int* done, ConvTest cv,
                      int* nres = nullptr) {
-  const bool df = h->built_precision == MTO_MIXED;
+  const bool mixed_build = h->built_precision == MTO_MIXED;
+  const bool df = which == 1 ? mixed_build : (sizeof(T) == 4 || (mixed_build && h->inner_split));
   const int fam = which == 1 ? F_PRECOND : (df ? (sizeof(T) == 8 ? F_APPLYDF64 : F_APPLY32) : F_APPLY64);
   TimedScope ts(h, fam);
   int ci = 0;
@@ -441,6 +442,17 @@ __global__ void __launch_bounds__(256) cg_init_kernel(int64_t n, const T* __rest
   if (kJacobi) reduce_out(g, gout);
 }
 
+// r^T z after the multigrid cycle (one launch, last-block reduction)
+__global__ void __launch_bounds__(256) cg_dot_kernel(int64_t n, const double* __restrict__ a,
+                                                     const double* __restrict__ b, Red out,
+                                                     const int* __restrict__ done) {
+  if (done && *done) return;
+  double s = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    s += a[j] * b[j];
+  reduce_out(s, out);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) copy_kernel(int64_t n, const T* __restrict__ a, T* __restrict__ b) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
@@ -499,6 +511,12 @@ __global__ void __launch_bounds__(256) demote_kernel(int64_t n, const double* __
   }
 }
 
+// u += d
+__global__ void __launch_bounds__(256) axpy_kernel(int64_t n, const double* __restrict__ d, double* __restrict__ u) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    u[i] += d[i];
+}
+
 // u += x32 / scale
 __global__ void __launch_bounds__(256) promote_kernel(int64_t n, const float* __restrict__ x32, double inv_scale,
                                                       double* __restrict__ u) {
@@ -549,18 +567,40 @@ CGVecs<float> cg_vecs<float>(mto_handle h, float* x, float* r) {
 // result j of reduction slot k
 inline const double* res_slot(mto_handle h, int k) { return h->cg_res + 8 * k; }
 
+// The preconditioner step z = M^-1 r with r^T z into reduction slot `slot` (element-block Schwarz:
+// one result per class launch; multigrid: one).
+template <typename T>
+mto_status precond_step(mto_handle h, const CGVecs<T>& v, int pc, int deg, int slot, const int* done);
+template <>
+mto_status precond_step<double>(mto_handle h, const CGVecs<double>& v, int pc, int deg, int slot,
+                                const int* done) {
+  ConvTest none{};
+  if (pc == MTO_PREC_SCHWARZ) return apply_all<double>(h, 1, v.r, v.z, slot, done, none);
+  MTO_TRY(mg_vcycle(h, v.r, v.z, deg, done));
+  TimedScope ts(h, F_VECTOR);
+  cg_dot_kernel<<<kVecBlocks, 256, 0, h->stream>>>(h->ndof, v.r, v.z, red_slot(h, slot, 0), done);
+  return mto_after_launch(h, "cg_dot_kernel");
+}
+template <>
+mto_status precond_step<float>(mto_handle h, const CGVecs<float>& v, int pc, int deg, int slot, const int* done) {
+  ConvTest none{};
+  if (pc == MTO_PREC_SCHWARZ) return apply_all<float>(h, 1, v.r, v.z, slot, done, none);
+  return mto_fail(h, MTO_EINVAL, "the multigrid preconditioner needs FP64 vectors (precision MTO_FP64)");
+}
+
 // The launches of CG iteration `local` of a chunk (nc = number of order classes).
 template <typename T>
-mto_status cg_iteration(mto_handle h, const CGVecs<T>& v, bool schwarz, int nrm, const double* ref, double tol2,
+mto_status cg_iteration(mto_handle h, const CGVecs<T>& v, int pc, int deg, int nrm, const double* ref, double tol2,
                         int local, int nc) {
   const int64_t n = h->ndof;
   const int par = local & 1, nxt = par ^ 1;
-  const int ng = schwarz ? nc : 1;
+  const bool jac = pc == MTO_PREC_JACOBI;
+  const int ng = pc == MTO_PREC_SCHWARZ ? nc : 1;
   ConvTest none{};
   MTO_TRY(apply_all<T>(h, 0, v.p, v.q, kDel + par, h->flags, none));
   {
     TimedScope ts(h, F_VECTOR);
-    if (schwarz)
+    if (!jac)
       cg_vector_kernel<T, false><<<kVecBlocks, 256, 0, h->stream>>>(
           n, v.x, v.r, v.p, v.q, v.z, v.invd, res_slot(h, kGam + par), ng, res_slot(h, kDel + par), nc,
           red_slot(h, -1, 0), red_slot(h, kRR + nxt, 0), red_slot(h, kRD + nxt, 0), h->cg_base, local, h->flags,
@@ -572,11 +612,11 @@ mto_status cg_iteration(mto_handle h, const CGVecs<T>& v, bool schwarz, int nrm,
           h->flags, h->flags + 1);
     MTO_TRY(mto_after_launch(h, "cg_vector_kernel"));
   }
-  if (schwarz) MTO_TRY(apply_all<T>(h, 1, v.r, v.z, kGam + nxt, h->flags, none));
+  if (!jac) MTO_TRY(precond_step<T>(h, v, pc, deg, kGam + nxt, h->flags));
   {
     TimedScope ts(h, F_VECTOR);
     ConvTest cv{res_slot(h, nrm ? kRD + nxt : kRR + nxt), 1, ref, tol2, h->cg_base, local, h->flags, h->flags + 1};
-    if (schwarz)
+    if (!jac)
       cg_direction_kernel<T, false><<<kVecBlocks, 256, 0, h->stream>>>(
           n, v.r, v.z, v.p, v.invd, res_slot(h, kGam + nxt), res_slot(h, kGam + par), ng, cv);
     else
@@ -591,8 +631,9 @@ mto_status cg_iteration(mto_handle h, const CGVecs<T>& v, bool schwarz, int nrm,
 // residual norm^2 (l2 or Jacobi) <= tol2 * (*ref) or after max_it iterations.  Iterations run in
 // chunks of `chunk` (even), each captured once as a CUDA graph and replayed.
 template <typename T>
-mto_status run_cg(mto_handle h, T* x, T* r, bool schwarz, int nrm, const double* ref, double tol2, int max_it,
+mto_status run_cg(mto_handle h, T* x, T* r, int pc, int deg, int nrm, const double* ref, double tol2, int max_it,
                   int chunk, int* iters) {
+  const bool schwarz = pc != MTO_PREC_JACOBI;   // z kept in its own vector
   const int64_t n = h->ndof;
   CGVecs<T> v = cg_vecs<T>(h, x, r);
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->flags, 0, 2 * sizeof(int), h->stream), "memset"));
@@ -612,8 +653,12 @@ mto_status run_cg(mto_handle h, T* x, T* r, bool schwarz, int nrm, const double*
                                                                  red_slot(h, kGam, 0));
     MTO_TRY(mto_after_launch(h, "cg_init_kernel"));
   }
+  if (pc == MTO_PREC_MG) {
+    for (auto& l : h->mg) MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(l.q, 0, l.n * sizeof(double), h->stream), "memset"));
+    MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->mg_q0, 0, n * sizeof(double), h->stream), "memset"));
+  }
   if (schwarz) {
-    MTO_TRY(apply_all<T>(h, 1, v.r, v.z, kGam, nullptr, none));
+    MTO_TRY(precond_step<T>(h, v, pc, deg, kGam, nullptr));
     TimedScope ts(h, F_VECTOR);
     copy_kernel<T><<<kVecBlocks, 256, 0, h->stream>>>(n, v.z, v.p);
     MTO_TRY(mto_after_launch(h, "copy_kernel"));
@@ -622,8 +667,8 @@ mto_status run_cg(mto_handle h, T* x, T* r, bool schwarz, int nrm, const double*
   const bool use_graph = h->use_graphs;
   GraphEntry* ge = nullptr;
   if (use_graph) {
-    GraphKey key{sizeof(T), (const void*)x, (const void*)r, schwarz, nrm, ref, tol2, chunk, h->timing.on,
-                 h->built_precision};
+    GraphKey key{sizeof(T), (const void*)x, (const void*)r, pc, deg, nrm, ref, tol2, chunk, h->timing.on,
+                 2 * h->built_precision + (h->inner_split ? 1 : 0)};
     ge = find_graph(h, key);
     if (!ge) {
       ge = new_graph(h, key);
@@ -633,7 +678,7 @@ mto_status run_cg(mto_handle h, T* x, T* r, bool schwarz, int nrm, const double*
       h->timing.capture_list = &ge->events;
       mto_status st = MTO_OK;
       for (int l = 0; l < chunk && st == MTO_OK; ++l)
-        st = cg_iteration<T>(h, v, schwarz, nrm, ref, tol2, l, nc);
+        st = cg_iteration<T>(h, v, pc, deg, nrm, ref, tol2, l, nc);
       if (st == MTO_OK) {
         advance_kernel<<<1, 32, 0, h->stream>>>(h->cg_base, chunk);
         st = mto_after_launch(h, "advance_kernel");
@@ -656,7 +701,7 @@ mto_status run_cg(mto_handle h, T* x, T* r, bool schwarz, int nrm, const double*
       h->launches += ge->launches_per_replay;
       k += chunk;
     } else {
-      for (int l = 0; l < chunk; ++l) MTO_TRY(cg_iteration<T>(h, v, schwarz, nrm, ref, tol2, l, nc));
+      for (int l = 0; l < chunk; ++l) MTO_TRY(cg_iteration<T>(h, v, pc, deg, nrm, ref, tol2, l, nc));
       advance_kernel<<<1, 32, 0, h->stream>>>(h->cg_base, chunk);
       MTO_TRY(mto_after_launch(h, "advance_kernel"));
       k += chunk;
@@ -703,6 +748,18 @@ mto_status apply64(mto_handle h, const double* x, double* y) {
   return apply_all<double>(h, 0, x, y, -1, nullptr, none);
 }
 
+mto_status apply_fine(mto_handle h, const double* x, double* y, const int* done) {
+  ConvTest none{};
+  return apply_all<double>(h, 0, x, y, -1, done, none);
+}
+
+mto_status apply_q1(mto_handle h, const MGLevel& l, const double* x, double* y, const int* done) {
+  ConvTest none{};
+  ebe_kernel<1, false, double><<<ebe_blocks_p<1>(l.nel), 256, 0, h->stream>>>(
+      l.K, nullptr, nullptr, 40, l.nel, l.gmap, nullptr, x, y, Red{nullptr, nullptr, nullptr}, done, none);
+  return mto_after_launch(h, "ebe_kernel");
+}
+
 mto_status dot64(mto_handle h, const double* a, const double* b, int64_t n, double* out_dev) {
   dot_kernel<<<kVecBlocks, 256, 0, h->stream>>>(n, a, b, h->cg_part);
   MTO_TRY(mto_after_launch(h, "dot_kernel"));
@@ -714,8 +771,14 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
                  double* relres_out) {
   const int64_t n = h->ndof;
   const int grd = grid_for(n, 256, 152 * 4);
-  const bool schwarz = o->precond == MTO_PREC_SCHWARZ;
-  if (schwarz && !h->schwarz_valid) MTO_TRY(build_schwarz(h));
+  const int pc = o->precond;
+  const int deg = o->mg_degree > 0 ? o->mg_degree : 4;
+  if (pc == MTO_PREC_SCHWARZ && !h->schwarz_valid) MTO_TRY(build_schwarz(h));
+  if (pc == MTO_PREC_MG) {
+    if (o->precision == MTO_MIXED32)
+      return mto_fail(h, MTO_EINVAL, "mto_solve: the multigrid preconditioner needs FP64 vectors");
+    if (!h->mg_valid) MTO_TRY(mg_build(h));
+  }
   if (!o->warm_start) MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(u, 0, sizeof(double) * n, h->stream), "memset"));
   else {
     mask_kernel<<<grd, 256, 0, h->stream>>>(n, h->invd64, u);
@@ -726,8 +789,11 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
   double rr = 0.0, ff = 0.0;
   const int max_outer = o->max_outer > 0 ? o->max_outer : 50;
   const int nrm = o->norm == MTO_NORM_JACOBI ? 1 : 0;
+  const double itol = o->inner_rtol > 0 ? o->inner_rtol : 1e-6;
   mto_status st = MTO_ENOCONV;
   for (int outer = 0; outer <= max_outer; ++outer) {
+    // FP64 residual with the FP64 element matrices
+    h->inner_split = false;
     MTO_TRY(true_residual(h, f, u, nrm, &rr, &ff));
     if (!std::isfinite(rr)) {
       st = mto_fail(h, MTO_ENAN, "mto_solve: non-finite residual");
@@ -739,12 +805,27 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
     }
     if (total >= o->max_iter || outer == max_outer) break;
     int it = 0;
+    const int cap = o->inner_max > 0 ? o->inner_max : 1 << 30;
+    const int budget = o->max_iter - total < cap ? o->max_iter - total : cap;
     if (o->precision == MTO_FP64) {
-      // h->red[1] (h->red[3]) holds f^T f (f^T D^-1 f): CG runs until the residual norm meets rtol
-      MTO_TRY(run_cg<double>(h, u, h->r64, schwarz, nrm, h->red + (nrm ? 3 : 1), o->rtol * o->rtol,
+      // plain FP64 PCG on u itself; h->red[1] (h->red[3]) holds f^T f (f^T D^-1 f)
+      MTO_TRY(run_cg<double>(h, u, h->r64, pc, deg, nrm, h->red + (nrm ? 3 : 1), o->rtol * o->rtol,
                              o->max_iter - total, chunk, &it));
+    } else if (o->precision == MTO_MIXED) {
+      // refinement step: K_split d = r with FP64 vectors (d in s64, from zero), to inner_rtol
+      // relative to the current residual (h->red[0] / h->red[2]), then u += d
+      h->inner_split = true;
+      MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->s64, 0, sizeof(double) * n, h->stream), "memset"));
+      const mto_status si = run_cg<double>(h, h->s64, h->r64, pc, deg, nrm, h->red + (nrm ? 2 : 0), itol * itol,
+                                           budget, chunk, &it);
+      h->inner_split = false;
+      MTO_TRY(si);
+      TimedScope ts(h, F_VECTOR);
+      axpy_kernel<<<grd, 256, 0, h->stream>>>(n, h->s64, u);
+      MTO_TRY(mto_after_launch(h, "axpy_kernel"));
     } else {
-      const double rr2 = h->host_pinned[0];                 // l2 norm^2 of the FP64 residual
+      // refinement step with FP32 vectors: the residual scaled to unit l2 norm
+      const double rr2 = h->host_pinned[0];
       const double scale = 1.0 / std::sqrt(rr2);
       {
         TimedScope ts(h, F_VECTOR);
@@ -755,10 +836,7 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
       h->host_pinned[32] = nrm ? h->host_pinned[2] / rr2 : 1.0;
       MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->red + 4, h->host_pinned + 32, sizeof(double),
                                                 cudaMemcpyHostToDevice, h->stream), "copy"));
-      const double itol = o->inner_rtol > 0 ? o->inner_rtol : 1e-4;
-      const int cap = o->inner_max > 0 ? o->inner_max : 1 << 30;
-      const int budget = o->max_iter - total < cap ? o->max_iter - total : cap;
-      MTO_TRY(run_cg<float>(h, h->x32, h->r32, schwarz, nrm, h->red + 4, itol * itol, budget, chunk, &it));
+      MTO_TRY(run_cg<float>(h, h->x32, h->r32, pc, deg, nrm, h->red + 4, itol * itol, budget, chunk, &it));
       {
         TimedScope ts(h, F_VECTOR);
         promote_kernel<<<grd, 256, 0, h->stream>>>(n, h->x32, 1.0 / scale, u);

@@ -247,9 +247,8 @@ __global__ void gather_element_matrix_kernel(int P, int L, const int2* __restric
 
 template <int PO>
 void launch_diag(mto_handle h, const PClass& c, double* diag) {
-  const bool df = h->built_precision == MTO_MIXED;
   diag_kernel<PO><<<grid_for(c.n, 128, 1 << 30), 128, 0, h->stream>>>(c.n, c.L, c.dpos, c.gmap, h->cons_d,
-                                                                      df ? nullptr : c.K64, c.K32, c.K32lo, diag);
+                                                                      c.K64, c.K32, c.K32lo, diag);
 }
 
 // Element-block (additive Schwarz) preconditioner M^-1 = sum_e P_e^T B_e P_e with
@@ -360,8 +359,7 @@ mto_status launch_schwarz(mto_handle h, PClass& c) {
                                                    (int)smem), "cudaFuncSetAttribute"));
   const bool df = h->built_precision == MTO_MIXED;
   const int blocks = grid_for(c.n, wpb, 152 * 8);
-  schwarz_kernel<PO><<<blocks, 32 * wpb, smem, h->stream>>>(c.n, c.L, c.dpos, c.gmap, h->cons_d,
-                                                            df ? nullptr : c.K64, c.K32,
+  schwarz_kernel<PO><<<blocks, 32 * wpb, smem, h->stream>>>(c.n, c.L, c.dpos, c.gmap, h->cons_d, c.K64, c.K32,
                                                             c.K32lo, h->diag64, h->invd64, df ? nullptr : c.B64,
                                                             c.B32, c.B32lo);
   return mto_after_launch(h, "schwarz_kernel");
@@ -400,9 +398,8 @@ mto_status element_matrix(mto_handle h, int64_t e, double* host_out) {
   MTO_TRY(mto_cuda_check(h, cudaMemcpy(&slot, h->slot_d + e, sizeof(int), cudaMemcpyDeviceToHost), "copy"));
   double* tmp = nullptr;
   MTO_TRY(mto_cuda_check(h, cudaMalloc(&tmp, sizeof(double) * c.P), "cudaMalloc"));
-  const bool df = h->built_precision == MTO_MIXED;
-  gather_element_matrix_kernel<<<(c.P + 255) / 256, 256, 0, h->stream>>>(c.P, c.L, c.dpos, slot,
-                                                                         df ? nullptr : c.K64, c.K32, c.K32lo, tmp);
+  gather_element_matrix_kernel<<<(c.P + 255) / 256, 256, 0, h->stream>>>(c.P, c.L, c.dpos, slot, c.K64, c.K32,
+                                                                         c.K32lo, tmp);
   mto_status st = mto_after_launch(h, "gather_element_matrix_kernel");
   if (st == MTO_OK)
     st = mto_cuda_check(h, cudaMemcpyAsync(host_out, tmp, sizeof(double) * c.P, cudaMemcpyDeviceToHost, h->stream), "copy");
@@ -446,7 +443,7 @@ mto_status build_elements(mto_handle h, const double* rho, const mto_material* m
   for (int p = 1; p <= MTO_P_MAX; ++p) {
     PClass& c = h->pc[p];
     if (c.n == 0) continue;
-    if (precision == MTO_FP64 && !c.K64) MTO_TRY(mto_alloc(h, &c.K64, (size_t)c.L * c.n));
+    if (!c.K64) MTO_TRY(mto_alloc(h, &c.K64, (size_t)c.L * c.n));
     if (precision == MTO_MIXED && !c.K32) {
       MTO_TRY(mto_alloc(h, &c.K32, (size_t)c.L * c.n));
       MTO_TRY(mto_alloc(h, &c.K32lo, (size_t)c.L * c.n));
@@ -463,8 +460,7 @@ mto_status build_elements(mto_handle h, const double* rho, const mto_material* m
       cudaFuncSetAttribute(build_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     build_simt_kernel<<<(b.n + 31) / 32, 256, smem, h->stream>>>(
         b.n, b.S, b.P, b.elem, b.slot, h->design_off_d, rho, m->E0, m->Emin, m->q, b.K0T, c.L, c.dpos,
-        precision == MTO_FP64 ? c.K64 : nullptr, precision == MTO_MIXED ? c.K32 : nullptr,
-        precision == MTO_MIXED ? c.K32lo : nullptr);
+        c.K64, precision == MTO_MIXED ? c.K32 : nullptr, precision == MTO_MIXED ? c.K32lo : nullptr);
     MTO_TRY(mto_after_launch(h, "build_simt_kernel"));
   }
   return MTO_OK;

@@ -700,9 +700,8 @@ mto_status indicators(mto_handle h, const double* u, const double* rho, const mt
     const int n0 = 2 * (b.p + 1) * (b.p + 1), n1 = 2 * (b.p + 2) * (b.p + 2);
     size_t smem = sizeof(double) * ((size_t)n1 * n1 + packed_size(n1) + n0 + n1 + n1 + b.S + n0);
     if (smem > 48 * 1024) cudaFuncSetAttribute(qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const bool df = h->built_precision == MTO_MIXED;
     qr_kernel<<<b.n, 32, smem, h->stream>>>(b.p, b.d, b.n, b.elem, b.slot, c.L, c.dpos, c.gmap, h->cons_d,
-                                            df ? nullptr : c.K64, c.K32, c.K32lo, b1.K0T,
+                                            c.K64, c.K32, c.K32lo, b1.K0T,
                                             h->qr[b.p].R, u, rho, h->design_off_d, m->E0, m->Emin, m->q, B, h->hx,
                                             h->hy, eq_);
     MTO_TRY(mto_after_launch(h, "qr_kernel"));

@@ -1,0 +1,794 @@
+// Multigrid preconditioner for the PCG of step (b).  The paper does not name its solver; on the
+// binary 0/1 designs of these workloads (stiffness contrast 1e9) one-level preconditioners need
+// tens of thousands of iterations, and their count grows with the mesh, so the solve is
+// preconditioned by one V-cycle of an element-based Galerkin multigrid:
+//
+//   level 0   the order-p element operator itself (minimum-rule conforming, any p map);
+//   level 1   bilinear Q1 on the same mesh.  Its element matrices are the exact Galerkin products
+//             N_e^T K_e N_e, N_e = bilinear interpolation of the four vertex values at the
+//             element's GLL nodes: a Q1 field is continuous and lies in every element's space, so
+//             the element-wise products assemble to P^T K P for the global prolongation P;
+//   level l+1 2x2 agglomeration of level l: K_E = sum_c J_c^T K_c J_c with J_c the bilinear
+//             interpolation of the coarse element's vertices at its child's vertices (again the
+//             exact Galerkin operator, because bilinear coarse fields are bilinear on the children);
+//   coarsest  a dense inverse (at most 2048 DOFs).
+//
+// Smoothing: Chebyshev polynomials of the Jacobi-scaled operator on [lmax / 30, lmax], lmax from
+// a power iteration (x 1.1), the same polynomial before and after the coarse correction, so the
+// cycle is a symmetric positive definite preconditioner.  Supported DOFs are masked on every level
+// (they coincide with vertices of the coarser grids for the clamped edge and the MBB supports; the
+// fine-level mask is applied to every transfer).  All levels keep FP64 vectors; level 0 applies
+// whichever element matrices were built (FP64 or the split-precision pair).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "mto_internal.cuh"
+
+namespace mto {
+namespace {
+
+constexpr int kCoarseTarget = 256;    // stop coarsening at or below this many DOFs
+constexpr int kCoarseMax = 2048;      // largest coarsest grid for the dense inverse
+constexpr double kChebRatio = 30.0;   // lmin = lmax / ratio
+constexpr int kPowerIts = 30;
+constexpr int kMGBlocks = 152 * 4;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum of one double; valid in thread 0
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double part[32];
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) part[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (w == 0) {
+    s = l < (int)((blockDim.x + 31) >> 5) ? part[l] : 0.0;
+    s = warp_sum(s);
+  }
+  __syncthreads();
+  return s;
+}
+
+// Entry K[i][j] of an element row in the circulant-diagonal layout (n_e = ne).
+__device__ __forceinline__ int circ_pos(int i, int j, int ne) {
+  int k = j - i;
+  if (k < 0) k += ne;
+  if (2 * k <= ne) return k * ne + i;
+  return (ne - k) * ne + j;
+}
+
+// ---------------------------------------------------------------- Galerkin operators
+// Level 1 from the order-PO elements: K1 = N^T K_e N per element (one thread per element).
+// The component blocks separate: K1[2V1+c1][2V2+c2] = sum_{a,b} B[a][V1] K_e[2a+c1][2b+c2] B[b][V2].
+template <int PO>
+__global__ void __launch_bounds__(128) mg_galerkin_p_kernel(int n, const int* __restrict__ elem, int L,
+                                                            const double* __restrict__ K64,
+                                                            const float* __restrict__ Kh,
+                                                            const float* __restrict__ Kl,
+                                                            const double* __restrict__ B,
+                                                            double* __restrict__ K1) {
+  constexpr int NN = (PO + 1) * (PO + 1), NE = 2 * NN;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const size_t row = (size_t)k * L;
+  double acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.0;
+  for (int a = 0; a < NN; ++a) {
+    double ba[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) ba[v] = B[a * 4 + v];
+#pragma unroll
+    for (int c1 = 0; c1 < 2; ++c1) {
+      const int i = 2 * a + c1;
+      double t[2][4];
+#pragma unroll
+      for (int c2 = 0; c2 < 2; ++c2)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) t[c2][v] = 0.0;
+      for (int b = 0; b < NN; ++b) {
+#pragma unroll
+        for (int c2 = 0; c2 < 2; ++c2) {
+          const int pos = circ_pos(i, 2 * b + c2, NE);
+          const double kij = K64 ? K64[row + pos] : (double)Kh[row + pos] + (double)Kl[row + pos];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) t[c2][v] = fma(kij, B[b * 4 + v], t[c2][v]);
+        }
+      }
+#pragma unroll
+      for (int v1 = 0; v1 < 4; ++v1)
+#pragma unroll
+        for (int c2 = 0; c2 < 2; ++c2)
+#pragma unroll
+          for (int v2 = 0; v2 < 4; ++v2) acc[2 * v1 + c1][2 * v2 + c2] = fma(ba[v1], t[c2][v2], acc[2 * v1 + c1][2 * v2 + c2]);
+    }
+  }
+  const int e = elem[k];
+  double* out = K1 + (size_t)e * 40;
+#pragma unroll
+  for (int kk = 0; kk <= 4; ++kk)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int j = (i + kk) & 7;
+      out[kk * 8 + i] = 0.5 * (acc[i][j] + acc[j][i]);
+    }
+}
+
+// Level l+1 from level l: K_E = sum over the 2x2 children of J_c^T K_c J_c (one thread per coarse
+// element).  Child vertex (vx, vy) of child (cx, cy) sits at ((cx + vx) / 2, (cy + vy) / 2) of the
+// coarse element; coarse vertex (X, Y) has weight (X ? s : 1 - s) (Y ? t : 1 - t) there.
+__global__ void __launch_bounds__(128) mg_galerkin_h_kernel(int nxc, int nyc, int nxf, const double* __restrict__ Kf,
+                                                            double* __restrict__ Kc) {
+  const int E = blockIdx.x * blockDim.x + threadIdx.x;
+  if (E >= nxc * nyc) return;
+  const int EX = E % nxc, EY = E / nxc;
+  double acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.0;
+  for (int cy = 0; cy < 2; ++cy)
+    for (int cx = 0; cx < 2; ++cx) {
+      const double* kc = Kf + (size_t)((2 * EY + cy) * nxf + 2 * EX + cx) * 40;
+      double J[4][4];   // [child vertex][coarse vertex]
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const double s = 0.5 * (cx + (v & 1)), t = 0.5 * (cy + (v >> 1));
+#pragma unroll
+        for (int V = 0; V < 4; ++V) J[v][V] = ((V & 1) ? s : 1.0 - s) * ((V >> 1) ? t : 1.0 - t);
+      }
+      double K[8][8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) K[i][j] = kc[circ_pos(i, j, 8)];
+#pragma unroll
+      for (int c1 = 0; c1 < 2; ++c1)
+#pragma unroll
+        for (int c2 = 0; c2 < 2; ++c2) {
+          double T[4][4];   // [child vertex v1][coarse vertex V2] = sum_v2 K[2v1+c1][2v2+c2] J[v2][V2]
+#pragma unroll
+          for (int v1 = 0; v1 < 4; ++v1)
+#pragma unroll
+            for (int V2 = 0; V2 < 4; ++V2) {
+              double t = 0.0;
+#pragma unroll
+              for (int v2 = 0; v2 < 4; ++v2) t = fma(K[2 * v1 + c1][2 * v2 + c2], J[v2][V2], t);
+              T[v1][V2] = t;
+            }
+#pragma unroll
+          for (int V1 = 0; V1 < 4; ++V1)
+#pragma unroll
+            for (int V2 = 0; V2 < 4; ++V2) {
+              double t = 0.0;
+#pragma unroll
+              for (int v1 = 0; v1 < 4; ++v1) t = fma(J[v1][V1], T[v1][V2], t);
+              acc[2 * V1 + c1][2 * V2 + c2] += t;
+            }
+        }
+    }
+  double* out = Kc + (size_t)E * 40;
+#pragma unroll
+  for (int kk = 0; kk <= 4; ++kk)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int j = (i + kk) & 7;
+      out[kk * 8 + i] = 0.5 * (acc[i][j] + acc[j][i]);
+    }
+}
+
+// assembled diagonal of a Q1 level (atomics), then the masked inverse
+__global__ void mg_diag_kernel(int nel, const int* __restrict__ gmap, const double* __restrict__ K,
+                               double* __restrict__ diag) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nel) return;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) atomicAdd(diag + 2 * (size_t)gmap[4 * e + (i >> 1)] + (i & 1), K[(size_t)e * 40 + i]);
+}
+
+__global__ void mg_invd_kernel(int64_t n, const double* __restrict__ mask, double* __restrict__ diag_inv) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double dg = diag_inv[i];
+    diag_inv[i] = (mask[i] != 0.0 && dg > 0.0) ? 1.0 / dg : 0.0;
+  }
+}
+
+// coarsest level: dense assembly, supported rows/columns replaced by identity, in-place
+// Gauss-Jordan inversion (SPD: no pivoting) in one block
+__global__ void mg_dense_assemble_kernel(int nel, int N, const int* __restrict__ gmap, const double* __restrict__ K,
+                                         double* __restrict__ A) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nel) return;
+  for (int i = 0; i < 8; ++i) {
+    const int gi = 2 * gmap[4 * e + (i >> 1)] + (i & 1);
+    for (int j = 0; j < 8; ++j) {
+      const int gj = 2 * gmap[4 * e + (j >> 1)] + (j & 1);
+      atomicAdd(A + (size_t)gi * N + gj, K[(size_t)e * 40 + circ_pos(i, j, 8)]);
+    }
+  }
+}
+
+__global__ void mg_dense_fix_kernel(int N, const double* __restrict__ mask, double* __restrict__ A) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)N * N;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / N), j = (int)(t % N);
+    if (mask[i] == 0.0 || mask[j] == 0.0) A[t] = (i == j) ? 1.0 : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(1024) mg_gauss_jordan_kernel(int N, double* __restrict__ A, int* __restrict__ err) {
+  extern __shared__ double col[];   // [N] column k before elimination
+  for (int k = 0; k < N; ++k) {
+    const double piv = A[(size_t)k * N + k];
+    __syncthreads();
+    if (!(piv > 0.0)) {
+      if (threadIdx.x == 0) *err = MTO_ENAN;
+      return;   // uniform: every thread read the same pivot
+    }
+    const double inv = 1.0 / piv;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) col[i] = A[(size_t)i * N + k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x) A[(size_t)k * N + j] = (j == k) ? inv : A[(size_t)k * N + j] * inv;
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < (int64_t)N * N; t += blockDim.x) {
+      const int i = (int)(t / N), j = (int)(t % N);
+      if (i == k) continue;
+      if (j == k) A[t] = -col[i] * inv;
+      else A[t] = fma(-col[i], A[(size_t)k * N + j], A[t]);
+    }
+    __syncthreads();
+  }
+}
+
+// x = Ainv b (one warp per row)
+__global__ void __launch_bounds__(256) mg_coarse_solve_kernel(int N, const double* __restrict__ Ainv,
+                                                              const double* __restrict__ b, double* __restrict__ x,
+                                                              const int* __restrict__ done) {
+  if (done && *done) return;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, l = threadIdx.x & 31;
+  if (w >= N) return;
+  double s = 0.0;
+  for (int j = l; j < N; j += 32) s = fma(Ainv[(size_t)w * N + j], b[j], s);
+  s = warp_sum(s);
+  if (l == 0) x[w] = s;
+}
+
+// ---------------------------------------------------------------- smoothing and transfers
+// One Chebyshev step on level vectors: r = D^-1 (b - q) (q = A x, then cleared), step 0:
+// d = r / theta, step s > 0: d = rho_s rho_{s-1} d + (2 rho_s / delta) r; x = d (xzero) or x += d.
+__global__ void __launch_bounds__(256) mg_cheb_kernel(int64_t n, const double* __restrict__ b, double* __restrict__ q,
+                                                      const double* __restrict__ invd, double* __restrict__ x,
+                                                      double* __restrict__ d, const double* __restrict__ lmax,
+                                                      int step, int xzero, const int* __restrict__ done) {
+  if (done && *done) return;
+  const double lm = *lmax, lo = lm / kChebRatio;
+  const double th = 0.5 * (lm + lo), de = 0.5 * (lm - lo), sg = th / de;
+  double c1 = 0.0, c2 = 1.0 / th;
+  if (step > 0) {
+    double rp = 1.0 / sg, rc = rp;
+    for (int j = 1; j <= step; ++j) {
+      rp = rc;
+      rc = 1.0 / (2.0 * sg - rp);
+    }
+    c1 = rc * rp;
+    c2 = 2.0 * rc / de;
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double r = invd[i] * (b[i] - q[i]);
+    q[i] = 0.0;
+    const double dn = step > 0 ? fma(c1, d[i], c2 * r) : c2 * r;
+    d[i] = dn;
+    x[i] = xzero ? dn : x[i] + dn;
+  }
+}
+
+// residual on free DOFs: d = (b - q) masked, q cleared
+__global__ void __launch_bounds__(256) mg_residual_kernel(int64_t n, const double* __restrict__ b,
+                                                          double* __restrict__ q, const double* __restrict__ invd,
+                                                          double* __restrict__ d, const int* __restrict__ done) {
+  if (done && *done) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    d[i] = invd[i] != 0.0 ? b[i] - q[i] : 0.0;
+    q[i] = 0.0;
+  }
+}
+
+// level 0 -> 1: b1 = P^T r by the vertex-wise transposed table
+__global__ void __launch_bounds__(256) mg_restrict0_kernel(int64_t nv, const int* __restrict__ ptr,
+                                                           const int* __restrict__ node, const double* __restrict__ w,
+                                                           const double* __restrict__ r, const double* __restrict__ mask,
+                                                           double* __restrict__ b1, const int* __restrict__ done) {
+  if (done && *done) return;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int k = ptr[v]; k < ptr[v + 1]; ++k) {
+      const double wk = w[k];
+      const size_t g = 2 * (size_t)node[k];
+      s0 = fma(wk, r[g], s0);
+      s1 = fma(wk, r[g + 1], s1);
+    }
+    b1[2 * v] = mask[2 * v] * s0;
+    b1[2 * v + 1] = mask[2 * v + 1] * s1;
+  }
+}
+
+// level 1 -> 0: x += P x1 on free DOFs
+__global__ void __launch_bounds__(256) mg_prolong0_kernel(int64_t nn, const int* __restrict__ idx,
+                                                          const double* __restrict__ w, const double* __restrict__ x1,
+                                                          const double* __restrict__ invd, double* __restrict__ x,
+                                                          const int* __restrict__ done) {
+  if (done && *done) return;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double wk = w[4 * g + k];
+      const size_t v = 2 * (size_t)idx[4 * g + k];
+      s0 = fma(wk, x1[v], s0);
+      s1 = fma(wk, x1[v + 1], s1);
+    }
+    if (invd[2 * g] != 0.0) x[2 * g] += s0;
+    if (invd[2 * g + 1] != 0.0) x[2 * g + 1] += s1;
+  }
+}
+
+// level l -> l+1 on vertex grids (full weighting: the transpose of bilinear interpolation)
+__global__ void __launch_bounds__(256) mg_restrict_h_kernel(int nxc, int nyc, int nxf, int nyf,
+                                                            const double* __restrict__ r, const double* __restrict__ mask,
+                                                            double* __restrict__ bc, const int* __restrict__ done) {
+  if (done && *done) return;
+  const int64_t nvc = (int64_t)(nxc + 1) * (nyc + 1);
+  for (int64_t V = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; V < nvc; V += (int64_t)gridDim.x * blockDim.x) {
+    const int I = (int)(V % (nxc + 1)), J = (int)(V / (nxc + 1));
+    double s0 = 0.0, s1 = 0.0;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int j = 2 * J + dy;
+      if (j < 0 || j > nyf) continue;
+      const double wy = dy == 0 ? 1.0 : 0.5;
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int i = 2 * I + dx;
+        if (i < 0 || i > nxf) continue;
+        const double wgt = wy * (dx == 0 ? 1.0 : 0.5);
+        const size_t f = 2 * ((size_t)j * (nxf + 1) + i);
+        s0 = fma(wgt, r[f], s0);
+        s1 = fma(wgt, r[f + 1], s1);
+      }
+    }
+    bc[2 * V] = mask[2 * V] * s0;
+    bc[2 * V + 1] = mask[2 * V + 1] * s1;
+  }
+}
+
+// level l+1 -> l: x += bilinear interpolation of the coarse correction (free DOFs)
+__global__ void __launch_bounds__(256) mg_prolong_h_kernel(int nxc, int nxf, int nyf, const double* __restrict__ xc,
+                                                           const double* __restrict__ mask, double* __restrict__ xf,
+                                                           const int* __restrict__ done) {
+  if (done && *done) return;
+  const int64_t nvf = (int64_t)(nxf + 1) * (nyf + 1);
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nvf; v += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(v % (nxf + 1)), j = (int)(v / (nxf + 1));
+    const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1;
+    const double wi = (i & 1) ? 0.5 : 1.0, wj = (j & 1) ? 0.5 : 1.0;
+    double s0 = 0.0, s1 = 0.0;
+    const int is[2] = {i0, i1}, js[2] = {j0, j1};
+    const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1;
+    for (int b = 0; b < nj; ++b)
+      for (int a = 0; a < ni; ++a) {
+        const size_t c = 2 * ((size_t)js[b] * (nxc + 1) + is[a]);
+        s0 = fma(wi * wj, xc[c], s0);
+        s1 = fma(wi * wj, xc[c + 1], s1);
+      }
+    xf[2 * v] += mask[2 * v] * s0;
+    xf[2 * v + 1] += mask[2 * v + 1] * s1;
+  }
+}
+
+// ---------------------------------------------------------------- power iteration for lmax
+__global__ void mg_pow_init_kernel(int64_t n, const double* __restrict__ invd, double* __restrict__ v,
+                                   double* __restrict__ q) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t hsh = (uint32_t)(i * 2654435761ull);
+    v[i] = invd[i] != 0.0 ? 1.0 + (double)(hsh >> 8) * (1.0 / 16777216.0) : 0.0;
+    q[i] = 0.0;
+  }
+}
+
+// w = D^-1 q (q cleared), ||w||^2 reduced by the last block into *res
+__global__ void __launch_bounds__(256) mg_pow_step_kernel(int64_t n, double* __restrict__ q,
+                                                          const double* __restrict__ invd, double* __restrict__ w,
+                                                          double* __restrict__ part, unsigned* __restrict__ cnt,
+                                                          double* __restrict__ res) {
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double wi = invd[i] * q[i];
+    q[i] = 0.0;
+    w[i] = wi;
+    s += wi * wi;
+  }
+  __shared__ int last;
+  s = block_sum(s);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s;
+    __threadfence();
+    last = (atomicAdd(cnt, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double t = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(part + i);
+    t = block_sum(t);
+    if (threadIdx.x == 0) {
+      *res = t;
+      *cnt = 0u;
+    }
+  }
+}
+
+// v = w / ||w||
+__global__ void mg_pow_norm_kernel(int64_t n, const double* __restrict__ w, const double* __restrict__ res,
+                                   double* __restrict__ v) {
+  const double sc = 1.0 / sqrt(__ldcg(res));
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = w[i] * sc;
+}
+
+__global__ void mg_pow_final_kernel(const double* __restrict__ res, double* __restrict__ lmax) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *lmax = 1.1 * sqrt(__ldcg(res));
+}
+
+int vec_grid(int64_t n) { return grid_for(n, 256, kMGBlocks); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+void mg_release(mto_handle h) {
+  for (auto& l : h->mg)
+    for (void* p : {(void*)l.gmap, (void*)l.K, (void*)l.mask, (void*)l.invd, (void*)l.x, (void*)l.b, (void*)l.q,
+                    (void*)l.d})
+      cudaFree(p);
+  h->mg.clear();
+  for (void* p : {(void*)h->mg_pidx, (void*)h->mg_pw, (void*)h->mg_rptr, (void*)h->mg_rnode, (void*)h->mg_rw,
+                  (void*)h->mg_btab, (void*)h->mg_v0, (void*)h->mg_q0, (void*)h->mg_d0, (void*)h->mg_Ainv,
+                  (void*)h->mg_lmax, (void*)h->mg_part, (void*)h->mg_cnt, (void*)h->mg_res})
+    cudaFree(p);
+  h->mg_pidx = nullptr;
+  h->mg_pw = h->mg_rw = h->mg_btab = h->mg_v0 = h->mg_q0 = h->mg_d0 = h->mg_Ainv = h->mg_lmax = nullptr;
+  h->mg_part = h->mg_res = nullptr;
+  h->mg_rptr = h->mg_rnode = nullptr;
+  h->mg_cnt = nullptr;
+  h->mg_ok = h->mg_valid = false;
+}
+
+// Level sizes, vertex maps and the level-0 <-> level-1 transfer tables (host, once per mesh).
+mto_status mg_setup(mto_handle h) {
+  mg_release(h);
+  int nx = h->nelx, ny = h->nely;
+  std::vector<std::pair<int, int>> dims{{nx, ny}};
+  while (nx % 2 == 0 && ny % 2 == 0 && 2LL * (nx + 1) * (ny + 1) > kCoarseTarget) {
+    nx /= 2;
+    ny /= 2;
+    dims.push_back({nx, ny});
+  }
+  const int64_t ncoarse = 2LL * (nx + 1) * (ny + 1);
+  if (ncoarse > kCoarseMax) {
+    h->mg_why = "multigrid needs mesh sides that halve down to a grid of at most 2048 DOFs (" +
+                std::to_string(nx) + " x " + std::to_string(ny) + " elements cannot be halved)";
+    return MTO_OK;
+  }
+  h->mg.resize(dims.size());
+  for (size_t l = 0; l < dims.size(); ++l) {
+    MGLevel& L = h->mg[l];
+    L.nx = dims[l].first;
+    L.ny = dims[l].second;
+    L.nel = L.nx * L.ny;
+    L.nv = (int64_t)(L.nx + 1) * (L.ny + 1);
+    L.n = 2 * L.nv;
+    std::vector<int> gm((size_t)4 * L.nel);
+    for (int e = 0; e < L.nel; ++e) {
+      const int ex = e % L.nx, ey = e / L.nx;
+      const int v0 = ey * (L.nx + 1) + ex;
+      gm[4 * e + 0] = v0;
+      gm[4 * e + 1] = v0 + 1;
+      gm[4 * e + 2] = v0 + L.nx + 1;
+      gm[4 * e + 3] = v0 + L.nx + 2;
+    }
+    MTO_TRY(mto_alloc(h, &L.gmap, gm.size()));
+    MTO_TRY(mto_cuda_check(h, cudaMemcpy(L.gmap, gm.data(), gm.size() * sizeof(int), cudaMemcpyHostToDevice), "upload"));
+    MTO_TRY(mto_alloc(h, &L.K, (size_t)40 * L.nel));
+    for (double** v : {&L.mask, &L.invd, &L.x, &L.b, &L.q, &L.d}) MTO_TRY(mto_alloc(h, v, L.n));
+    MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(L.q, 0, L.n * sizeof(double), h->stream), "memset"));
+  }
+
+  // bilinear weights of the four vertices at the GLL nodes of each order (node (a, b), x fastest)
+  std::vector<double> btab;
+  for (int p = 1; p <= kPMaxTab; ++p) {
+    h->mg_boff[p] = (int)btab.size();
+    double z[kPMaxTab + 2];
+    gll_nodes(p, z);
+    for (int b = 0; b <= p; ++b)
+      for (int a = 0; a <= p; ++a) {
+        const double s = 0.5 * (1.0 + z[a]), t = 0.5 * (1.0 + z[b]);
+        for (int V = 0; V < 4; ++V) btab.push_back(((V & 1) ? s : 1.0 - s) * ((V >> 1) ? t : 1.0 - t));
+      }
+  }
+  MTO_TRY(mto_alloc(h, &h->mg_btab, btab.size()));
+  MTO_TRY(mto_cuda_check(h, cudaMemcpy(h->mg_btab, btab.data(), btab.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
+
+  // prolongation level 1 -> 0: every global node takes the bilinear interpolant of the vertices
+  // of an element in which it is a free (unconstrained) local node
+  const int64_t nn = h->n_nodes;
+  std::vector<int> pidx((size_t)4 * nn, 0);
+  std::vector<double> pw((size_t)4 * nn, 0.0);
+  std::vector<char> seen(nn, 0);
+  for (int64_t e = 0; e < h->nel; ++e) {
+    const int p = h->p_host[e];
+    const int ex = (int)(e % h->nelx), ey = (int)(e / h->nelx);
+    const int v0 = ey * (h->nelx + 1) + ex;
+    const int vs[4] = {v0, v0 + 1, v0 + h->nelx + 1, v0 + h->nelx + 2};
+    for (int b = 0; b <= p; ++b)
+      for (int a = 0; a <= p; ++a) {
+        int64_t nodes[kConsMax];
+        double w[kConsMax];
+        if (local_node_map_public(h, e, a, b, nodes, w) != 1) continue;
+        const int64_t g = nodes[0];
+        if (seen[g]) continue;
+        seen[g] = 1;
+        const double* bw = btab.data() + h->mg_boff[p] + 4 * (b * (p + 1) + a);
+        for (int V = 0; V < 4; ++V) {
+          pidx[4 * g + V] = vs[V];
+          pw[4 * g + V] = bw[V];
+        }
+      }
+  }
+  for (int64_t g = 0; g < nn; ++g)
+    if (!seen[g]) return mto_fail(h, MTO_EINVAL, "mg_setup: a node belongs to no element as a free node");
+  // restriction: the transpose, by vertex (exact zero weights dropped)
+  const int64_t nv = h->mg[0].nv;
+  std::vector<int> rptr(nv + 1, 0);
+  for (int64_t g = 0; g < nn; ++g)
+    for (int V = 0; V < 4; ++V)
+      if (pw[4 * g + V] != 0.0) ++rptr[pidx[4 * g + V] + 1];
+  for (int64_t v = 0; v < nv; ++v) rptr[v + 1] += rptr[v];
+  std::vector<int> rnode(rptr[nv]);
+  std::vector<double> rw(rptr[nv]);
+  std::vector<int> fill(rptr.begin(), rptr.end() - 1);
+  for (int64_t g = 0; g < nn; ++g)
+    for (int V = 0; V < 4; ++V)
+      if (pw[4 * g + V] != 0.0) {
+        const int v = pidx[4 * g + V];
+        rnode[fill[v]] = (int)g;
+        rw[fill[v]] = pw[4 * g + V];
+        ++fill[v];
+      }
+  MTO_TRY(mto_alloc(h, &h->mg_pidx, pidx.size()));
+  MTO_TRY(mto_alloc(h, &h->mg_pw, pw.size()));
+  MTO_TRY(mto_alloc(h, &h->mg_rptr, rptr.size()));
+  MTO_TRY(mto_alloc(h, &h->mg_rnode, rnode.size()));
+  MTO_TRY(mto_alloc(h, &h->mg_rw, rw.size()));
+  MTO_TRY(mto_cuda_check(h, cudaMemcpy(h->mg_pidx, pidx.data(), pidx.size() * sizeof(int), cudaMemcpyHostToDevice), "upload"));
+  MTO_TRY(mto_cuda_check(h, cudaMemcpy(h->mg_pw, pw.data(), pw.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
+  MTO_TRY(mto_cuda_check(h, cudaMemcpy(h->mg_rptr, rptr.data(), rptr.size() * sizeof(int), cudaMemcpyHostToDevice), "upload"));
+  MTO_TRY(mto_cuda_check(h, cudaMemcpy(h->mg_rnode, rnode.data(), rnode.size() * sizeof(int), cudaMemcpyHostToDevice), "upload"));
+  MTO_TRY(mto_cuda_check(h, cudaMemcpy(h->mg_rw, rw.data(), rw.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
+
+  for (double** v : {&h->mg_v0, &h->mg_q0, &h->mg_d0}) MTO_TRY(mto_alloc(h, v, h->ndof));
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->mg_q0, 0, h->ndof * sizeof(double), h->stream), "memset"));
+  MTO_TRY(mto_alloc(h, &h->mg_Ainv, (size_t)ncoarse * ncoarse));
+  MTO_TRY(mto_alloc(h, &h->mg_lmax, h->mg.size() + 1));
+  MTO_TRY(mto_alloc(h, &h->mg_part, kMGBlocks));
+  MTO_TRY(mto_alloc(h, &h->mg_cnt, 8));
+  MTO_TRY(mto_alloc(h, &h->mg_res, 8));
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->mg_cnt, 0, 8 * sizeof(unsigned), h->stream), "memset"));
+  h->mg_ok = true;
+  h->mg_valid = false;
+  return MTO_OK;
+}
+
+// Supports on every level: level 1 takes the fine mask of the vertex DOFs (vertices come first
+// in the global numbering), level l+1 the mask of the coinciding level-l vertex.
+mto_status mg_set_masks(mto_handle h) {
+  if (!h->mg_ok) return MTO_OK;
+  std::vector<char> fixed(h->ndof, 0);
+  for (int64_t g : h->fixed_host) fixed[g] = 1;
+  std::vector<double> m(h->mg[0].n);
+  for (int64_t i = 0; i < h->mg[0].n; ++i) m[i] = fixed[i] ? 0.0 : 1.0;
+  for (size_t l = 0; l < h->mg.size(); ++l) {
+    const MGLevel& L = h->mg[l];
+    if (l > 0) {
+      const MGLevel& F = h->mg[l - 1];
+      std::vector<double> mc(L.n);
+      for (int J = 0; J <= L.ny; ++J)
+        for (int I = 0; I <= L.nx; ++I) {
+          const int64_t V = (int64_t)J * (L.nx + 1) + I, v = (int64_t)(2 * J) * (F.nx + 1) + 2 * I;
+          mc[2 * V] = m[2 * v];
+          mc[2 * V + 1] = m[2 * v + 1];
+        }
+      m.swap(mc);
+    }
+    MTO_TRY(mto_cuda_check(h, cudaMemcpy(L.mask, m.data(), L.n * sizeof(double), cudaMemcpyHostToDevice), "upload"));
+  }
+  h->mg_valid = false;
+  return MTO_OK;
+}
+
+namespace {
+
+// lmax of D^-1 A on one level by power iteration (level < 0: the fine operator)
+mto_status mg_power(mto_handle h, int level, double* lmax_out) {
+  const bool fine = level < 0;
+  const int64_t n = fine ? h->ndof : h->mg[level].n;
+  const double* invd = fine ? h->invd64 : h->mg[level].invd;
+  double* v = fine ? h->mg_v0 : h->mg[level].x;
+  double* q = fine ? h->mg_q0 : h->mg[level].q;
+  double* w = fine ? h->mg_d0 : h->mg[level].d;
+  const int grd = vec_grid(n);
+  mg_pow_init_kernel<<<grd, 256, 0, h->stream>>>(n, invd, v, q);
+  MTO_TRY(mto_after_launch(h, "mg_pow_init_kernel"));
+  for (int it = 0; it < kPowerIts; ++it) {
+    if (fine) MTO_TRY(apply_fine(h, v, q, nullptr));
+    else MTO_TRY(apply_q1(h, h->mg[level], v, q, nullptr));
+    mg_pow_step_kernel<<<grd, 256, 0, h->stream>>>(n, q, invd, w, h->mg_part, h->mg_cnt, h->mg_res);
+    MTO_TRY(mto_after_launch(h, "mg_pow_step_kernel"));
+    if (it + 1 < kPowerIts) {
+      mg_pow_norm_kernel<<<grd, 256, 0, h->stream>>>(n, w, h->mg_res, v);
+      MTO_TRY(mto_after_launch(h, "mg_pow_norm_kernel"));
+    }
+  }
+  mg_pow_final_kernel<<<1, 32, 0, h->stream>>>(h->mg_res, lmax_out);
+  return mto_after_launch(h, "mg_pow_final_kernel");
+}
+
+}  // namespace
+
+// Galerkin operators of every level, diagonals, Chebyshev bounds and the coarsest inverse, for the
+// element matrices of the last build (lazily, at the first multigrid solve after a build).
+mto_status mg_build(mto_handle h) {
+  if (!h->mg_ok) return mto_fail(h, MTO_EINVAL, h->mg_why.empty() ? "multigrid unavailable" : h->mg_why);
+  {
+  TimedScope ts(h, F_PRECOND);
+  MGLevel& L1 = h->mg[0];
+  for (int p = 1; p <= MTO_P_MAX; ++p) {
+    const PClass& c = h->pc[p];
+    if (c.n == 0) continue;
+    const double* B = h->mg_btab + h->mg_boff[p];
+    const double* K64 = c.K64;   // both builds keep the FP64 matrices
+    const int grd = (c.n + 127) / 128;
+    switch (p) {
+      case 1: mg_galerkin_p_kernel<1><<<grd, 128, 0, h->stream>>>(c.n, c.elem, c.L, K64, c.K32, c.K32lo, B, L1.K); break;
+      case 2: mg_galerkin_p_kernel<2><<<grd, 128, 0, h->stream>>>(c.n, c.elem, c.L, K64, c.K32, c.K32lo, B, L1.K); break;
+      case 3: mg_galerkin_p_kernel<3><<<grd, 128, 0, h->stream>>>(c.n, c.elem, c.L, K64, c.K32, c.K32lo, B, L1.K); break;
+      case 4: mg_galerkin_p_kernel<4><<<grd, 128, 0, h->stream>>>(c.n, c.elem, c.L, K64, c.K32, c.K32lo, B, L1.K); break;
+      case 5: mg_galerkin_p_kernel<5><<<grd, 128, 0, h->stream>>>(c.n, c.elem, c.L, K64, c.K32, c.K32lo, B, L1.K); break;
+      case 6: mg_galerkin_p_kernel<6><<<grd, 128, 0, h->stream>>>(c.n, c.elem, c.L, K64, c.K32, c.K32lo, B, L1.K); break;
+    }
+    MTO_TRY(mto_after_launch(h, "mg_galerkin_p_kernel"));
+  }
+  for (size_t l = 1; l < h->mg.size(); ++l) {
+    const MGLevel& F = h->mg[l - 1];
+    MGLevel& C = h->mg[l];
+    mg_galerkin_h_kernel<<<(C.nel + 127) / 128, 128, 0, h->stream>>>(C.nx, C.ny, F.nx, F.K, C.K);
+    MTO_TRY(mto_after_launch(h, "mg_galerkin_h_kernel"));
+  }
+  for (auto& L : h->mg) {
+    MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(L.invd, 0, L.n * sizeof(double), h->stream), "memset"));
+    mg_diag_kernel<<<(L.nel + 127) / 128, 128, 0, h->stream>>>(L.nel, L.gmap, L.K, L.invd);
+    MTO_TRY(mto_after_launch(h, "mg_diag_kernel"));
+    mg_invd_kernel<<<vec_grid(L.n), 256, 0, h->stream>>>(L.n, L.mask, L.invd);
+    MTO_TRY(mto_after_launch(h, "mg_invd_kernel"));
+    MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(L.q, 0, L.n * sizeof(double), h->stream), "memset"));
+  }
+  // coarsest: dense inverse
+  const MGLevel& C = h->mg.back();
+  const int N = (int)C.n;
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->mg_Ainv, 0, sizeof(double) * N * N, h->stream), "memset"));
+  mg_dense_assemble_kernel<<<(C.nel + 127) / 128, 128, 0, h->stream>>>(C.nel, N, C.gmap, C.K, h->mg_Ainv);
+  MTO_TRY(mto_after_launch(h, "mg_dense_assemble_kernel"));
+  mg_dense_fix_kernel<<<vec_grid((int64_t)N * N), 256, 0, h->stream>>>(N, C.mask, h->mg_Ainv);
+  MTO_TRY(mto_after_launch(h, "mg_dense_fix_kernel"));
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->flags + 6, 0, sizeof(int), h->stream), "memset"));
+  mg_gauss_jordan_kernel<<<1, 1024, N * sizeof(double), h->stream>>>(N, h->mg_Ainv, h->flags + 6);
+  MTO_TRY(mto_after_launch(h, "mg_gauss_jordan_kernel"));
+  }
+  // Chebyshev bounds: fine level first, then every smoothed Q1 level
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->mg_q0, 0, h->ndof * sizeof(double), h->stream), "memset"));
+  MTO_TRY(mg_power(h, -1, h->mg_lmax));
+  for (size_t l = 0; l + 1 < h->mg.size(); ++l) MTO_TRY(mg_power(h, (int)l, h->mg_lmax + 1 + l));
+  for (auto& L : h->mg) MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(L.q, 0, L.n * sizeof(double), h->stream), "memset"));
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->mg_q0, 0, h->ndof * sizeof(double), h->stream), "memset"));
+  int err = 0;
+  MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->host_flags + 8, h->flags + 6, sizeof(int), cudaMemcpyDeviceToHost,
+                                            h->stream), "copy"));
+  MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "mg_build"));
+  err = h->host_flags[8];
+  if (err) return mto_fail(h, MTO_ENAN, "mg_build: coarsest operator not positive definite");
+  h->mg_valid = true;
+  return MTO_OK;
+}
+
+// z = M^-1 r: one V-cycle.  Level-0 vectors: b = r, x = z, q = mg_q0 (A x, kept zero between
+// uses), d = mg_d0 (Chebyshev direction, then the residual).
+mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const int* done) {
+  const int nl = (int)h->mg.size();
+  const int k = degree;
+  auto smooth = [&](int lev, const double* b, double* x, double* q, double* d, const double* invd, int64_t n,
+                    bool pre) -> mto_status {
+    const double* lm = h->mg_lmax + (lev + 1);
+    const int grd = vec_grid(n);
+    for (int s = 0; s < k; ++s) {
+      const bool skip_apply = pre && s == 0;   // x = 0: A x = 0
+      if (!skip_apply) {
+        if (lev < 0) MTO_TRY(apply_fine(h, x, q, done));
+        else {
+          TimedScope ts(h, F_PRECOND);
+          MTO_TRY(apply_q1(h, h->mg[lev], x, q, done));
+        }
+      }
+      TimedScope ts(h, F_PRECOND);
+      mg_cheb_kernel<<<grd, 256, 0, h->stream>>>(n, b, q, invd, x, d, lm, s, pre && s == 0, done);
+      MTO_TRY(mto_after_launch(h, "mg_cheb_kernel"));
+    }
+    return MTO_OK;
+  };
+  // level 0 pre-smoothing and residual
+  MTO_TRY(smooth(-1, r, z, h->mg_q0, h->mg_d0, h->invd64, h->ndof, true));
+  MTO_TRY(apply_fine(h, z, h->mg_q0, done));
+  {
+    TimedScope ts(h, F_PRECOND);
+    mg_residual_kernel<<<vec_grid(h->ndof), 256, 0, h->stream>>>(h->ndof, r, h->mg_q0, h->invd64, h->mg_d0, done);
+    MTO_TRY(mto_after_launch(h, "mg_residual_kernel"));
+    MGLevel& L1 = h->mg[0];
+    mg_restrict0_kernel<<<vec_grid(L1.nv), 256, 0, h->stream>>>(L1.nv, h->mg_rptr, h->mg_rnode, h->mg_rw, h->mg_d0,
+                                                               L1.mask, L1.b, done);
+    MTO_TRY(mto_after_launch(h, "mg_restrict0_kernel"));
+  }
+  // Q1 levels down
+  for (int l = 0; l < nl - 1; ++l) {
+    MGLevel& L = h->mg[l];
+    MGLevel& C = h->mg[l + 1];
+    MTO_TRY(smooth(l, L.b, L.x, L.q, L.d, L.invd, L.n, true));
+    TimedScope ts(h, F_PRECOND);
+    MTO_TRY(apply_q1(h, L, L.x, L.q, done));
+    mg_residual_kernel<<<vec_grid(L.n), 256, 0, h->stream>>>(L.n, L.b, L.q, L.invd, L.d, done);
+    MTO_TRY(mto_after_launch(h, "mg_residual_kernel"));
+    mg_restrict_h_kernel<<<vec_grid(C.nv), 256, 0, h->stream>>>(C.nx, C.ny, L.nx, L.ny, L.d, C.mask, C.b, done);
+    MTO_TRY(mto_after_launch(h, "mg_restrict_h_kernel"));
+  }
+  {
+    TimedScope ts(h, F_PRECOND);
+    const MGLevel& C = h->mg.back();
+    mg_coarse_solve_kernel<<<(int)((C.n * 32 + 255) / 256), 256, 0, h->stream>>>((int)C.n, h->mg_Ainv, C.b, C.x,
+                                                                                   done);
+    MTO_TRY(mto_after_launch(h, "mg_coarse_solve_kernel"));
+  }
+  // up
+  for (int l = nl - 2; l >= 0; --l) {
+    MGLevel& L = h->mg[l];
+    const MGLevel& C = h->mg[l + 1];
+    {
+      TimedScope ts(h, F_PRECOND);
+      mg_prolong_h_kernel<<<vec_grid(L.nv), 256, 0, h->stream>>>(C.nx, L.nx, L.ny, C.x, L.mask, L.x, done);
+      MTO_TRY(mto_after_launch(h, "mg_prolong_h_kernel"));
+    }
+    MTO_TRY(smooth(l, L.b, L.x, L.q, L.d, L.invd, L.n, false));
+  }
+  {
+    TimedScope ts(h, F_PRECOND);
+    mg_prolong0_kernel<<<vec_grid(h->n_nodes), 256, 0, h->stream>>>(h->n_nodes, h->mg_pidx, h->mg_pw, h->mg[0].x,
+                                                                    h->invd64, z, done);
+    MTO_TRY(mto_after_launch(h, "mg_prolong0_kernel"));
+  }
+  return smooth(-1, r, z, h->mg_q0, h->mg_d0, h->invd64, h->ndof, false);
+}
+
+}  // namespace mto

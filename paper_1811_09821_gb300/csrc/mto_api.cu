@@ -180,6 +180,7 @@ void release_mesh(mto_handle h) {
     q = QRTab();
   }
   free_dev(h, h->slot_d);
+  mg_release(h);
   for (double** v : {&h->diag64, &h->invd64, &h->r64, &h->p64, &h->s64, &h->u64, &h->w64, &h->cg_part})
     free_dev(h, *v);
   for (float** v : {&h->invd32, &h->x32, &h->r32, &h->p32, &h->s32, &h->u32, &h->w32}) free_dev(h, *v);
@@ -266,6 +267,10 @@ int local_node_map(mto_handle h, int64_t e, int a, int b, int64_t* nodes, double
 }
 
 }  // namespace
+
+int mto::local_node_map_public(mto_handle h, int64_t e, int a, int b, int64_t* nodes, double* w) {
+  return local_node_map(h, e, a, b, nodes, w);
+}
 
 extern "C" {
 
@@ -522,6 +527,8 @@ mto_status mto_setup(mto_handle h, int32_t nelx, int32_t nely, double hx, double
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->flags, 0, 64 * sizeof(int), h->stream), "memset"));
   MTO_TRY(build_tables(h));
   MTO_TRY(build_sens_tables(h));
+  MTO_TRY(mg_setup(h));
+  MTO_TRY(mg_set_masks(h));
   MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "mto_setup"));
   h->have_setup = true;
   if (ndof) *ndof = h->ndof;
@@ -549,6 +556,7 @@ mto_status mto_set_supports(mto_handle h, const int64_t* fixed, int64_t n) {
   }
   h->have_supports = true;
   h->schwarz_valid = false;
+  MTO_TRY(mg_set_masks(h));
   if (h->built_precision >= 0) MTO_TRY(build_diagonal(h, h->built_precision));
   return MTO_OK;
 }
@@ -619,6 +627,7 @@ mto_status mto_build_elements(mto_handle h, const double* rho, const mto_materia
   cudaSetDevice(h->device);
   h->built_precision = precision;
   h->schwarz_valid = false;
+  h->mg_valid = false;
   MTO_TRY(build_elements(h, rho, mat, precision));
   if (h->have_supports) MTO_TRY(build_diagonal(h, precision));
   return MTO_OK;
@@ -641,10 +650,12 @@ mto_status mto_solve(mto_handle h, const double* f, double* u, const mto_solve_o
   if (!h || !h->have_setup || !f || !u || !opts) return mto_fail(h, MTO_EINVAL, "mto_solve: bad arguments");
   if (!h->have_supports) return mto_fail(h, MTO_EINVAL, "mto_solve: call mto_set_supports first");
   if (h->built_precision < 0) return mto_fail(h, MTO_EINVAL, "mto_solve: call mto_build_elements first");
-  if (opts->precision == MTO_MIXED && h->built_precision != MTO_MIXED)
-    return mto_fail(h, MTO_EINVAL, "mto_solve: the mixed solve needs the split-precision (MTO_MIXED) build");
+  if (opts->precision != MTO_FP64 && opts->precision != MTO_MIXED && opts->precision != MTO_MIXED32)
+    return mto_fail(h, MTO_EINVAL, "mto_solve: bad precision");
+  if (opts->precision != MTO_FP64 && h->built_precision != MTO_MIXED)
+    return mto_fail(h, MTO_EINVAL, "mto_solve: the mixed solves need the split-precision (MTO_MIXED) build");
   if (!(opts->rtol > 0) || opts->max_iter < 1 || opts->check_every < 1 ||
-      (opts->precond != MTO_PREC_JACOBI && opts->precond != MTO_PREC_SCHWARZ))
+      (opts->precond != MTO_PREC_JACOBI && opts->precond != MTO_PREC_SCHWARZ && opts->precond != MTO_PREC_MG))
     return mto_fail(h, MTO_EINVAL, "mto_solve: bad options");
   cudaSetDevice(h->device);
   return solve(h, f, u, opts, iters, relres);

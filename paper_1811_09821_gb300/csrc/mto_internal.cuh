@@ -48,8 +48,8 @@ struct PClass {
   int* gmap = nullptr;   // [n][(p+1)^2] global node id, or -(1 + constraint index)
   int2* dpos = nullptr;  // [P] row positions of packed entry c (second one or -1)
   int* posc = nullptr;   // [L] packed entry stored at each row position
-  double* K64 = nullptr;   // FP64 path
-  float* K32 = nullptr;    // split-precision pair (mixed path): hi = fl32(K_e) ...
+  double* K64 = nullptr;   // FP64 matrices (both builds)
+  float* K32 = nullptr;    // split-precision pair (mixed build only): hi = fl32(K_e) ...
   float* K32lo = nullptr;  // ... and lo = fl32(K_e - hi), same layout
   double* B64 = nullptr;   // element-block preconditioner (K_e + Delta_e)^-1, same layouts
   float* B32 = nullptr;
@@ -89,12 +89,26 @@ struct Timing {
   double ms[F_COUNT] = {0};
 };
 
+// One bilinear (Q1) level of the multigrid hierarchy on an nx x ny grid of elements.  Element
+// matrices are FP64 rows of the circulant-diagonal layout (n_e = 8, L = 40), so the element
+// operator kernel of order 1 applies them.
+struct MGLevel {
+  int nx = 0, ny = 0, nel = 0;
+  int64_t nv = 0, n = 0;           // vertices, DOFs
+  int* gmap = nullptr;             // [nel][4] vertex ids (x fastest)
+  double* K = nullptr;             // [nel][40]
+  double* mask = nullptr;          // [n] 0 on supported DOFs, else 1
+  double* invd = nullptr;          // [n] inverse diagonal, 0 on supported DOFs
+  double *x = nullptr, *b = nullptr, *q = nullptr, *d = nullptr;   // [n] cycle vectors
+};
+
 // A captured chunk of CG iterations, replayed until convergence.
 struct GraphKey {
   size_t tsize;
   const void* x;
   const void* r;
-  bool schwarz;
+  int pc;                  // preconditioner (MTO_PREC_*)
+  int deg;                 // multigrid smoothing degree
   int nrm;
   const double* ref;
   double tol2;
@@ -102,7 +116,7 @@ struct GraphKey {
   bool timing;
   int prec;
   bool operator==(const GraphKey& o) const {
-    return tsize == o.tsize && x == o.x && r == o.r && schwarz == o.schwarz && nrm == o.nrm && ref == o.ref &&
+    return tsize == o.tsize && x == o.x && r == o.r && pc == o.pc && deg == o.deg && nrm == o.nrm && ref == o.ref &&
            tol2 == o.tol2 && chunk == o.chunk && timing == o.timing && prec == o.prec;
   }
 };
@@ -171,6 +185,24 @@ struct mto_handle_s {
   unsigned* cg_cnt = nullptr;                  // [64]
   int* cg_base = nullptr;                      // first iteration of the running chunk
   bool schwarz_valid = false;
+  bool inner_split = false;                    // operator applies use the split pair (mixed inner solves)
+  // multigrid preconditioner: levels 1.. (Q1), fine-level transfer tables and work vectors
+  std::vector<mto::MGLevel> mg;
+  bool mg_ok = false, mg_valid = false;
+  std::string mg_why;                          // why no hierarchy exists (mesh does not coarsen)
+  int* mg_pidx = nullptr;                      // [n_nodes][4] Q1 vertices of each fine node
+  double* mg_pw = nullptr;                     // [n_nodes][4] their bilinear weights
+  int* mg_rptr = nullptr;                      // [nv + 1] restriction CSR by vertex
+  int* mg_rnode = nullptr;
+  double* mg_rw = nullptr;
+  double* mg_btab = nullptr;                   // bilinear weights at the GLL nodes, per order
+  int mg_boff[mto::kPMaxTab + 2] = {0};
+  double *mg_v0 = nullptr, *mg_q0 = nullptr, *mg_d0 = nullptr;   // [ndof] fine-level scratch
+  double* mg_Ainv = nullptr;                   // coarsest-level dense inverse [N][N]
+  double* mg_lmax = nullptr;                   // [levels] Chebyshev upper bounds
+  double* mg_part = nullptr;                   // reduction partials
+  unsigned* mg_cnt = nullptr;
+  double* mg_res = nullptr;
   int build_path = MTO_BUILD_SIMT;
   bool use_graphs = true;
   std::vector<mto::GraphEntry*> graphs;
@@ -371,12 +403,22 @@ mto_status build_elements(mto_handle h, const double* rho, const mto_material* m
 mto_status build_diagonal(mto_handle h, int precision);
 mto_status element_matrix(mto_handle h, int64_t e, double* host_out);
 mto_status build_schwarz(mto_handle h);                                 // element-block preconditioner
+// mto_api.cu: (node, weight) list of local node (a, b) of element e (minimum-rule constraints)
+int local_node_map_public(mto_handle h, int64_t e, int a, int b, int64_t* nodes, double* w);
+// mg.cu (multigrid preconditioner)
+mto_status mg_setup(mto_handle h);                                      // hierarchy, transfer tables
+mto_status mg_set_masks(mto_handle h);                                  // supports on every level
+mto_status mg_build(mto_handle h);                                      // Galerkin operators, bounds
+mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const int* done);
+void mg_release(mto_handle h);
 // tc.cu
 mto_status tc_tables(mto_handle h);
 mto_status tc_build_class(mto_handle h, const BClass& b, const double* rho, const mto_material* m, int precision);
 int ebe_blocks(int p, int n);                                           // grid of one operator launch
 // apply.cu
 mto_status apply64(mto_handle h, const double* x, double* y);        // y += K x (FP64 vectors)
+mto_status apply_fine(mto_handle h, const double* x, double* y, const int* done);   // same, early exit
+mto_status apply_q1(mto_handle h, const MGLevel& l, const double* x, double* y, const int* done);
 mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts* o, int32_t* iters,
                  double* relres);
 // sens.cu

@@ -10,14 +10,15 @@
 // sum_i a_i 2^-7i and K0/tau = sum_j b_j 2^-7j with integer a_i in [0, 127], b_j in [-127, 127]
 // (exact in BF16).  Every slice product a_i . b_j over K <= 64 subcells is an integer below 2^20,
 // and all pairs of one level g = i + j share the weight 2^-7g: each level accumulates its (at most
-// 7) slice GEMMs in one FP32 TMEM accumulator exactly (sums below 2^23).  Levels g = 2..8 are
-// kept (49 bits of the row/column scale); the epilogue adds the levels from the smallest with
-// FP32 TwoSum into the hi/lo pair and rescales by sigma_e tau_pos (powers of two, exact).
+// 7) slice GEMMs in one FP32 TMEM accumulator exactly (sums below 2^23).  Levels g = 2..9 are
+// kept (the dropped levels weigh below 2^-47 of the row/column scale); the epilogue adds the
+// levels from the smallest in FP64 (the FP64 matrices) and, for the mixed build, with FP32
+// TwoSum into the hi/lo pair, and rescales by sigma_e tau_pos (powers of two, exact).
 //
 // One CTA (4 warps) per 128 elements: the A slices (7 x 128 x K) are formed in shared memory from
 // rho once; the CTA then walks the N tiles of 64 positions: B slices copied to shared memory, one
-// thread issues the 28 x (K/16) tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = 128, N = 64)
-// into 7 level accumulators (448 TMEM columns), commits to an mbarrier, and all threads read
+// thread issues the 34 x (K/16) tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = 128, N = 64)
+// into 8 level accumulators (all 512 TMEM columns), commits to an mbarrier, and all threads read
 // their row back with tcgen05.ld and store 64 consecutive entries of their element's row.
 // Operands use the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix).
 // Every wait is bounded: on expiry the kernel records an error word and skips the tile.
@@ -33,8 +34,8 @@ constexpr int kTM = 128;        // elements per CTA (MMA M)
 constexpr int kTN = 64;         // positions per N tile (MMA N)
 constexpr int kSlices = 7;      // slices per operand
 constexpr int kSliceBits = 7;
-constexpr int kLevels = 7;      // levels g = i + j = 2..8
-constexpr int kTmemCols = 512;  // 7 x 64 = 448 used
+constexpr int kLevels = 8;      // levels g = i + j = 2..9
+constexpr int kTmemCols = 512;  // 8 x 64 = 512 used
 constexpr unsigned kSpinLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -274,10 +275,12 @@ __global__ void __launch_bounds__(128, 1) tc_build_kernel(
 #pragma unroll 1
     for (int ch = 0; ch < kTN / 16; ++ch) {
       float sh[16], slo[16];
+      double sd[16];
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         sh[c] = 0.0f;
         slo[c] = 0.0f;
+        sd[c] = 0.0;
       }
 #pragma unroll 1
       for (int g = kLevels - 1; g >= 0; --g) {
@@ -286,7 +289,11 @@ __global__ void __launch_bounds__(128, 1) tc_build_kernel(
         tmem_wait_ld();
         const float wgt = ldexpf(1.0f, -kSliceBits * (g + 2));
 #pragma unroll
-        for (int c = 0; c < 16; ++c) two_sum(sh[c], slo[c], __uint_as_float(v[c]) * wgt);
+        for (int c = 0; c < 16; ++c) {
+          const float t = __uint_as_float(v[c]) * wgt;   // exact: integer below 2^23 times 2^-7g
+          sd[c] += (double)t;                             // FP64 sum of the levels (the K64 output)
+          if (Kh) two_sum(sh[c], slo[c], t);              // FP32 pair (the split output)
+        }
       }
       if (act) {
         const int pos0 = tile * kTN + ch * 16;
@@ -295,12 +302,11 @@ __global__ void __launch_bounds__(128, 1) tc_build_kernel(
           const int pos = pos0 + c;
           if (pos >= L) break;
           const float sc = sig * __ldg(tau + pos);
-          const float hi = sh[c] + slo[c];
-          const float lo = slo[c] - (hi - sh[c]);
           const size_t o = (size_t)sl * L + pos;
-          if (K64) {
-            K64[o] = (double)(hi * sc) + (double)(lo * sc);
-          } else {
+          K64[o] = sd[c] * (double)sc;
+          if (Kh) {
+            const float hi = sh[c] + slo[c];
+            const float lo = slo[c] - (hi - sh[c]);
             Kh[o] = hi * sc;
             Kl[o] = lo * sc;
           }
@@ -354,7 +360,7 @@ mto_status tc_build_class(mto_handle h, const BClass& b, const double* rho, cons
   const int grid = (b.n + kTM - 1) / kTM;
   tc_build_kernel<<<grid, 128, smem, h->stream>>>(
       b.n, b.S, kpad, c.L, ntile, b.elem, b.slot, h->design_off_d, rho, m->E0, m->Emin, m->q, b.tcB, b.tcTau,
-      precision == MTO_FP64 ? c.K64 : nullptr, c.K32, c.K32lo, h->flags + 4);
+      c.K64, precision == MTO_MIXED ? c.K32 : nullptr, precision == MTO_MIXED ? c.K32lo : nullptr, h->flags + 4);
   return mto_after_launch(h, "tc_build_kernel");
 }
 
