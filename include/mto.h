@@ -248,10 +248,12 @@ mto_status mto_map_update(mto_handle h, const double* gamma_a, const double* gam
 mto_status mto_oc_update(mto_handle h, const double* rho, const double* dc, double volfrac,
                          double move, double eta, double* rho_new, double* lambda);
 
-/* Kernel-family timing for benchmarks.  When enabled, the launches of each family below are
- * bracketed by CUDA events recorded on the handle's stream; mto_timing_read synchronises the
- * stream and returns the number of kernel launches and their summed device time (ms) since the
- * last mto_timing_enable (which resets the counters).  Families: */
+/* Kernel-family timing for benchmarks.  enable = 1: the launches of each family below are
+ * bracketed by CUDA events recorded on the handle's stream; enable = 2 (sampled, low overhead):
+ * only the first element-operator launch of every captured chunk of PCG iterations is bracketed;
+ * 0: off.  mto_timing_read synchronises the stream and returns the number of timed kernel
+ * launches and their summed device time (ms) since the last mto_timing_enable (which resets the
+ * counters).  Families: */
 #define MTO_TIME_APPLY32 0   /* split-precision operator on FP32 vectors (mixed inner PCG) */
 #define MTO_TIME_APPLY64 1   /* FP64 element-by-element operator (plain FP64 path) */
 #define MTO_TIME_BUILD 2     /* step (a): subcell tables and element matrices */

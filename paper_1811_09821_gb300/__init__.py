@@ -261,7 +261,9 @@ class Handle:
         self._check(self.L.mto_set_build_path(self.h, path))
 
     def timing_enable(self, on=True):
-        self._check(self.L.mto_timing_enable(self.h, int(bool(on))))
+        """on: True (every kernel family), "sampled" (the first operator launch of each chunk of
+        PCG iterations only: low overhead) or False."""
+        self._check(self.L.mto_timing_enable(self.h, 2 if on == "sampled" else int(bool(on))))
 
     def timing_read(self):
         """{family: (kernel launches, device ms)} since the last timing_enable."""

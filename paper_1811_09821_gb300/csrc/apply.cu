@@ -597,7 +597,10 @@ mto_status cg_iteration(mto_handle h, const CGVecs<T>& v, int pc, int deg, int n
   const bool jac = pc == MTO_PREC_JACOBI;
   const int ng = pc == MTO_PREC_SCHWARZ ? nc : 1;
   ConvTest none{};
-  MTO_TRY(apply_all<T>(h, 0, v.p, v.q, kDel + par, h->flags, none));
+  h->timing.sample = local == 0;   // sampled timing: the first operator launch of every chunk
+  const mto_status sa = apply_all<T>(h, 0, v.p, v.q, kDel + par, h->flags, none);
+  h->timing.sample = false;
+  MTO_TRY(sa);
   {
     TimedScope ts(h, F_VECTOR);
     if (!jac)
@@ -667,7 +670,8 @@ mto_status run_cg(mto_handle h, T* x, T* r, int pc, int deg, int nrm, const doub
   const bool use_graph = h->use_graphs;
   GraphEntry* ge = nullptr;
   if (use_graph) {
-    GraphKey key{sizeof(T), (const void*)x, (const void*)r, pc, deg, nrm, ref, tol2, chunk, h->timing.on,
+    GraphKey key{sizeof(T), (const void*)x, (const void*)r, pc, deg, nrm, ref, tol2, chunk,
+                 h->timing.on ? (h->timing.sampled ? 2 : 1) : 0,
                  2 * h->built_precision + (h->inner_split ? 1 : 0)};
     ge = find_graph(h, key);
     if (!ge) {
@@ -773,6 +777,10 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
   const int grd = grid_for(n, 256, 152 * 4);
   const int pc = o->precond;
   const int deg = o->mg_degree > 0 ? o->mg_degree : 4;
+  if (pc == MTO_PREC_SCHWARZ && h->n_cons > 0)
+    return mto_fail(h, MTO_EINVAL,
+                    "mto_solve: the element-block Schwarz preconditioner is limited to meshes without order "
+                    "jumps (hanging nodes); use MTO_PREC_MG or MTO_PREC_JACOBI");
   if (pc == MTO_PREC_SCHWARZ && !h->schwarz_valid) MTO_TRY(build_schwarz(h));
   if (pc == MTO_PREC_MG) {
     if (o->precision == MTO_MIXED32)
@@ -814,10 +822,16 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
     } else if (o->precision == MTO_MIXED) {
       // refinement step: K_split d = r with FP64 vectors (d in s64, from zero), to inner_rtol
       // relative to the current residual (h->red[0] / h->red[2]), then u += d
+      // (asking no more than a third of the remaining reduction: the last step stops early)
+      const double need = o->rtol * std::sqrt(ff / rr) / 3.0;
+      const double tol_i = need > itol ? (need < 0.1 ? need : 0.1) : itol;
+      // the stopping threshold goes to the device (h->red[6]) so the captured graphs stay valid
+      h->host_pinned[33] = tol_i * tol_i * h->host_pinned[nrm ? 2 : 0];
+      MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->red + 6, h->host_pinned + 33, sizeof(double),
+                                                cudaMemcpyHostToDevice, h->stream), "copy"));
       h->inner_split = true;
       MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->s64, 0, sizeof(double) * n, h->stream), "memset"));
-      const mto_status si = run_cg<double>(h, h->s64, h->r64, pc, deg, nrm, h->red + (nrm ? 2 : 0), itol * itol,
-                                           budget, chunk, &it);
+      const mto_status si = run_cg<double>(h, h->s64, h->r64, pc, deg, nrm, h->red + 6, 1.0, budget, chunk, &it);
       h->inner_split = false;
       MTO_TRY(si);
       TimedScope ts(h, F_VECTOR);

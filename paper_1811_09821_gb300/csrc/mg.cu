@@ -33,6 +33,7 @@ constexpr int kCoarseTarget = 256;    // stop coarsening at or below this many D
 constexpr int kCoarseMax = 2048;      // largest coarsest grid for the dense inverse
 constexpr double kChebRatio = 30.0;   // lmin = lmax / ratio
 constexpr int kPowerIts = 30;
+constexpr int kCoarseDegree = 2;      // Chebyshev degree on the Q1 levels (the fine level: the option)
 constexpr int kMGBlocks = 152 * 4;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -720,9 +721,9 @@ mto_status mg_build(mto_handle h) {
 // uses), d = mg_d0 (Chebyshev direction, then the residual).
 mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const int* done) {
   const int nl = (int)h->mg.size();
-  const int k = degree;
   auto smooth = [&](int lev, const double* b, double* x, double* q, double* d, const double* invd, int64_t n,
                     bool pre) -> mto_status {
+    const int k = lev < 0 ? degree : kCoarseDegree;
     const double* lm = h->mg_lmax + (lev + 1);
     const int grd = vec_grid(n);
     for (int s = 0; s < k; ++s) {

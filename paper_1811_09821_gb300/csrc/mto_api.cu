@@ -52,7 +52,7 @@ cudaEvent_t take_event(mto_handle h) {
 }  // namespace
 
 TimedScope::TimedScope(mto_handle h_, int fam_) : h(h_), fam(fam_), launches0(h_->launches) {
-  if (!h->timing.on) return;
+  if (!h->timing.on || (h->timing.sampled && !h->timing.sample)) return;
   if (!h->timing.capture_list && h->timing.pending.size() > 4096) {
     cudaStreamSynchronize(h->stream);
     timing_harvest(h);
@@ -730,6 +730,7 @@ mto_status mto_timing_enable(mto_handle h, int32_t enable) {
     h->timing.launches[f] = 0;
   }
   h->timing.on = enable != 0;
+  h->timing.sampled = enable == 2;
   return MTO_OK;
 }
 

@@ -81,6 +81,8 @@ enum Family { F_APPLY32 = 0, F_APPLY64 = 1, F_BUILD = 2, F_SENS = 3, F_INDICATOR
 
 struct Timing {
   bool on = false;
+  bool sampled = false;   // record only the operator launches marked by `sample` (low overhead)
+  bool sample = false;
   struct Pending { int fam; int launches; cudaEvent_t a, b; };
   std::vector<cudaEvent_t> pool;
   std::vector<Pending> pending;
@@ -113,7 +115,7 @@ struct GraphKey {
   const double* ref;
   double tol2;
   int chunk;
-  bool timing;
+  int timing;
   int prec;
   bool operator==(const GraphKey& o) const {
     return tsize == o.tsize && x == o.x && r == o.r && pc == o.pc && deg == o.deg && nrm == o.nrm && ref == o.ref &&

@@ -113,20 +113,28 @@ def test_operator_matches_assembled_oracle(mto, name, build):
 @pytest.mark.parametrize("name", CASES)
 def test_tensor_core_build_matches_simt(mto, name):
     """The sliced tcgen05 build (d <= 8) and the FP64 CUDA-core build give the same element
-    matrices to ~1e-14 of each element's largest entry, in both storage precisions."""
+    matrices to 1e-13 of each element's largest entry (the slicing keeps ~49 bits of each operand
+    against the FP64 sum's 53; cancellation among the subcell terms amplifies both), and the mixed
+    solves on the two builds (FP64 matrices for the refinement residual, the split pair inside)
+    agree on C to 1e-9."""
     o = oracle_results(name)
     pr, m = o["pr"], o["mesh"]
     h, fixed, f, mat, rho = gpu_setup(mto, pr)
     rng = np.random.default_rng(5)
     sample = rng.choice(m.nel, min(m.nel, 48), replace=False)
     for build in (mto.MTO_FP64, mto.MTO_MIXED):
-        got = {}
+        got, C = {}, {}
         for path in (mto.BUILD_TENSOR, mto.BUILD_SIMT):
             h.set_build_path(path)
             h.build_elements(rho, mat, build)
             got[path] = [h.element_matrix(int(e), int(m.p[e])) for e in sample]
+            u = torch.zeros(h.ndof, dtype=torch.float64, device="cuda")
+            h.solve(f, u, precision=build, rtol=1e-10, norm=mto.NORM_JACOBI, max_iter=400000, precond=mto.PREC_MG)
+            C[path] = float(f @ u)
         for a, b in zip(got[mto.BUILD_TENSOR], got[mto.BUILD_SIMT]):
-            assert np.abs(a - b).max() <= 2e-14 * np.abs(b).max()
+            assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
+        assert abs(C[mto.BUILD_TENSOR] - C[mto.BUILD_SIMT]) <= 1e-9 * abs(C[mto.BUILD_SIMT])
+    h.set_build_path(mto.BUILD_SIMT)
     h.close()
 
 
@@ -144,6 +152,8 @@ PATHS = {"fp64": ("MTO_FP64", "MTO_FP64"), "mixed": ("MTO_MIXED", "MTO_MIXED"),
 def test_solve_and_sensitivity_parity(mto, name, path, precond):
     if path == "mixed32" and (name != "cantilever_20x10_p2_d4" or precond == "mg"):
         pytest.skip("FP32-vector inner solves are checked on the smooth-density case (Schwarz)")
+    if precond == "schwarz" and name.startswith("dp_"):
+        pytest.skip("the element-block Schwarz preconditioner is refused on meshes with order jumps")
     o = oracle_results(name)
     pr = o["pr"]
     build, sprec = (getattr(mto, k) for k in PATHS[path])
@@ -156,7 +166,7 @@ def test_solve_and_sensitivity_parity(mto, name, path, precond):
     uerr = np.linalg.norm(ug - o["u"]) / np.linalg.norm(o["u"])
     assert uerr < 1e-8, (uerr, it, rr)
     dc = torch.zeros(h.design_len, dtype=torch.float64, device="cuda")
-    C = h.sensitivity(u, f, rho, mat, dc, precision=build)
+    C = h.sensitivity(u, f, rho, mat, dc, precision=mto.MTO_FP64)
     assert abs(C - o["C"]) < 1e-8 * abs(o["C"]), (C, o["C"], uerr, it)
     dce = np.abs(dc.cpu().numpy() - o["dc"]).max() / np.abs(o["dc"]).max()
     assert dce < 1e-6, dce
@@ -166,17 +176,22 @@ def test_solve_and_sensitivity_parity(mto, name, path, precond):
 
 
 def test_multigrid_iterations_and_limits(mto):
-    """The multigrid cycle is a strong preconditioner (far fewer iterations than the element-block
-    one on the smooth-density dp case), works when the Q1 grid of the mesh is itself the coarsest,
-    and is refused (not faked) on meshes that do not halve to a small coarsest grid."""
+    """The multigrid cycle is a strong preconditioner (several times fewer iterations than point
+    Jacobi on the dp case), works when the Q1 grid of the mesh is itself the coarsest, and is
+    refused (not faked) on meshes that do not halve to a small coarsest grid; the element-block
+    Schwarz preconditioner is refused on meshes with order jumps."""
     pr = W.named("dp_cantilever_40x20")
     h, fixed, f, mat, rho = gpu_setup(mto, pr)
     h.build_elements(rho, mat, mto.MTO_FP64)
     its = {}
-    for pc in (mto.PREC_SCHWARZ, mto.PREC_MG):
+    for pc in (mto.PREC_JACOBI, mto.PREC_MG):
         u = torch.zeros(h.ndof, dtype=torch.float64, device="cuda")
         its[pc], _ = h.solve(f, u, rtol=1e-8, max_iter=400000, precond=pc, check_every=8)
-    assert its[mto.PREC_MG] * 5 < its[mto.PREC_SCHWARZ], its
+    assert its[mto.PREC_MG] * 4 < its[mto.PREC_JACOBI], its
+    u = torch.zeros(h.ndof, dtype=torch.float64, device="cuda")
+    with pytest.raises(mto.MTOError) as ei:
+        h.solve(f, u, precond=mto.PREC_SCHWARZ)
+    assert ei.value.status == 1 and "order" in str(ei.value)
     h.close()
     # 8 x 4 Q2: the Q1 grid (90 DOFs) is the coarsest level
     nel = 32

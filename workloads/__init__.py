@@ -181,9 +181,22 @@ def mbb_smooth(nelx=1024, nely=512, p=3, d=8, vol=0.2, sigma=8.0, seed_index=5):
                    np.full(nel, d, np.int32), rho, MBB)
 
 
+def _brace_bias(ny, nx, width):
+    """1 within ``width`` cells of the two diagonals of an ny x nx grid, else 0: the X bracing of a
+    truss-like cantilever (without it a thin frame alone is a near-mechanism)."""
+    y, x = np.mgrid[0:ny, 0:nx] + 0.5
+    b = np.zeros((ny, nx))
+    for (x0, y0, x1, y1) in ((0.0, 0.0, nx, ny), (0.0, ny, nx, 0.0)):
+        dx, dy = x1 - x0, y1 - y0
+        dist = np.abs(dy * (x - x0) - dx * (y - y0)) / np.hypot(dx, dy)
+        b[dist <= width] = 1.0
+    return b
+
+
 def dp_cantilever(nelx=320, nely=160, vol=0.1, seed_index=3, p_levels=(1, 2, 3, 4), d_levels=(1, 2, 4, 8)):
     """dp-adaptive cantilever: smooth random order and design maps with refined bands where the
-    density gradient is large; smooth densities at mean ``vol``.
+    density gradient is large; smooth densities at mean ``vol`` on a braced frame (a frame of one
+    element and X bracing, so the structure carries the load like an optimized truss).
 
     Orders: a smoothed field quantised to p_levels, +1 (capped) where |grad rho| is above its 80th
     percentile.  Design counts: an independent smoothed field quantised to d_levels, raised to the
@@ -192,7 +205,8 @@ def dp_cantilever(nelx=320, nely=160, vol=0.1, seed_index=3, p_levels=(1, 2, 3, 
     rng = np.random.default_rng(SEED_BASE + seed_index)
     r = 8
     s = _smooth_noise(rng, nely * r, nelx * r, 3.0 * r)
-    s = s + 4.0 * _frame_bias(nely * r, nelx * r, max(r, (nely * r) // 40))
+    s = s + 4.0 * np.maximum(_frame_bias(nely * r, nelx * r, max(r, (nely * r) // 80)),
+                             _brace_bias(nely * r, nelx * r, max(r, (nely * r) // 80)))
     fine = _sigmoid_volume(s, vol)
     # per-element gradient magnitude of the element-mean density
     em = fine.reshape(nely, r, nelx, r).mean(axis=(1, 3))
@@ -241,7 +255,10 @@ def named(name):
         "mbb_40x20_p3_d8": lambda: mbb_binary(40, 20, sigma=4.0, seed_index=12),
         "mbb_40x20_p3_d8_islands": lambda: mbb_binary(40, 20, sigma=4.0, seed_index=12, connected=False),
         "dp_cantilever_320x160": lambda: dp_cantilever(),
-        "dp_cantilever_40x20": lambda: dp_cantilever(40, 20, seed_index=13),
+        "dp_cantilever_40x20": lambda: dp_cantilever(40, 20, vol=0.3, seed_index=13),
         "mbb_1024x512_p3_d8": lambda: mbb_smooth(),
+        # a quarter of the large beam: element matrices (~1.1 GB for both storages) above L2, for
+        # hardware-counter captures of one operator launch
+        "mbb_512x256_p3_d8": lambda: mbb_smooth(512, 256, seed_index=6),
     }
     return table[name]()
