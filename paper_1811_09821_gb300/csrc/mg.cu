@@ -11,7 +11,8 @@
 //   level l+1 2x2 agglomeration of level l: K_E = sum_c J_c^T K_c J_c with J_c the bilinear
 //             interpolation of the coarse element's vertices at its child's vertices (again the
 //             exact Galerkin operator, because bilinear coarse fields are bilinear on the children);
-//   coarsest  a dense inverse (at most 2048 DOFs).
+//   coarsest  a dense inverse (at most 2048 DOFs; coarsening stops at the first grid that small,
+//             since one dense mat-vec costs less than the launches of two more levels).
 //
 // Smoothing: Chebyshev polynomials of the Jacobi-scaled operator on [lmax / 30, lmax], lmax from
 // a power iteration (x 1.1), the same polynomial before and after the coarse correction, so the
@@ -29,7 +30,7 @@
 namespace mto {
 namespace {
 
-constexpr int kCoarseTarget = 256;    // stop coarsening at or below this many DOFs
+constexpr int kCoarseTarget = 2048;   // stop coarsening at or below this many DOFs
 constexpr int kCoarseMax = 2048;      // largest coarsest grid for the dense inverse
 constexpr double kChebRatio = 30.0;   // lmin = lmax / ratio
 constexpr int kPowerIts = 30;
@@ -227,27 +228,23 @@ __global__ void mg_dense_fix_kernel(int N, const double* __restrict__ mask, doub
   }
 }
 
-__global__ void __launch_bounds__(1024) mg_gauss_jordan_kernel(int N, double* __restrict__ A, int* __restrict__ err) {
-  extern __shared__ double col[];   // [N] column k before elimination
-  for (int k = 0; k < N; ++k) {
-    const double piv = A[(size_t)k * N + k];
-    __syncthreads();
-    if (!(piv > 0.0)) {
-      if (threadIdx.x == 0) *err = MTO_ENAN;
-      return;   // uniform: every thread read the same pivot
-    }
-    const double inv = 1.0 / piv;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) col[i] = A[(size_t)i * N + k];
-    __syncthreads();
-    for (int j = threadIdx.x; j < N; j += blockDim.x) A[(size_t)k * N + j] = (j == k) ? inv : A[(size_t)k * N + j] * inv;
-    __syncthreads();
-    for (int64_t t = threadIdx.x; t < (int64_t)N * N; t += blockDim.x) {
-      const int i = (int)(t / N), j = (int)(t % N);
-      if (i == k) continue;
-      if (j == k) A[t] = -col[i] * inv;
-      else A[t] = fma(-col[i], A[(size_t)k * N + j], A[t]);
-    }
-    __syncthreads();
+// One Gauss-Jordan step of the in-place inversion (SPD: no pivoting), from buffer A into B so that
+// every entry is computed from the previous step's values; N launches invert the matrix.
+__global__ void __launch_bounds__(256) mg_gj_step_kernel(int N, int k, const double* __restrict__ A,
+                                                         double* __restrict__ B, int* __restrict__ err) {
+  const double piv = A[(size_t)k * N + k];
+  if (!(piv > 0.0)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *err = MTO_ENAN;
+  }
+  const double inv = 1.0 / piv;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)N * N;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / N), j = (int)(t - (int64_t)i * N);
+    double v;
+    if (i == k) v = (j == k) ? inv : A[(size_t)k * N + j] * inv;
+    else if (j == k) v = -A[(size_t)i * N + k] * inv;
+    else v = fma(-A[(size_t)i * N + k] * inv, A[(size_t)k * N + j], A[t]);
+    B[t] = v;
   }
 }
 
@@ -461,10 +458,12 @@ void mg_release(mto_handle h) {
   h->mg.clear();
   for (void* p : {(void*)h->mg_pidx, (void*)h->mg_pw, (void*)h->mg_rptr, (void*)h->mg_rnode, (void*)h->mg_rw,
                   (void*)h->mg_btab, (void*)h->mg_v0, (void*)h->mg_q0, (void*)h->mg_d0, (void*)h->mg_Ainv,
+                  (void*)h->mg_Awork,
                   (void*)h->mg_lmax, (void*)h->mg_part, (void*)h->mg_cnt, (void*)h->mg_res})
     cudaFree(p);
   h->mg_pidx = nullptr;
   h->mg_pw = h->mg_rw = h->mg_btab = h->mg_v0 = h->mg_q0 = h->mg_d0 = h->mg_Ainv = h->mg_lmax = nullptr;
+  h->mg_Awork = h->mg_Acur = nullptr;
   h->mg_part = h->mg_res = nullptr;
   h->mg_rptr = h->mg_rnode = nullptr;
   h->mg_cnt = nullptr;
@@ -586,6 +585,7 @@ mto_status mg_setup(mto_handle h) {
   for (double** v : {&h->mg_v0, &h->mg_q0, &h->mg_d0}) MTO_TRY(mto_alloc(h, v, h->ndof));
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->mg_q0, 0, h->ndof * sizeof(double), h->stream), "memset"));
   MTO_TRY(mto_alloc(h, &h->mg_Ainv, (size_t)ncoarse * ncoarse));
+  MTO_TRY(mto_alloc(h, &h->mg_Awork, (size_t)ncoarse * ncoarse));
   MTO_TRY(mto_alloc(h, &h->mg_lmax, h->mg.size() + 1));
   MTO_TRY(mto_alloc(h, &h->mg_part, kMGBlocks));
   MTO_TRY(mto_alloc(h, &h->mg_cnt, 8));
@@ -698,8 +698,15 @@ mto_status mg_build(mto_handle h) {
   mg_dense_fix_kernel<<<vec_grid((int64_t)N * N), 256, 0, h->stream>>>(N, C.mask, h->mg_Ainv);
   MTO_TRY(mto_after_launch(h, "mg_dense_fix_kernel"));
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->flags + 6, 0, sizeof(int), h->stream), "memset"));
-  mg_gauss_jordan_kernel<<<1, 1024, N * sizeof(double), h->stream>>>(N, h->mg_Ainv, h->flags + 6);
-  MTO_TRY(mto_after_launch(h, "mg_gauss_jordan_kernel"));
+  {
+    double* bufs[2] = {h->mg_Ainv, h->mg_Awork};
+    const int grd = vec_grid((int64_t)N * N);
+    for (int k = 0; k < N; ++k) {
+      mg_gj_step_kernel<<<grd, 256, 0, h->stream>>>(N, k, bufs[k & 1], bufs[(k + 1) & 1], h->flags + 6);
+      MTO_TRY(mto_after_launch(h, "mg_gj_step_kernel"));
+    }
+    h->mg_Acur = bufs[N & 1];
+  }
   }
   // Chebyshev bounds: fine level first, then every smoothed Q1 level
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->mg_q0, 0, h->ndof * sizeof(double), h->stream), "memset"));
@@ -768,7 +775,7 @@ mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const
   {
     TimedScope ts(h, F_PRECOND);
     const MGLevel& C = h->mg.back();
-    mg_coarse_solve_kernel<<<(int)((C.n * 32 + 255) / 256), 256, 0, h->stream>>>((int)C.n, h->mg_Ainv, C.b, C.x,
+    mg_coarse_solve_kernel<<<(int)((C.n * 32 + 255) / 256), 256, 0, h->stream>>>((int)C.n, h->mg_Acur, C.b, C.x,
                                                                                    done);
     MTO_TRY(mto_after_launch(h, "mg_coarse_solve_kernel"));
   }

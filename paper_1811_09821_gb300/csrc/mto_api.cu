@@ -1,6 +1,7 @@
 // C ABI entry points: handle lifecycle, mesh setup (minimum-rule DOF numbering and element
 // classes), supports, numbering queries, and dispatch to the kernel translation units.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -282,6 +283,9 @@ mto_status mto_create(mto_handle* out, int device, void* stream) {
   mto_handle h = new mto_handle_s();
   h->device = device;
   h->user_stream = (cudaStream_t)stream;
+  // MTO_NO_GRAPHS=1 launches the PCG iterations one kernel at a time instead of replaying captured
+  // graphs (same kernels and arithmetic; for profilers that handle graphs poorly)
+  if (const char* ng = std::getenv("MTO_NO_GRAPHS")) h->use_graphs = !(ng[0] == '1');
   cudaSetDevice(device);
   if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||

@@ -200,7 +200,9 @@ struct mto_handle_s {
   double* mg_btab = nullptr;                   // bilinear weights at the GLL nodes, per order
   int mg_boff[mto::kPMaxTab + 2] = {0};
   double *mg_v0 = nullptr, *mg_q0 = nullptr, *mg_d0 = nullptr;   // [ndof] fine-level scratch
-  double* mg_Ainv = nullptr;                   // coarsest-level dense inverse [N][N]
+  double* mg_Ainv = nullptr;                   // coarsest level: two [N][N] buffers of the
+  double* mg_Awork = nullptr;                  // Gauss-Jordan steps ...
+  double* mg_Acur = nullptr;                   // ... and the one holding the inverse
   double* mg_lmax = nullptr;                   // [levels] Chebyshev upper bounds
   double* mg_part = nullptr;                   // reduction partials
   unsigned* mg_cnt = nullptr;
