@@ -257,6 +257,104 @@ __global__ void __launch_bounds__(256) ebe_kernel(const double* __restrict__ K64
   if (red.part) reduce_out(dot, red);
 }
 
+// The split-precision operator for n_e <= 32 (one row per lane), software-pipelined: a persistent
+// grid walks its elements with a stride, and while a warp computes one element's rows it already
+// holds the next element's hi/lo rows (2 (n_e/2 + 1) registers each) and node map, so the
+// element stream from L2/HBM never waits on the arithmetic.  Same arithmetic as ebe_kernel.
+template <int PO, typename TX>
+__global__ void __launch_bounds__(256, 2) ebe_df_pipe_kernel(const float* __restrict__ Kh,
+                                                             const float* __restrict__ Kl, int L, int n,
+                                                             const int* __restrict__ gmap,
+                                                             const Constraint* __restrict__ cons,
+                                                             const TX* __restrict__ x, TX* __restrict__ y, Red red,
+                                                             const int* __restrict__ done) {
+  constexpr int N1 = PO + 1, NN = N1 * N1, NE = 2 * NN, ND = NE / 2 + 1;
+  constexpr int W = WarpShape<NE>::W, G = WarpShape<NE>::G;
+  static_assert(WarpShape<NE>::M == 1, "one row per lane");
+  constexpr bool kSplitX = sizeof(TX) == 8;
+  if (done && *done) return;
+  const int lane = threadIdx.x & 31;
+  const int li = lane % W, gb = lane - li, gid = lane / W;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int stride = nwarps * G;
+  float ah[ND], al[ND];
+  int gn;
+  auto fetch = [&](int e, float (&h)[ND], float (&l)[ND], int& g) {
+    const bool v = e < n && li < NE;
+    const size_t rowb = (size_t)(v ? e : 0) * L;
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      h[k] = v ? __ldg(Kh + rowb + k * NE + li) : 0.0f;
+      l[k] = v ? __ldg(Kl + rowb + k * NE + li) : 0.0f;
+    }
+    g = v ? __ldg(gmap + (size_t)e * NN + (li >> 1)) : 0;
+  };
+  double dot = 0.0;
+  int base = warp * G;
+  if (base < n) fetch(base + gid, ah, al, gn);
+  for (; base < n; base += stride) {
+    const int e = base + gid;
+    const bool act = e < n && li < NE;
+    const int g = gn;
+    // gather x_e
+    double xd = 0.0;
+    if (act) {
+      if (g >= 0) {
+        xd = (double)x[2 * (size_t)g + (li & 1)];
+      } else {
+        const Constraint& c = cons[-g - 1];
+        for (int q = 0; q < c.cnt; ++q) xd += c.w[q] * (double)x[2 * (size_t)c.node[q] + (li & 1)];
+      }
+    }
+    // the next element's rows and node map, in flight during this element's arithmetic
+    float bh[ND], bl[ND];
+    int gnext = 0;
+    fetch(base + stride + gid, bh, bl, gnext);
+    const float xh = (float)xd;
+    const float xl = kSplitX ? (float)(xd - (double)xh) : 0.0f;
+    float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      int j = li + k;
+      if (j >= NE) j -= NE;
+      const int src = gb + j;
+      const float xjh = __shfl_sync(0xffffffffu, xh, src);
+      const float xjl = kSplitX ? __shfl_sync(0xffffffffu, xl, src) : 0.0f;
+      float pp, pe;
+      df_prod<kSplitX>(ah[k], al[k], xjh, xjl, pp, pe);
+      df_acc(sh, sl, pp, pe);
+      if (k > 0 && 2 * k != NE) {
+        float tp, te;
+        df_prod<kSplitX>(ah[k], al[k], xh, xl, tp, te);
+        int s = li - k;
+        if (s < 0) s += NE;
+        const float rp = __shfl_sync(0xffffffffu, tp, gb + s);
+        const float re = __shfl_sync(0xffffffffu, te, gb + s);
+        df_acc(sh, sl, rp, re);
+      }
+    }
+    // scatter P_e^T y_e and the curvature term
+    if (act) {
+      const double yv = (double)sh + (double)sl;
+      if (g >= 0) {
+        atomicAdd(y + 2 * (size_t)g + (li & 1), (TX)yv);
+      } else {
+        const Constraint& c = cons[-g - 1];
+        for (int q = 0; q < c.cnt; ++q) atomicAdd(y + 2 * (size_t)c.node[q] + (li & 1), (TX)(c.w[q] * yv));
+      }
+      if (red.part) dot += xd * yv;
+    }
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      ah[k] = bh[k];
+      al[k] = bl[k];
+    }
+    gn = gnext;
+  }
+  if (red.part) reduce_out(dot, red);
+}
+
 }  // namespace
 
 // Blocks of one element-operator launch for an order class (fixed per class size).
@@ -284,6 +382,18 @@ namespace {
 template <int PO, bool kDF, typename TX>
 void launch_ebe(mto_handle h, const PClass& c, const double* M64, const float* Mh, const float* Ml, const TX* x,
                 TX* y, Red red, const int* done, const ConvTest& cv) {
+  constexpr int NE = 2 * (PO + 1) * (PO + 1);
+  if constexpr (kDF && WarpShape<NE>::M == 1) {
+    if (!cv.res) {
+      // persistent: two blocks of 8 warps per SM (the register budget of the pipelined rows)
+      const int warps = (c.n + WarpShape<NE>::G - 1) / WarpShape<NE>::G;
+      int blocks = (warps + 7) / 8;
+      if (blocks > 152 * 2) blocks = 152 * 2;
+      ebe_df_pipe_kernel<PO, TX><<<blocks, 256, 0, h->stream>>>(Mh, Ml, c.L, c.n, c.gmap, h->cons_d, x, y, red,
+                                                                  done);
+      return;
+    }
+  }
   ebe_kernel<PO, kDF, TX><<<ebe_blocks_p<PO>(c.n), 256, 0, h->stream>>>(M64, Mh, Ml, c.L, c.n, c.gmap, h->cons_d, x,
                                                                         y, red, done, cv);
 }
@@ -442,17 +552,6 @@ __global__ void __launch_bounds__(256) cg_init_kernel(int64_t n, const T* __rest
   if (kJacobi) reduce_out(g, gout);
 }
 
-// r^T z after the multigrid cycle (one launch, last-block reduction)
-__global__ void __launch_bounds__(256) cg_dot_kernel(int64_t n, const double* __restrict__ a,
-                                                     const double* __restrict__ b, Red out,
-                                                     const int* __restrict__ done) {
-  if (done && *done) return;
-  double s = 0.0;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-    s += a[j] * b[j];
-  reduce_out(s, out);
-}
-
 template <typename T>
 __global__ void __launch_bounds__(256) copy_kernel(int64_t n, const T* __restrict__ a, T* __restrict__ b) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
@@ -576,10 +675,8 @@ mto_status precond_step<double>(mto_handle h, const CGVecs<double>& v, int pc, i
                                 const int* done) {
   ConvTest none{};
   if (pc == MTO_PREC_SCHWARZ) return apply_all<double>(h, 1, v.r, v.z, slot, done, none);
-  MTO_TRY(mg_vcycle(h, v.r, v.z, deg, done));
-  TimedScope ts(h, F_VECTOR);
-  cg_dot_kernel<<<kVecBlocks, 256, 0, h->stream>>>(h->ndof, v.r, v.z, red_slot(h, slot, 0), done);
-  return mto_after_launch(h, "cg_dot_kernel");
+  const Red rd = red_slot(h, slot, 0);   // r^T z from the cycle's last smoothing step
+  return mg_vcycle(h, v.r, v.z, deg, done, rd.part, rd.cnt, rd.res);
 }
 template <>
 mto_status precond_step<float>(mto_handle h, const CGVecs<float>& v, int pc, int deg, int slot, const int* done) {

@@ -264,10 +264,14 @@ __global__ void __launch_bounds__(256) mg_coarse_solve_kernel(int N, const doubl
 // ---------------------------------------------------------------- smoothing and transfers
 // One Chebyshev step on level vectors: r = D^-1 (b - q) (q = A x, then cleared), step 0:
 // d = r / theta, step s > 0: d = rho_s rho_{s-1} d + (2 rho_s / delta) r; x = d (xzero) or x += d.
+// With dpart set, also b^T x of the updated x (the PCG's r^T z after the cycle's last step),
+// reduced by the last block to finish in index order into *dres.
 __global__ void __launch_bounds__(256) mg_cheb_kernel(int64_t n, const double* __restrict__ b, double* __restrict__ q,
                                                       const double* __restrict__ invd, double* __restrict__ x,
                                                       double* __restrict__ d, const double* __restrict__ lmax,
-                                                      int step, int xzero, const int* __restrict__ done) {
+                                                      int step, int xzero, const int* __restrict__ done,
+                                                      double* __restrict__ dpart, unsigned* __restrict__ dcnt,
+                                                      double* __restrict__ dres) {
   if (done && *done) return;
   const double lm = *lmax, lo = lm / kChebRatio;
   const double th = 0.5 * (lm + lo), de = 0.5 * (lm - lo), sg = th / de;
@@ -281,50 +285,65 @@ __global__ void __launch_bounds__(256) mg_cheb_kernel(int64_t n, const double* _
     c1 = rc * rp;
     c2 = 2.0 * rc / de;
   }
+  double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double r = invd[i] * (b[i] - q[i]);
+    const double bi = b[i];
+    const double r = invd[i] * (bi - q[i]);
     q[i] = 0.0;
     const double dn = step > 0 ? fma(c1, d[i], c2 * r) : c2 * r;
     d[i] = dn;
-    x[i] = xzero ? dn : x[i] + dn;
+    const double xn = xzero ? dn : x[i] + dn;
+    x[i] = xn;
+    acc = fma(bi, xn, acc);
+  }
+  if (!dpart) return;
+  __shared__ int last;
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) {
+    dpart[blockIdx.x] = acc;
+    __threadfence();
+    last = (atomicAdd(dcnt, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double t = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(dpart + i);
+    t = block_sum(t);
+    if (threadIdx.x == 0) {
+      *dres = t;
+      *dcnt = 0u;
+    }
   }
 }
 
-// residual on free DOFs: d = (b - q) masked, q cleared
-__global__ void __launch_bounds__(256) mg_residual_kernel(int64_t n, const double* __restrict__ b,
-                                                          double* __restrict__ q, const double* __restrict__ invd,
-                                                          double* __restrict__ d, const int* __restrict__ done) {
-  if (done && *done) return;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    d[i] = invd[i] != 0.0 ? b[i] - q[i] : 0.0;
-    q[i] = 0.0;
-  }
-}
-
-// level 0 -> 1: b1 = P^T r by the vertex-wise transposed table
+// level 0 -> 1: b1 = P^T r by the vertex-wise transposed table, the residual r = b - q formed on
+// the fly on free DOFs (q = A x stays; the prolongation clears it)
 __global__ void __launch_bounds__(256) mg_restrict0_kernel(int64_t nv, const int* __restrict__ ptr,
                                                            const int* __restrict__ node, const double* __restrict__ w,
-                                                           const double* __restrict__ r, const double* __restrict__ mask,
-                                                           double* __restrict__ b1, const int* __restrict__ done) {
+                                                           const double* __restrict__ b, const double* __restrict__ q,
+                                                           const double* __restrict__ invd,
+                                                           const double* __restrict__ mask, double* __restrict__ b1,
+                                                           const int* __restrict__ done) {
   if (done && *done) return;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
     double s0 = 0.0, s1 = 0.0;
     for (int k = ptr[v]; k < ptr[v + 1]; ++k) {
       const double wk = w[k];
       const size_t g = 2 * (size_t)node[k];
-      s0 = fma(wk, r[g], s0);
-      s1 = fma(wk, r[g + 1], s1);
+      if (invd[g] != 0.0) s0 = fma(wk, b[g] - q[g], s0);
+      if (invd[g + 1] != 0.0) s1 = fma(wk, b[g + 1] - q[g + 1], s1);
     }
     b1[2 * v] = mask[2 * v] * s0;
     b1[2 * v + 1] = mask[2 * v + 1] * s1;
   }
 }
 
-// level 1 -> 0: x += P x1 on free DOFs
+// level 1 -> 0: x += P x1 on free DOFs; q (A x of the pre-smoothed x) cleared
 __global__ void __launch_bounds__(256) mg_prolong0_kernel(int64_t nn, const int* __restrict__ idx,
                                                           const double* __restrict__ w, const double* __restrict__ x1,
                                                           const double* __restrict__ invd, double* __restrict__ x,
-                                                          const int* __restrict__ done) {
+                                                          double* __restrict__ q, const int* __restrict__ done) {
   if (done && *done) return;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
     double s0 = 0.0, s1 = 0.0;
@@ -337,12 +356,17 @@ __global__ void __launch_bounds__(256) mg_prolong0_kernel(int64_t nn, const int*
     }
     if (invd[2 * g] != 0.0) x[2 * g] += s0;
     if (invd[2 * g + 1] != 0.0) x[2 * g + 1] += s1;
+    q[2 * g] = 0.0;
+    q[2 * g + 1] = 0.0;
   }
 }
 
-// level l -> l+1 on vertex grids (full weighting: the transpose of bilinear interpolation)
+// level l -> l+1 on vertex grids (full weighting: the transpose of bilinear interpolation) of the
+// residual r = b - q formed on the fly on free DOFs (q stays; the prolongation clears it)
 __global__ void __launch_bounds__(256) mg_restrict_h_kernel(int nxc, int nyc, int nxf, int nyf,
-                                                            const double* __restrict__ r, const double* __restrict__ mask,
+                                                            const double* __restrict__ b, const double* __restrict__ q,
+                                                            const double* __restrict__ invd,
+                                                            const double* __restrict__ mask,
                                                             double* __restrict__ bc, const int* __restrict__ done) {
   if (done && *done) return;
   const int64_t nvc = (int64_t)(nxc + 1) * (nyc + 1);
@@ -358,8 +382,8 @@ __global__ void __launch_bounds__(256) mg_restrict_h_kernel(int nxc, int nyc, in
         if (i < 0 || i > nxf) continue;
         const double wgt = wy * (dx == 0 ? 1.0 : 0.5);
         const size_t f = 2 * ((size_t)j * (nxf + 1) + i);
-        s0 = fma(wgt, r[f], s0);
-        s1 = fma(wgt, r[f + 1], s1);
+        if (invd[f] != 0.0) s0 = fma(wgt, b[f] - q[f], s0);
+        if (invd[f + 1] != 0.0) s1 = fma(wgt, b[f + 1] - q[f + 1], s1);
       }
     }
     bc[2 * V] = mask[2 * V] * s0;
@@ -367,10 +391,10 @@ __global__ void __launch_bounds__(256) mg_restrict_h_kernel(int nxc, int nyc, in
   }
 }
 
-// level l+1 -> l: x += bilinear interpolation of the coarse correction (free DOFs)
+// level l+1 -> l: x += bilinear interpolation of the coarse correction (free DOFs); q cleared
 __global__ void __launch_bounds__(256) mg_prolong_h_kernel(int nxc, int nxf, int nyf, const double* __restrict__ xc,
                                                            const double* __restrict__ mask, double* __restrict__ xf,
-                                                           const int* __restrict__ done) {
+                                                           double* __restrict__ q, const int* __restrict__ done) {
   if (done && *done) return;
   const int64_t nvf = (int64_t)(nxf + 1) * (nyf + 1);
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nvf; v += (int64_t)gridDim.x * blockDim.x) {
@@ -388,6 +412,8 @@ __global__ void __launch_bounds__(256) mg_prolong_h_kernel(int nxc, int nxf, int
       }
     xf[2 * v] += mask[2 * v] * s0;
     xf[2 * v + 1] += mask[2 * v + 1] * s1;
+    q[2 * v] = 0.0;
+    q[2 * v + 1] = 0.0;
   }
 }
 
@@ -725,11 +751,13 @@ mto_status mg_build(mto_handle h) {
 }
 
 // z = M^-1 r: one V-cycle.  Level-0 vectors: b = r, x = z, q = mg_q0 (A x, kept zero between
-// uses), d = mg_d0 (Chebyshev direction, then the residual).
-mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const int* done) {
+// uses), d = mg_d0 (Chebyshev direction).  With dot_part set, the last smoothing step also reduces
+// r^T z into *dot_res (block partials in dot_part, counter dot_cnt).
+mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const int* done, double* dot_part,
+                     unsigned* dot_cnt, double* dot_res) {
   const int nl = (int)h->mg.size();
   auto smooth = [&](int lev, const double* b, double* x, double* q, double* d, const double* invd, int64_t n,
-                    bool pre) -> mto_status {
+                    bool pre, bool with_dot) -> mto_status {
     const int k = lev < 0 ? degree : kCoarseDegree;
     const double* lm = h->mg_lmax + (lev + 1);
     const int grd = vec_grid(n);
@@ -743,33 +771,32 @@ mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const
         }
       }
       TimedScope ts(h, F_PRECOND);
-      mg_cheb_kernel<<<grd, 256, 0, h->stream>>>(n, b, q, invd, x, d, lm, s, pre && s == 0, done);
+      const bool dot = with_dot && s == k - 1;
+      mg_cheb_kernel<<<grd, 256, 0, h->stream>>>(n, b, q, invd, x, d, lm, s, pre && s == 0, done,
+                                                  dot ? dot_part : nullptr, dot_cnt, dot_res);
       MTO_TRY(mto_after_launch(h, "mg_cheb_kernel"));
     }
     return MTO_OK;
   };
   // level 0 pre-smoothing and residual
-  MTO_TRY(smooth(-1, r, z, h->mg_q0, h->mg_d0, h->invd64, h->ndof, true));
+  MTO_TRY(smooth(-1, r, z, h->mg_q0, h->mg_d0, h->invd64, h->ndof, true, false));
   MTO_TRY(apply_fine(h, z, h->mg_q0, done));
   {
     TimedScope ts(h, F_PRECOND);
-    mg_residual_kernel<<<vec_grid(h->ndof), 256, 0, h->stream>>>(h->ndof, r, h->mg_q0, h->invd64, h->mg_d0, done);
-    MTO_TRY(mto_after_launch(h, "mg_residual_kernel"));
     MGLevel& L1 = h->mg[0];
-    mg_restrict0_kernel<<<vec_grid(L1.nv), 256, 0, h->stream>>>(L1.nv, h->mg_rptr, h->mg_rnode, h->mg_rw, h->mg_d0,
-                                                               L1.mask, L1.b, done);
+    mg_restrict0_kernel<<<vec_grid(L1.nv), 256, 0, h->stream>>>(L1.nv, h->mg_rptr, h->mg_rnode, h->mg_rw, r,
+                                                               h->mg_q0, h->invd64, L1.mask, L1.b, done);
     MTO_TRY(mto_after_launch(h, "mg_restrict0_kernel"));
   }
   // Q1 levels down
   for (int l = 0; l < nl - 1; ++l) {
     MGLevel& L = h->mg[l];
     MGLevel& C = h->mg[l + 1];
-    MTO_TRY(smooth(l, L.b, L.x, L.q, L.d, L.invd, L.n, true));
+    MTO_TRY(smooth(l, L.b, L.x, L.q, L.d, L.invd, L.n, true, false));
     TimedScope ts(h, F_PRECOND);
     MTO_TRY(apply_q1(h, L, L.x, L.q, done));
-    mg_residual_kernel<<<vec_grid(L.n), 256, 0, h->stream>>>(L.n, L.b, L.q, L.invd, L.d, done);
-    MTO_TRY(mto_after_launch(h, "mg_residual_kernel"));
-    mg_restrict_h_kernel<<<vec_grid(C.nv), 256, 0, h->stream>>>(C.nx, C.ny, L.nx, L.ny, L.d, C.mask, C.b, done);
+    mg_restrict_h_kernel<<<vec_grid(C.nv), 256, 0, h->stream>>>(C.nx, C.ny, L.nx, L.ny, L.b, L.q, L.invd, C.mask,
+                                                                C.b, done);
     MTO_TRY(mto_after_launch(h, "mg_restrict_h_kernel"));
   }
   {
@@ -785,18 +812,18 @@ mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const
     const MGLevel& C = h->mg[l + 1];
     {
       TimedScope ts(h, F_PRECOND);
-      mg_prolong_h_kernel<<<vec_grid(L.nv), 256, 0, h->stream>>>(C.nx, L.nx, L.ny, C.x, L.mask, L.x, done);
+      mg_prolong_h_kernel<<<vec_grid(L.nv), 256, 0, h->stream>>>(C.nx, L.nx, L.ny, C.x, L.mask, L.x, L.q, done);
       MTO_TRY(mto_after_launch(h, "mg_prolong_h_kernel"));
     }
-    MTO_TRY(smooth(l, L.b, L.x, L.q, L.d, L.invd, L.n, false));
+    MTO_TRY(smooth(l, L.b, L.x, L.q, L.d, L.invd, L.n, false, false));
   }
   {
     TimedScope ts(h, F_PRECOND);
     mg_prolong0_kernel<<<vec_grid(h->n_nodes), 256, 0, h->stream>>>(h->n_nodes, h->mg_pidx, h->mg_pw, h->mg[0].x,
-                                                                    h->invd64, z, done);
+                                                                    h->invd64, z, h->mg_q0, done);
     MTO_TRY(mto_after_launch(h, "mg_prolong0_kernel"));
   }
-  return smooth(-1, r, z, h->mg_q0, h->mg_d0, h->invd64, h->ndof, false);
+  return smooth(-1, r, z, h->mg_q0, h->mg_d0, h->invd64, h->ndof, false, true);
 }
 
 }  // namespace mto

@@ -413,7 +413,8 @@ int local_node_map_public(mto_handle h, int64_t e, int a, int b, int64_t* nodes,
 mto_status mg_setup(mto_handle h);                                      // hierarchy, transfer tables
 mto_status mg_set_masks(mto_handle h);                                  // supports on every level
 mto_status mg_build(mto_handle h);                                      // Galerkin operators, bounds
-mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const int* done);
+mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const int* done, double* dot_part,
+                     unsigned* dot_cnt, double* dot_res);
 void mg_release(mto_handle h);
 // tc.cu
 mto_status tc_tables(mto_handle h);
