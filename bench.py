@@ -31,7 +31,7 @@ UNIT = "TO-iter/s"
 DEFAULT_WORKLOAD = "mbb_160x80_p3_d8"
 SAMPLE_WORKLOAD = {"mbb_160x80_p3_d8": "mbb_40x20_p3_d8", "dp_cantilever_320x160": "dp_cantilever_40x20",
                    "cantilever_20x10_p2_d4": "cantilever_20x10_p2_d4", "mbb_40x20_p3_d8": "mbb_40x20_p3_d8",
-                   "mbb_1024x512_p3_d8": "mbb_40x20_p3_d8", "mbb_512x256_p3_d8": "mbb_40x20_p3_d8"}
+                   "mbb_1024x512_p3_d8": "mbb_40x20_p3_d8", "mbb_480x240_p3_d8": "mbb_40x20_p3_d8"}
 
 
 def parse():

@@ -114,9 +114,9 @@ def test_operator_matches_assembled_oracle(mto, name, build):
 def test_tensor_core_build_matches_simt(mto, name):
     """The sliced tcgen05 build (d <= 8) and the FP64 CUDA-core build give the same element
     matrices to 1e-13 of each element's largest entry (the slicing keeps ~49 bits of each operand
-    against the FP64 sum's 53; cancellation among the subcell terms amplifies both), and the mixed
-    solves on the two builds (FP64 matrices for the refinement residual, the split pair inside)
-    agree on C to 1e-9."""
+    against the FP64 sum's 53; cancellation among the subcell terms amplifies both), and the solves
+    on the two builds agree on C to 1e-7 (matrix differences of 1e-13 move C by up to the
+    condition number times that: 7e-9 measured on the dp case)."""
     o = oracle_results(name)
     pr, m = o["pr"], o["mesh"]
     h, fixed, f, mat, rho = gpu_setup(mto, pr)
@@ -133,7 +133,7 @@ def test_tensor_core_build_matches_simt(mto, name):
             C[path] = float(f @ u)
         for a, b in zip(got[mto.BUILD_TENSOR], got[mto.BUILD_SIMT]):
             assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
-        assert abs(C[mto.BUILD_TENSOR] - C[mto.BUILD_SIMT]) <= 1e-9 * abs(C[mto.BUILD_SIMT])
+        assert abs(C[mto.BUILD_TENSOR] - C[mto.BUILD_SIMT]) <= 1e-7 * abs(C[mto.BUILD_SIMT])
     h.set_build_path(mto.BUILD_SIMT)
     h.close()
 
@@ -161,7 +161,10 @@ def test_solve_and_sensitivity_parity(mto, name, path, precond):
     h, fixed, f, mat, rho = gpu_setup(mto, pr)
     h.build_elements(rho, mat, build)
     u = torch.zeros(h.ndof, dtype=torch.float64, device="cuda")
-    it, rr = h.solve(f, u, precision=sprec, rtol=1e-9, norm=mto.NORM_JACOBI, max_iter=400000, precond=pc)
+    # Jacobi-scaled residual 1e-10 (u to ~1e-9 on these cases); if the FP64 residual floor stops
+    # the solve first, the u check below decides
+    it, rr = h.solve(f, u, precision=sprec, rtol=1e-10, norm=mto.NORM_JACOBI, max_iter=40000, precond=pc,
+                     raise_on_noconv=False)
     ug = u.cpu().numpy()
     uerr = np.linalg.norm(ug - o["u"]) / np.linalg.norm(o["u"])
     assert uerr < 1e-8, (uerr, it, rr)
@@ -298,12 +301,13 @@ def test_oc_update_parity(mto):
     h, fixed, f, mat, rho = gpu_setup(mto, pr)
     dc = torch.tensor(o["dc"], device="cuda")
     out = torch.zeros_like(rho)
-    lam = h.oc_update(rho, dc, 0.2, out)
+    vol = 0.25   # the design holds 0.30; the move limit 0.2 allows 0.222 .. 0.461
+    lam = h.oc_update(rho, dc, vol, out)
     dv = ooc.subcell_areas(m)
-    want, wl = ooc.oc_update(pr.rho, o["dc"], dv, 0.2 * m.nel)
+    want, wl = ooc.oc_update(pr.rho, o["dc"], dv, vol * m.nel)
     assert abs(lam - wl) < 1e-8 * wl
     np.testing.assert_allclose(out.cpu().numpy(), want, rtol=1e-9, atol=1e-12)
-    assert abs(out.cpu().numpy() @ dv - 0.2 * m.nel) < 1e-8 * m.nel
+    assert abs(out.cpu().numpy() @ dv - vol * m.nel) < 1e-8 * m.nel
     h.close()
 
 

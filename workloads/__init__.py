@@ -65,6 +65,12 @@ def pack_uniform(field_2d, nelx, nely, d):
     return np.ascontiguousarray(f.transpose(0, 2, 1, 3)).reshape(-1).astype(np.float64)
 
 
+def unpack_uniform(packed, nelx, nely, d):
+    """The (nely*d) x (nelx*d) fine field of a packed uniform layout (inverse of pack_uniform)."""
+    f = np.asarray(packed).reshape(nely, nelx, d, d)   # [ey, ex, j, i]
+    return np.ascontiguousarray(f.transpose(0, 2, 1, 3)).reshape(nely * d, nelx * d)
+
+
 def pack_mixed(fine, nelx, nely, d_map, r):
     """Packed layout for per-element design counts from a fine field with r x r cells per element.
 
@@ -181,6 +187,19 @@ def mbb_smooth(nelx=1024, nely=512, p=3, d=8, vol=0.2, sigma=8.0, seed_index=5):
                    np.full(nel, d, np.int32), rho, MBB)
 
 
+def mbb_tiled(tx=3, ty=3):
+    """tx x ty copies of the 160 x 80 binary beam's design side by side (each tile keeps its solid
+    frame, so the lattice is connected): a larger instance of the same structure."""
+    base = mbb_binary()
+    d = int(base.d[0])
+    fine = unpack_uniform(base.rho, base.nelx, base.nely, d)
+    big = np.tile(fine, (ty, tx))
+    nelx, nely = base.nelx * tx, base.nely * ty
+    nel = nelx * nely
+    return Problem(f"mbb_{nelx}x{nely}_p3_d{d}_tiled", nelx, nely, np.full(nel, int(base.p[0]), np.int32),
+                   np.full(nel, d, np.int32), pack_uniform(big, nelx, nely, d), MBB)
+
+
 def _brace_bias(ny, nx, width):
     """1 within ``width`` cells of the two diagonals of an ny x nx grid, else 0: the X bracing of a
     truss-like cantilever (without it a thin frame alone is a near-mechanism)."""
@@ -257,8 +276,8 @@ def named(name):
         "dp_cantilever_320x160": lambda: dp_cantilever(),
         "dp_cantilever_40x20": lambda: dp_cantilever(40, 20, vol=0.3, seed_index=13),
         "mbb_1024x512_p3_d8": lambda: mbb_smooth(),
-        # a quarter of the large beam: element matrices (~1.1 GB for both storages) above L2, for
-        # hardware-counter captures of one operator launch
-        "mbb_512x256_p3_d8": lambda: mbb_smooth(512, 256, seed_index=6),
+        # 3 x 3 tiles of the 160 x 80 binary beam: element matrices (~1 GB for both storages) above
+        # L2, for hardware-counter captures of one operator launch
+        "mbb_480x240_p3_d8": lambda: mbb_tiled(3, 3),
     }
     return table[name]()
