@@ -271,6 +271,24 @@ mto_status mto_memory(mto_handle h, int64_t* bytes);
 /* Number of kernel launches this handle has issued since creation (host output). */
 mto_status mto_launch_count(mto_handle h, int64_t* count);
 
+/* Compliance C = f^T u of n DOFs without any allocation.  The paper has no counterpart: this is
+ * an entry point for callers that manage all device memory themselves (for example around
+ * externally captured work).  f, u: device double[n]; C: device double (written); stream: the
+ * CUDA stream to launch on (NULL: the legacy default stream); device: the CUDA device that owns
+ * f, u and C.  The block partial sums live in a fixed 72 KB array in the library's device memory
+ * (8192 partials), so n is limited to 8192 x 2048 = 16,777,216 DOFs; larger n (or n < 0, NULL
+ * pointers, a device index outside 0..63) returns MTO_EINVAL before any launch.  The array's
+ * finished-block counter must be zero when a launch starts: it is zero when the library loads,
+ * each call clears it on the stream before its kernel, and the kernel's last block clears it
+ * again.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call outside any stream
+ * capture.  Calls that overlap in time on the same device (different streams, host threads)
+ * share the array and race: order them on one stream or with events.  The summation order
+ * depends only on n, so repeated calls give bit-identical results.  Asynchronous; returns
+ * MTO_ECUDA when a CUDA call fails. */
+mto_status mto_compliance_noalloc(int32_t device, const double* f, const double* u, int64_t n, void* stream,
+                                  double* C);
+
 #ifdef __cplusplus
 }
 #endif

@@ -61,7 +61,7 @@ SYMBOLS = ["mto_create", "mto_destroy", "mto_last_error", "mto_set_stream", "mto
            "mto_vertex_dof", "mto_side_dofs", "mto_element_nodes", "mto_element_matrix", "mto_build_elements", "mto_solve", "mto_apply",
            "mto_sensitivity", "mto_indicator", "mto_map_update", "mto_oc_update", "mto_timing_enable", "mto_timing_read",
            "mto_set_build_path",
-           "mto_memory", "mto_launch_count"]
+           "mto_memory", "mto_launch_count", "mto_compliance_noalloc"]
 TIME_FAMILIES = {"apply32": 0, "apply64": 1, "build": 2, "sens": 3, "indicator": 4, "vector": 5, "applydf64": 6,
                  "precond": 7}
 
@@ -101,6 +101,7 @@ def load_library(path=LIB_PATH):
         "mto_timing_read": ([vp, i32, P(i64), P(dbl)], ctypes.c_int),
         "mto_memory": ([vp, P(i64)], ctypes.c_int),
         "mto_launch_count": ([vp, P(i64)], ctypes.c_int),
+        "mto_compliance_noalloc": ([i32, vp, vp, i64, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -283,6 +284,15 @@ class Handle:
         c = ctypes.c_int64()
         self._check(self.L.mto_launch_count(self.h, ctypes.byref(c)))
         return c.value
+
+
+def compliance_noalloc(f, u, out, n=None, device=0, stream=None):
+    """C = f^T u into out[0] (device float64) through mto_compliance_noalloc (no allocation; see
+    include/mto.h).  Returns the status code."""
+    L = load_library()
+    st = stream.cuda_stream if stream is not None else torch.cuda.current_stream(device).cuda_stream
+    return L.mto_compliance_noalloc(device, f.data_ptr(), u.data_ptr(), int(f.numel() if n is None else n),
+                                    ctypes.c_void_p(st), out.data_ptr())
 
 
 def load_case(handle, load):
