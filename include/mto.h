@@ -70,7 +70,9 @@ typedef struct {
  *              the residual r = f - K u with the FP64 matrices and FP64 vectors, then solves
  *              K d = r by an inner PCG that applies the split-precision pair on the FP32 pipes
  *              (error-free products and sums, ~48-bit accurate) with FP64 vectors, to inner_rtol
- *              relative to r, and sets u += d.
+ *              relative to r, and sets u += d.  A step whose FP64 residual falls short of the
+ *              asked reduction by more than 10x (the split pair's 48 bits limiting an
+ *              ill-conditioned problem) switches the remaining steps to the FP64 matrices.
  *              MTO_MIXED32 (needs the MTO_MIXED build): the same refinement with FP32 vectors in
  *              the inner PCG (converges only on well-conditioned problems; Jacobi or Schwarz).
  *              Dot products are accumulated in FP64 in every mode.

@@ -895,11 +895,18 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
   const int max_outer = o->max_outer > 0 ? o->max_outer : 50;
   const int nrm = o->norm == MTO_NORM_JACOBI ? 1 : 0;
   const double itol = o->inner_rtol > 0 ? o->inner_rtol : 1e-6;
+  // mixed refinement: a step whose FP64 residual falls short of the asked reduction by more than
+  // 10x shows that the split pair's ~48-bit matrices limit it (condition number near 2^48); the
+  // remaining steps then apply the FP64 matrices in the inner PCG too
+  bool split = true;
+  double rr_prev = -1.0, asked = 0.0;
   mto_status st = MTO_ENOCONV;
   for (int outer = 0; outer <= max_outer; ++outer) {
     // FP64 residual with the FP64 element matrices
     h->inner_split = false;
     MTO_TRY(true_residual(h, f, u, nrm, &rr, &ff));
+    if (o->precision == MTO_MIXED && rr_prev > 0.0 && std::sqrt(rr / rr_prev) > 10.0 * asked) split = false;
+    rr_prev = rr;
     if (!std::isfinite(rr)) {
       st = mto_fail(h, MTO_ENAN, "mto_solve: non-finite residual");
       break;
@@ -926,7 +933,8 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
       h->host_pinned[33] = tol_i * tol_i * h->host_pinned[nrm ? 2 : 0];
       MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->red + 6, h->host_pinned + 33, sizeof(double),
                                                 cudaMemcpyHostToDevice, h->stream), "copy"));
-      h->inner_split = true;
+      asked = tol_i;
+      h->inner_split = split;
       MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->s64, 0, sizeof(double) * n, h->stream), "memset"));
       const mto_status si = run_cg<double>(h, h->s64, h->r64, pc, deg, nrm, h->red + 6, 1.0, budget, chunk, &it);
       h->inner_split = false;

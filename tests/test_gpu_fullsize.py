@@ -115,55 +115,58 @@ def test_fullsize_density_indicator_sampled(mto, name):
     assert pn.min() >= 1 and pn.max() <= 5
 
 
-def energy_compliance(h, f, u, scratch):
-    """C* = 2 f^T u - u^T K u: the compliance as the stationary value of the potential energy,
-    exact at the solution and in error by only ||u - u*||_K^2 elsewhere (second order)."""
-    scratch.zero_()
-    h.apply(u, scratch)
-    return float(2.0 * (f @ u) - (u @ scratch))
+def element_energy(mto, h, u, f, rho, mat, dc, pr):
+    """u^T K(rho) u as sum_s E(rho_s) w_s with w_s = -dc_s / E'(rho_s) from the sensitivity kernel
+    (element-wise, after the rigid-motion removal: free of the cancellation that a global
+    u^T (K u) suffers on compliant designs)."""
+    h.sensitivity(u, f, rho, mat, dc, precision=mto.MTO_FP64, want_C=False)
+    r = rho.cpu().numpy()
+    E = oe.simp(r, pr.E0, pr.Emin, pr.q)
+    dE = oe.simp_deriv(r, pr.E0, pr.Emin, pr.q)
+    return float(np.sum(E * (-dc.cpu().numpy() / dE)))
 
 
 def test_fullsize_energy_split_and_fd_gradient(mto):
-    """dp-adaptive cantilever (smooth densities, all E' > 0): sum_s E_s w_s = u^T K u with
-    w_s = -dc_s / E'(rho_s) (an identity for any u: the sensitivity quadrature against the
-    operator), and the adjoint gradient matches central finite differences (h = 1e-6) of the
-    compliance at 50 seeded design points drawn with probability proportional to |dc|.  Each
-    perturbed compliance is the energy functional 2 f^T u - u^T K(rho +- h) u of a warm-started
-    solve (at h = 1e-6 the change of C is ~1e-11 of C, below any solve's residual, while the
-    functional is exact at the solution and second order in the displacement error)."""
+    """dp-adaptive cantilever (smooth densities, all E' > 0).  (1) sum_s E_s w_s, w_s =
+    -dc_s / E'(rho_s), equals u^T K u from the operator (to 1e-6: the global product loses ~1e-8 to
+    cancellation on this compliant design).  (2) The adjoint gradient against central finite
+    differences of the compliance along 5 seeded random directions over all 1.3M design values:
+    (C(rho + h v) - C(rho - h v)) / 2h = dc . v within 1e-5, each C the energy functional
+    2 f^T u - u^T K u of a re-solved u (exact at the solution, second order in the solve error).
+    h = 1e-4: a single design value moved by 1e-6 changes C by ~1e-11 of C, below what any FP64
+    solve of this size resolves, so the check moves all values along a direction (the oracle's own
+    tests check single-value differences with exact solves on small meshes)."""
     c = full_case(mto, "dp_cantilever_320x160")
     pr, h = c["pr"], c["h"]
-    h.build_elements(c["rho"], c["mat"], mto.MTO_FP64)
+    f, rho, mat = c["gf"], c["rho"], c["mat"]
+    h.build_elements(rho, mat, mto.MTO_FP64)
     u = torch.zeros(h.ndof, dtype=torch.float64, device="cuda")
-    h.solve(c["gf"], u, precision=mto.MTO_FP64, rtol=1e-9, max_iter=40000, precond=mto.PREC_MG,
-            raise_on_noconv=False)
+    h.solve(f, u, precision=mto.MTO_FP64, rtol=1e-8, max_iter=40000, precond=mto.PREC_MG)
     dc = torch.zeros(h.design_len, dtype=torch.float64, device="cuda")
-    h.sensitivity(u, c["gf"], c["rho"], c["mat"], dc, precision=mto.MTO_FP64)
-    dcn = dc.cpu().numpy()
+    h.sensitivity(u, f, rho, mat, dc, precision=mto.MTO_FP64)
+    dcn = dc.cpu().numpy().copy()
     scratch = torch.zeros_like(u)
     h.apply(u, scratch)
     uKu = float(u @ scratch)
-    E = oe.simp(pr.rho, pr.E0, pr.Emin, pr.q)
     dE = oe.simp_deriv(pr.rho, pr.E0, pr.Emin, pr.q)
     assert np.all(dE > 0)
-    w = -dcn / dE
-    assert abs(np.sum(E * w) - uKu) <= 1e-10 * abs(uKu)
+    eK = element_energy(mto, h, u, f, rho, mat, dc, pr)
+    assert abs(eK - uKu) <= 1e-6 * abs(uKu), (eK, uKu)
     rng = np.random.default_rng(181109821 + 3)
-    prob = np.abs(dcn) / np.abs(dcn).sum()
-    pts = rng.choice(len(dcn), 50, replace=False, p=prob)
-    hstep = 1e-6
+    hstep = 1e-4
     u0 = u.clone()
+    work = torch.zeros_like(dc)
     errs = []
-    for s in pts:
+    for _ in range(5):
+        v = rng.choice([-1.0, 1.0], size=len(dcn))
         vals = []
         for sign in (1.0, -1.0):
-            r2 = c["rho"].clone()
-            r2[int(s)] += sign * hstep
-            h.build_elements(r2, c["mat"], mto.MTO_FP64)
+            r2 = rho + sign * hstep * torch.tensor(v, device="cuda")
+            h.build_elements(r2, mat, mto.MTO_FP64)
             u.copy_(u0)
-            h.solve(c["gf"], u, precision=mto.MTO_FP64, rtol=1e-8, max_iter=500, warm_start=True,
-                    precond=mto.PREC_MG, raise_on_noconv=False)
-            vals.append(energy_compliance(h, c["gf"], u, scratch))
+            h.solve(f, u, precision=mto.MTO_FP64, rtol=1e-8, max_iter=40000, warm_start=True, precond=mto.PREC_MG)
+            vals.append(2.0 * float(f @ u) - element_energy(mto, h, u, f, r2, mat, work, pr))
         fd = (vals[0] - vals[1]) / (2 * hstep)
-        errs.append(abs(fd - dcn[s]) / np.abs(dcn).max())
-    assert max(errs) < 1e-5, max(errs)
+        want = float(dcn @ v)
+        errs.append(abs(fd - want) / abs(want))
+    assert max(errs) < 1e-5, errs
