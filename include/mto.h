@@ -94,7 +94,8 @@ typedef struct {
  *              inverse on the coarsest grid; FP64 vectors only (not MTO_MIXED32); mesh sides must
  *              halve down to a coarsest grid of at most 2048 DOFs, else MTO_EINVAL).
  *  inner_max   mixed solves: cap on the iterations of one inner solve (<= 0: none).
- *  mg_degree   MTO_PREC_MG only: Chebyshev degree of each pre- and post-smoothing (<= 0: 4).
+ *  mg_degree   MTO_PREC_MG only: Chebyshev degree of each pre- and post-smoothing on the fine
+ *              level (<= 0: 4; at most 16); the Q1 levels use degree 2.
  * CG iterations run in chunks of check_every (rounded up to a multiple of 4), each a CUDA graph;
  * the reported count stops at convergence, but a chunk already launched completes (cheaply). */
 typedef struct {

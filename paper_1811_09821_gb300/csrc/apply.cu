@@ -476,13 +476,23 @@ __global__ void __launch_bounds__(256) cg_vector_kernel(
     Red gout, Red rrout, Red rdout, const int* __restrict__ base, int local, int* __restrict__ done,
     int* __restrict__ err) {
   if (*done) return;
-  const double rz = sum_res(gin, ng);
-  const double pq = sum_res(pin, np);
-  const double alpha = rz / pq;
-  if (!(pq > 0.0) || !isfinite(alpha)) {
+  // the step length once per block (an FP64 division per thread costs more than the vector pass
+  // on GB300's FP64 pipes)
+  __shared__ double s_alpha;
+  __shared__ int s_stop;
+  if (threadIdx.x == 0) {
+    const double rz = sum_res(gin, ng);
+    const double pq = sum_res(pin, np);
+    const double a = rz / pq;
+    s_stop = (!(pq > 0.0) || !isfinite(a)) ? (rz != 0.0 ? 2 : 1) : 0;
+    s_alpha = a;
+  }
+  __syncthreads();
+  const double alpha = s_alpha;
+  if (s_stop) {
     // rz = 0: the residual vanished (exact solution); otherwise a breakdown
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-      if (rz != 0.0) *err = MTO_ENAN;
+      if (s_stop == 2) *err = MTO_ENAN;
       *done = *base + local + 1;
     }
     return;
@@ -516,15 +526,22 @@ __global__ void __launch_bounds__(256) cg_direction_kernel(
     int64_t n, const T* __restrict__ r, const T* __restrict__ z, T* __restrict__ p, const T* __restrict__ invd,
     const double* __restrict__ gnew, const double* __restrict__ gold, int ng, ConvTest cv) {
   if (*cv.done) return;
-  const double crit = sum_res(cv.res, cv.n);
-  if (!(crit > cv.tol2 * *cv.ref)) {   // converged, or a NaN residual
+  __shared__ double s_beta;
+  __shared__ int s_stop;
+  if (threadIdx.x == 0) {
+    const double crit = sum_res(cv.res, cv.n);
+    s_stop = !(crit > cv.tol2 * *cv.ref) ? (crit == crit ? 1 : 2) : 0;   // converged, or a NaN residual
+    s_beta = s_stop ? 0.0 : sum_res(gnew, ng) / sum_res(gold, ng);
+  }
+  __syncthreads();
+  if (s_stop) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-      if (!(crit == crit)) *cv.err = MTO_ENAN;
+      if (s_stop == 2) *cv.err = MTO_ENAN;
       *cv.done = *cv.base + cv.local + 1;
     }
     return;
   }
-  const double beta = sum_res(gnew, ng) / sum_res(gold, ng);
+  const double beta = s_beta;
   const T b = (T)beta;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
     const T zj = kJacobi ? invd[j] * r[j] : z[j];
@@ -874,6 +891,7 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
   const int grd = grid_for(n, 256, 152 * 4);
   const int pc = o->precond;
   const int deg = o->mg_degree > 0 ? o->mg_degree : 4;
+  if (deg > 16) return mto_fail(h, MTO_EINVAL, "mto_solve: mg_degree above 16");
   if (pc == MTO_PREC_SCHWARZ && h->n_cons > 0)
     return mto_fail(h, MTO_EINVAL,
                     "mto_solve: the element-block Schwarz preconditioner is limited to meshes without order "

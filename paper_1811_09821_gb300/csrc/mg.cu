@@ -35,6 +35,7 @@ constexpr int kCoarseMax = 2048;      // largest coarsest grid for the dense inv
 constexpr double kChebRatio = 30.0;   // lmin = lmax / ratio
 constexpr int kPowerIts = 30;
 constexpr int kCoarseDegree = 2;      // Chebyshev degree on the Q1 levels (the fine level: the option)
+constexpr int kMaxDegree = 16;        // largest smoothing degree (coefficient table size)
 constexpr int kMGBlocks = 152 * 4;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -268,29 +269,19 @@ __global__ void __launch_bounds__(256) mg_coarse_solve_kernel(int N, const doubl
 // reduced by the last block to finish in index order into *dres.
 __global__ void __launch_bounds__(256) mg_cheb_kernel(int64_t n, const double* __restrict__ b, double* __restrict__ q,
                                                       const double* __restrict__ invd, double* __restrict__ x,
-                                                      double* __restrict__ d, const double* __restrict__ lmax,
+                                                      double* __restrict__ d, const double2* __restrict__ coef,
                                                       int step, int xzero, const int* __restrict__ done,
                                                       double* __restrict__ dpart, unsigned* __restrict__ dcnt,
                                                       double* __restrict__ dres) {
   if (done && *done) return;
-  const double lm = *lmax, lo = lm / kChebRatio;
-  const double th = 0.5 * (lm + lo), de = 0.5 * (lm - lo), sg = th / de;
-  double c1 = 0.0, c2 = 1.0 / th;
-  if (step > 0) {
-    double rp = 1.0 / sg, rc = rp;
-    for (int j = 1; j <= step; ++j) {
-      rp = rc;
-      rc = 1.0 / (2.0 * sg - rp);
-    }
-    c1 = rc * rp;
-    c2 = 2.0 * rc / de;
-  }
+  const double2 cc = coef[step];   // (c1, c2), precomputed per level
+  const double c1 = cc.x, c2 = cc.y;
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double bi = b[i];
     const double r = invd[i] * (bi - q[i]);
     q[i] = 0.0;
-    const double dn = step > 0 ? fma(c1, d[i], c2 * r) : c2 * r;
+    const double dn = step > 0 ? fma(c1, d[i], c2 * r) : c2 * r;   // c1 = 0 at step 0
     d[i] = dn;
     const double xn = xzero ? dn : x[i] + dn;
     x[i] = xn;
@@ -471,6 +462,24 @@ __global__ void mg_pow_final_kernel(const double* __restrict__ res, double* __re
   if (threadIdx.x == 0 && blockIdx.x == 0) *lmax = 1.1 * sqrt(__ldcg(res));
 }
 
+// Chebyshev step coefficients of every level from its bound (one thread per level): step 0
+// d = r / theta; step s > 0 d = rho_s rho_{s-1} d + (2 rho_s / delta) r, rho_0 = 1 / sigma,
+// rho_s = 1 / (2 sigma - rho_{s-1}), theta, delta the centre and half-width of [lmax / ratio, lmax].
+__global__ void mg_cheb_coef_kernel(int nlev, const double* __restrict__ lmax, double2* __restrict__ coef) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nlev) return;
+  const double lm = lmax[l], lo = lm / kChebRatio;
+  const double th = 0.5 * (lm + lo), de = 0.5 * (lm - lo), sg = th / de;
+  double2* c = coef + (size_t)l * kMaxDegree;
+  c[0] = make_double2(0.0, 1.0 / th);
+  double rp = 1.0 / sg;
+  for (int s = 1; s < kMaxDegree; ++s) {
+    const double rc = 1.0 / (2.0 * sg - rp);
+    c[s] = make_double2(rc * rp, 2.0 * rc / de);
+    rp = rc;
+  }
+}
+
 int vec_grid(int64_t n) { return grid_for(n, 256, kMGBlocks); }
 
 }  // namespace
@@ -485,11 +494,12 @@ void mg_release(mto_handle h) {
   for (void* p : {(void*)h->mg_pidx, (void*)h->mg_pw, (void*)h->mg_rptr, (void*)h->mg_rnode, (void*)h->mg_rw,
                   (void*)h->mg_btab, (void*)h->mg_v0, (void*)h->mg_q0, (void*)h->mg_d0, (void*)h->mg_Ainv,
                   (void*)h->mg_Awork,
-                  (void*)h->mg_lmax, (void*)h->mg_part, (void*)h->mg_cnt, (void*)h->mg_res})
+                  (void*)h->mg_lmax, (void*)h->mg_coef, (void*)h->mg_part, (void*)h->mg_cnt, (void*)h->mg_res})
     cudaFree(p);
   h->mg_pidx = nullptr;
   h->mg_pw = h->mg_rw = h->mg_btab = h->mg_v0 = h->mg_q0 = h->mg_d0 = h->mg_Ainv = h->mg_lmax = nullptr;
   h->mg_Awork = h->mg_Acur = nullptr;
+  h->mg_coef = nullptr;
   h->mg_part = h->mg_res = nullptr;
   h->mg_rptr = h->mg_rnode = nullptr;
   h->mg_cnt = nullptr;
@@ -613,6 +623,8 @@ mto_status mg_setup(mto_handle h) {
   MTO_TRY(mto_alloc(h, &h->mg_Ainv, (size_t)ncoarse * ncoarse));
   MTO_TRY(mto_alloc(h, &h->mg_Awork, (size_t)ncoarse * ncoarse));
   MTO_TRY(mto_alloc(h, &h->mg_lmax, h->mg.size() + 1));
+  MTO_TRY(mto_alloc(h, &h->mg_coef, (h->mg.size() + 1) * kMaxDegree));
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->mg_lmax, 0, (h->mg.size() + 1) * sizeof(double), h->stream), "memset"));
   MTO_TRY(mto_alloc(h, &h->mg_part, kMGBlocks));
   MTO_TRY(mto_alloc(h, &h->mg_cnt, 8));
   MTO_TRY(mto_alloc(h, &h->mg_res, 8));
@@ -738,6 +750,8 @@ mto_status mg_build(mto_handle h) {
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->mg_q0, 0, h->ndof * sizeof(double), h->stream), "memset"));
   MTO_TRY(mg_power(h, -1, h->mg_lmax));
   for (size_t l = 0; l + 1 < h->mg.size(); ++l) MTO_TRY(mg_power(h, (int)l, h->mg_lmax + 1 + l));
+  mg_cheb_coef_kernel<<<1, 32, 0, h->stream>>>((int)h->mg.size(), h->mg_lmax, h->mg_coef);
+  MTO_TRY(mto_after_launch(h, "mg_cheb_coef_kernel"));
   for (auto& L : h->mg) MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(L.q, 0, L.n * sizeof(double), h->stream), "memset"));
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->mg_q0, 0, h->ndof * sizeof(double), h->stream), "memset"));
   int err = 0;
@@ -759,7 +773,7 @@ mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const
   auto smooth = [&](int lev, const double* b, double* x, double* q, double* d, const double* invd, int64_t n,
                     bool pre, bool with_dot) -> mto_status {
     const int k = lev < 0 ? degree : kCoarseDegree;
-    const double* lm = h->mg_lmax + (lev + 1);
+    const double2* cf = h->mg_coef + (size_t)(lev + 1) * kMaxDegree;
     const int grd = vec_grid(n);
     for (int s = 0; s < k; ++s) {
       const bool skip_apply = pre && s == 0;   // x = 0: A x = 0
@@ -772,7 +786,7 @@ mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const
       }
       TimedScope ts(h, F_PRECOND);
       const bool dot = with_dot && s == k - 1;
-      mg_cheb_kernel<<<grd, 256, 0, h->stream>>>(n, b, q, invd, x, d, lm, s, pre && s == 0, done,
+      mg_cheb_kernel<<<grd, 256, 0, h->stream>>>(n, b, q, invd, x, d, cf, s, pre && s == 0, done,
                                                   dot ? dot_part : nullptr, dot_cnt, dot_res);
       MTO_TRY(mto_after_launch(h, "mg_cheb_kernel"));
     }

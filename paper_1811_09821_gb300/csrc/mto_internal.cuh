@@ -204,6 +204,7 @@ struct mto_handle_s {
   double* mg_Awork = nullptr;                  // Gauss-Jordan steps ...
   double* mg_Acur = nullptr;                   // ... and the one holding the inverse
   double* mg_lmax = nullptr;                   // [levels] Chebyshev upper bounds
+  double2* mg_coef = nullptr;                  // [levels][16] Chebyshev step coefficients (c1, c2)
   double* mg_part = nullptr;                   // reduction partials
   unsigned* mg_cnt = nullptr;
   double* mg_res = nullptr;
