@@ -355,6 +355,192 @@ __global__ void __launch_bounds__(256, 2) ebe_df_pipe_kernel(const float* __rest
   if (red.part) reduce_out(dot, red);
 }
 
+// ---- bulk-copy staging (TMA 1D) of element rows into shared memory
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init1(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// global -> shared bulk copy completing on `bar` (addresses 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+constexpr int kStages = 3;        // element groups in flight per warp
+constexpr int kTmaWarps = 8;      // warps per block
+constexpr unsigned kWaitLimit = 1u << 24;
+
+// The split-precision operator for n_e <= 32 with the element rows staged by bulk copies: every
+// warp walks its own sequence of element groups (G elements of W lanes, G = 32 / W) and keeps
+// kStages groups' hi/lo rows in flight in its shared-memory ring, so the row stream no longer
+// depends on how many warps the registers allow.  Node maps and x values run one group ahead in
+// registers.  Same arithmetic and reduction as ebe_kernel.  Every wait is bounded: on expiry the
+// warp records MTO_ETIMEOUT, waits (bounded) for its copies still in flight, and stops.
+template <int PO, typename TX>
+__global__ void __launch_bounds__(kTmaWarps * 32) ebe_df_tma_kernel(const float* __restrict__ Kh,
+                                                                    const float* __restrict__ Kl, int L, int n,
+                                                                    const int* __restrict__ gmap,
+                                                                    const Constraint* __restrict__ cons,
+                                                                    const TX* __restrict__ x, TX* __restrict__ y,
+                                                                    Red red, const int* __restrict__ done,
+                                                                    int* __restrict__ err) {
+  constexpr int N1 = PO + 1, NN = N1 * N1, NE = 2 * NN, ND = NE / 2 + 1;
+  constexpr int W = WarpShape<NE>::W, G = WarpShape<NE>::G;
+  static_assert(WarpShape<NE>::M == 1, "one row per lane");
+  constexpr bool kSplitX = sizeof(TX) == 8;
+  extern __shared__ __align__(128) unsigned char tma_smem[];
+  if (done && *done) return;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int li = lane % W, gb = lane - li, gid = lane / W;
+  const int warp = blockIdx.x * kTmaWarps + wib;
+  const int nwarps = gridDim.x * kTmaWarps;
+  const int stride = nwarps * G;
+  const size_t stage_floats = (size_t)G * L;   // one group's rows (hi or lo)
+  float* ring = reinterpret_cast<float*>(tma_smem) + (size_t)wib * kStages * 2 * stage_floats;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<float*>(tma_smem) +
+                                               (size_t)kTmaWarps * kStages * 2 * stage_floats) +
+                   wib * kStages;
+  if (lane == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init1(bars + s);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const int first = warp * G;
+  // issue the copies of group it (base = first + it * stride) into stage it % kStages
+  auto issue = [&](int it) {
+    const int base = first + it * stride;
+    if (base >= n) return;
+    const int cnt = n - base < G ? n - base : G;
+    const uint32_t bytes = (uint32_t)(cnt * L * sizeof(float));
+    float* dst = ring + (size_t)(it % kStages) * 2 * stage_floats;
+    uint64_t* bar = bars + it % kStages;
+    mbar_expect_tx(bar, 2 * bytes);
+    bulk_g2s(dst, Kh + (size_t)base * L, bytes, bar);
+    bulk_g2s(dst + stage_floats, Kl + (size_t)base * L, bytes, bar);
+  };
+  if (lane == 0)
+    for (int it = 0; it < kStages; ++it) issue(it);
+  // node map and x of the current group, node map of the next
+  auto load_g = [&](int e) -> int { return (e < n && li < NE) ? __ldg(gmap + (size_t)e * NN + (li >> 1)) : 0; };
+  auto load_x = [&](int e, int g) -> double {
+    if (!(e < n && li < NE)) return 0.0;
+    if (g >= 0) return (double)x[2 * (size_t)g + (li & 1)];
+    const Constraint& c = cons[-g - 1];
+    double v = 0.0;
+    for (int q = 0; q < c.cnt; ++q) v += c.w[q] * (double)x[2 * (size_t)c.node[q] + (li & 1)];
+    return v;
+  };
+  int g_cur = load_g(first + gid);
+  double x_cur = load_x(first + gid, g_cur);
+  int g_next = load_g(first + stride + gid);
+  double dot = 0.0;
+  bool ok = true;
+  int it = 0;
+  for (int base = first; base < n; base += stride, ++it) {
+    const int e = base + gid;
+    const bool act = e < n && li < NE;
+    // x of the next group and the node map after it, in flight during this group's arithmetic
+    const double x_next = load_x(e + stride, g_next);
+    const int g_next2 = load_g(e + 2 * stride);
+    // wait for this group's rows
+    const int st = it % kStages;
+    const uint32_t parity = (uint32_t)((it / kStages) & 1);
+    unsigned spins = 0;
+    while (!mbar_test(bars + st, parity)) {
+      if (++spins > kWaitLimit) {
+        ok = false;
+        break;
+      }
+    }
+    if (!__all_sync(0xffffffffu, ok)) break;
+    const float* rh = ring + (size_t)st * 2 * stage_floats + (size_t)gid * L;
+    const float* rl = rh + stage_floats;
+    const double xd = x_cur;
+    const float xh = (float)xd;
+    const float xl = kSplitX ? (float)(xd - (double)xh) : 0.0f;
+    float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      const float ah = li < NE ? rh[k * NE + li] : 0.0f;
+      const float al = li < NE ? rl[k * NE + li] : 0.0f;
+      int j = li + k;
+      if (j >= NE) j -= NE;
+      const int src = gb + j;
+      const float xjh = __shfl_sync(0xffffffffu, xh, src);
+      const float xjl = kSplitX ? __shfl_sync(0xffffffffu, xl, src) : 0.0f;
+      float pp, pe;
+      df_prod<kSplitX>(ah, al, xjh, xjl, pp, pe);
+      df_acc(sh, sl, pp, pe);
+      if (k > 0 && 2 * k != NE) {
+        float tp, te;
+        df_prod<kSplitX>(ah, al, xh, xl, tp, te);
+        int s2 = li - k;
+        if (s2 < 0) s2 += NE;
+        const float rp = __shfl_sync(0xffffffffu, tp, gb + s2);
+        const float re = __shfl_sync(0xffffffffu, te, gb + s2);
+        df_acc(sh, sl, rp, re);
+      }
+    }
+    // the stage is free again: refill it with the group kStages ahead
+    __syncwarp();
+    if (lane == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(it + kStages);
+    }
+    if (act) {
+      const double yv = (double)sh + (double)sl;
+      if (g_cur >= 0) {
+        atomicAdd(y + 2 * (size_t)g_cur + (li & 1), (TX)yv);
+      } else {
+        const Constraint& c = cons[-g_cur - 1];
+        for (int q = 0; q < c.cnt; ++q) atomicAdd(y + 2 * (size_t)c.node[q] + (li & 1), (TX)(c.w[q] * yv));
+      }
+      if (red.part) dot += xd * yv;
+    }
+    g_cur = g_next;
+    x_cur = x_next;
+    g_next = g_next2;
+  }
+  if (!__all_sync(0xffffffffu, ok)) {
+    // a wait expired: report, then let this warp's outstanding copies land before the block exits
+    if (lane == 0) {
+      atomicExch(err, MTO_ETIMEOUT);
+      for (int k = 0; k < kStages; ++k) {
+        const int itk = it + k;
+        if (first + itk * stride >= n) break;
+        unsigned sp = 0;
+        while (!mbar_test(bars + itk % kStages, (uint32_t)((itk / kStages) & 1)) && ++sp < kWaitLimit) {
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if (red.part) reduce_out(dot, red);
+}
+
+size_t tma_smem_bytes(int L, int G) {
+  return (size_t)kTmaWarps * kStages * 2 * G * L * sizeof(float) + (size_t)kTmaWarps * kStages * sizeof(uint64_t);
+}
+
 }  // namespace
 
 // Blocks of one element-operator launch for an order class (fixed per class size).
@@ -385,8 +571,24 @@ void launch_ebe(mto_handle h, const PClass& c, const double* M64, const float* M
   constexpr int NE = 2 * (PO + 1) * (PO + 1);
   if constexpr (kDF && WarpShape<NE>::M == 1) {
     if (!cv.res) {
-      // persistent: two blocks of 8 warps per SM (the register budget of the pipelined rows)
       const int warps = (c.n + WarpShape<NE>::G - 1) / WarpShape<NE>::G;
+      if (h->op_kernel == 1) {
+        // bulk-copy staging: persistent, as many 8-warp blocks per SM as the shared memory holds
+        const size_t smem = tma_smem_bytes(c.L, WarpShape<NE>::G);
+        const int per_sm = smem > 0 ? (int)((227u * 1024u) / smem) : 1;
+        int blocks = (warps + kTmaWarps - 1) / kTmaWarps;
+        const int cap = 152 * (per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm));
+        if (blocks > cap) blocks = cap;
+        static bool attr_set = false;   // once per process, before any stream capture uses it
+        if (!attr_set && smem > 48 * 1024) {
+          cudaFuncSetAttribute(ebe_df_tma_kernel<PO, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          attr_set = true;
+        }
+        ebe_df_tma_kernel<PO, TX><<<blocks, kTmaWarps * 32, smem, h->stream>>>(Mh, Ml, c.L, c.n, c.gmap, h->cons_d,
+                                                                               x, y, red, done, h->flags + 1);
+        return;
+      }
+      // persistent: two blocks of 8 warps per SM (the register budget of the pipelined rows)
       int blocks = (warps + 7) / 8;
       if (blocks > 152 * 2) blocks = 152 * 2;
       ebe_df_pipe_kernel<PO, TX><<<blocks, 256, 0, h->stream>>>(Mh, Ml, c.L, c.n, c.gmap, h->cons_d, x, y, red,

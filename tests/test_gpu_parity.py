@@ -115,8 +115,9 @@ def test_tensor_core_build_matches_simt(mto, name):
     """The sliced tcgen05 build (d <= 8) and the FP64 CUDA-core build give the same element
     matrices to 1e-13 of each element's largest entry (the slicing keeps ~49 bits of each operand
     against the FP64 sum's 53; cancellation among the subcell terms amplifies both), and the solves
-    on the two builds agree on C to 1e-7 (matrix differences of 1e-13 move C by up to the
-    condition number times that: 7e-9 measured on the dp case)."""
+    on the two builds agree on C to 1e-5: matrix differences of 1e-13 move C by up to the condition
+    number times that (7e-9 on the dp case, 6.5e-7 on the binary beam), which is why the FP64
+    CUDA-core build stays the default for the 1e-8 compliance target."""
     o = oracle_results(name)
     pr, m = o["pr"], o["mesh"]
     h, fixed, f, mat, rho = gpu_setup(mto, pr)
@@ -134,7 +135,7 @@ def test_tensor_core_build_matches_simt(mto, name):
             C[path] = float(f @ u)
         for a, b in zip(got[mto.BUILD_TENSOR], got[mto.BUILD_SIMT]):
             assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
-        assert abs(C[mto.BUILD_TENSOR] - C[mto.BUILD_SIMT]) <= 1e-7 * abs(C[mto.BUILD_SIMT])
+        assert abs(C[mto.BUILD_TENSOR] - C[mto.BUILD_SIMT]) <= 1e-5 * abs(C[mto.BUILD_SIMT])
     h.set_build_path(mto.BUILD_SIMT)
     h.close()
 
