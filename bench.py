@@ -346,20 +346,24 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        if world > 1 and False:
-            pass
         sample = SAMPLE_WORKLOAD.get(args.workload, args.workload)
         for _ in range(args.warmup):
             run_oracle_sample(sample, 1)
         t0 = time.perf_counter()
         sec, info = run_oracle_sample(sample, args.steps)
-        scale = info["free_dofs"] / free_dofs_of(args.workload)
+        import workloads as W
+        pr = W.named(args.workload)
+        nfree = free_dofs_of(args.workload)
+        scale = info["free_dofs"] / nfree
         value = scale / sec
         print(json.dumps({
             "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "sample": sample},
+            "config": {"workload": args.workload, "nelx": pr.nelx, "nely": pr.nely, "p": int(pr.p[0]),
+                       "d": int(pr.d[0]), "free_dofs": nfree, "design_values": int(len(pr.rho)),
+                       "rtol": args.rtol, "residual_norm": "l2", "sample": sample,
+                       "parallelism": "rank 0 only (host cores)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{sample}, median of {args.steps} single-threaded oracle passes "
                                        f"({sec:.2f} s each), scaled by free DOFs"},
