@@ -65,7 +65,10 @@ typedef struct {
 } mto_material;
 
 /* Solver options.
- *  precision   MTO_FP64: one PCG with FP64 vectors on the FP64 element matrices (FP64 pipes).
+ *  precision   MTO_FP64: FP64 iterative refinement: each step forms r = f - K u, solves K d = r
+ *              by an inner PCG on the FP64 element matrices (FP64 pipes) with FP64 vectors to
+ *              inner_rtol relative to r (solving for the correction keeps the recursive CG
+ *              residual from drifting from the true one over long solves), and sets u += d.
  *              MTO_MIXED (needs the MTO_MIXED build): FP64 iterative refinement.  Each step forms
  *              the residual r = f - K u with the FP64 matrices and FP64 vectors, then solves
  *              K d = r by an inner PCG that applies the split-precision pair on the FP32 pipes
@@ -77,10 +80,10 @@ typedef struct {
  *              the inner PCG (converges only on well-conditioned problems; Jacobi or Schwarz).
  *              Dot products are accumulated in FP64 in every mode.
  *  rtol        stop when ||f - K u||_2 <= rtol ||f||_2 (free DOFs, FP64 residual).
- *  inner_rtol  mixed solves: relative residual reduction asked of each inner solve (<= 0: 1e-6).
+ *  inner_rtol  relative residual reduction asked of each inner solve (<= 0: 1e-6); the last
+ *              step asks only the remaining factor.
  *  max_iter    limit on the total number of (inner) PCG iterations.
- *  max_outer   limit on refinement steps (<= 0: 50; the FP64 solve restarts from its FP64
- *              residual when the recursive CG residual met rtol before the true one).
+ *  max_outer   limit on refinement steps (<= 0: 50).
  *  warm_start  nonzero: u on entry is the initial guess (else zero).
  *  check_every PCG iterations between host convergence checks (>= 1).
  *  norm        residual norm of the stopping tests: MTO_NORM_L2 (||r||_2 / ||f||_2) or

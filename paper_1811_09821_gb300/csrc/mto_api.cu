@@ -286,8 +286,9 @@ mto_status mto_create(mto_handle* out, int device, void* stream) {
   // MTO_NO_GRAPHS=1 launches the PCG iterations one kernel at a time instead of replaying captured
   // graphs (same kernels and arithmetic; for profilers that handle graphs poorly)
   if (const char* ng = std::getenv("MTO_NO_GRAPHS")) h->use_graphs = !(ng[0] == '1');
-  // MTO_OP_KERNEL=1 selects the bulk-copy staged split operator (n_e <= 32), 0 the register pipeline
-  if (const char* ok = std::getenv("MTO_OP_KERNEL")) h->op_kernel = ok[0] == '1' ? 1 : 0;
+  // MTO_OP_KERNEL=1 / 0 forces the bulk-copy staged / register-pipelined split operator
+  // (n_e <= 32); by default the staged one serves classes whose rows exceed 64 MB
+  if (const char* ok = std::getenv("MTO_OP_KERNEL")) h->op_kernel = ok[0] == '1' ? 1 : (ok[0] == '0' ? 0 : -1);
   cudaSetDevice(device);
   if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||

@@ -188,7 +188,8 @@ struct mto_handle_s {
   int* cg_base = nullptr;                      // first iteration of the running chunk
   bool schwarz_valid = false;
   bool inner_split = false;                    // operator applies use the split pair (mixed inner solves)
-  int op_kernel = 0;                           // split operator for n_e <= 32: 0 register pipeline, 1 bulk-copy staging
+  int op_kernel = -1;                          // split operator, n_e <= 32: 0 register pipeline, 1 bulk-copy
+                                               // staging, -1 by the size of the class's rows
   // multigrid preconditioner: levels 1.. (Q1), fine-level transfer tables and work vectors
   std::vector<mto::MGLevel> mg;
   bool mg_ok = false, mg_valid = false;
