@@ -177,6 +177,23 @@ def measured_peaks():
         return {}
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's timed milliseconds, on every rank (all-reduce MAX; NCCL on the GPU path,
+    any initialised backend works)."""
+    if world == 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, max_ms):
+    """Steps of all ranks per second of the slowest rank (every rank runs `steps` steps)."""
+    return world * steps / (max_ms * 1e-3)
+
+
 def run_gpu(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -243,13 +260,11 @@ def run_gpu(args, rank, world, local_rank):
         wall0 = time.perf_counter()
         mixed = timed(mto.MTO_MIXED, args.steps, args.warmup)
         wall1 = time.perf_counter()
+    torch.cuda.synchronize(dev)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([mixed["ms"]], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        mixed_ms_max = float(t.item())
-    else:
-        mixed_ms_max = mixed["ms"]
+        dist.barrier()
+    mixed_ms_max = max_over_ranks(mixed["ms"], world, dev)
     C_mixed = h.sensitivity(u, f, rho, mat, dc, precision=mto.MTO_FP64)
 
     fp64 = None
@@ -292,7 +307,7 @@ def run_gpu(args, rank, world, local_rank):
     steps = args.steps
     out = {
         "metric": METRIC,
-        "value": world * steps / (mixed_ms_max * 1e-3),
+        "value": whole_job_rate(world, steps, mixed_ms_max),
         "unit": UNIT,
         "n_gpus": world,
         "steps": steps,

@@ -33,7 +33,7 @@ namespace {
 constexpr int kCoarseTarget = 2048;   // stop coarsening at or below this many DOFs
 constexpr int kCoarseMax = 2048;      // largest coarsest grid for the dense inverse
 constexpr double kChebRatio = 30.0;   // lmin = lmax / ratio
-constexpr int kPowerIts = 40;
+constexpr int kPowerIts = 30;
 constexpr int kCoarseDegree = 2;      // Chebyshev degree on the Q1 levels (the fine level: the option)
 constexpr int kMaxDegree = 16;        // largest smoothing degree (coefficient table size)
 constexpr int kMGBlocks = 152 * 4;
@@ -459,7 +459,7 @@ __global__ void mg_pow_norm_kernel(int64_t n, const double* __restrict__ w, cons
 }
 
 __global__ void mg_pow_final_kernel(const double* __restrict__ res, double* __restrict__ lmax) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *lmax = 1.25 * sqrt(__ldcg(res));
+  if (threadIdx.x == 0 && blockIdx.x == 0) *lmax = 1.1 * sqrt(__ldcg(res));
 }
 
 // Chebyshev step coefficients of every level from its bound (one thread per level): step 0
