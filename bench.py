@@ -29,6 +29,10 @@ sys.path.insert(0, ROOT)
 METRIC = "TO iterations/s (solve+sensitivity) & MDOF·PCG-iter/s, mixed vs plain FP64 GPU"
 UNIT = "TO-iter/s"
 DEFAULT_WORKLOAD = "mbb_160x80_p3_d8"
+# DRAM bytes (read + write) per launch of the split operator ebe_df_pipe_kernel<3,double> on this
+# workload inside the solve, from one ncu capture with warm caches (mean of 3 launches); to be
+# re-taken whenever that kernel changes
+MEASURED_TRAFFIC = {"mbb_160x80_p3_d8": 55921408 + 72619}
 SAMPLE_WORKLOAD = {"mbb_160x80_p3_d8": "mbb_40x20_p3_d8", "dp_cantilever_320x160": "dp_cantilever_40x20",
                    "cantilever_20x10_p2_d4": "cantilever_20x10_p2_d4", "mbb_40x20_p3_d8": "mbb_40x20_p3_d8",
                    "mbb_1024x512_p3_d8": "mbb_40x20_p3_d8", "mbb_480x240_p3_d8": "mbb_40x20_p3_d8"}
@@ -332,9 +336,11 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": mixed["launches"],
         "roofline": {"bound": "hbm", "kernel": f"ebe_kernel<3,split,{'float' if vb == 4 else 'double'}> (element operator)",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "frac": (achieved / hbm) if achieved else None,
+                     "traffic": MEASURED_TRAFFIC.get(args.workload) if args.solve == "mixed" else None,
                      "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_ms * 1e3,
-                     "note": "peak = measured HBM copy; K_e of this workload is L2-resident across CG iterations"},
+                     "note": "peak = measured HBM copy; the element rows stream from DRAM on every launch "
+                             "(the multigrid cycle between launches evicts them from L2)"},
         "clocks": clk.summary(),
         "e2e": {"value": world * steps / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * (dlen + ndof), "d2h_bytes_per_step": 8 * (ndof + dlen)},

@@ -6,7 +6,7 @@
  * One analysis-plus-sensitivity pass per design iteration:
  *   (a) mto_build_elements  K_e = sum_s E(rho_s) K0_s over each element's d x d constant-density
  *                           subcells, SIMP E(rho) = Emin + rho^q (E0 - Emin)      (Eqs. 2-3, App. B)
- *   (b) mto_solve           K u = f by matrix-free Jacobi-preconditioned CG, minimum-rule
+ *   (b) mto_solve           K u = f by matrix-free preconditioned CG (multigrid), minimum-rule
  *                           conformity across p-jumps                              (Eq. 1)
  *   (c) mto_sensitivity     C = f^T u and dC/drho_s = -E'(rho_s) u_e^T K0_s u_e   (self-adjoint)
  *   (d) mto_indicator       Kelly Gamma^a (Eq. 9), density Gamma^d (Sec. 3.2.2), QR error

@@ -1,6 +1,7 @@
-// Step (b): the matrix-free operator y = sum_e P_e^T K_e P_e x and the Jacobi-preconditioned CG
-// solve of K u = f (Eq. 1).  The paper does not name its solver; conformity across p-jumps uses
-// the minimum-rule prolongations P_e built by mto_setup.
+// Step (b): the matrix-free operator y = sum_e P_e^T K_e P_e x and the preconditioned CG solve of
+// K u = f (Eq. 1) inside FP64 iterative refinement (Jacobi, element-block Schwarz or the multigrid
+// cycle of mg.cu as preconditioner).  The paper does not name its solver; conformity across
+// p-jumps uses the minimum-rule prolongations P_e built by mto_setup.
 //
 // Operator layout: one element per group of W lanes (one warp for Q3), element matrices in the
 // circulant-diagonal layout of mto_internal.cuh; see ebe_kernel.
