@@ -334,7 +334,9 @@ def run_gpu(args, rank, world, local_rank):
         "sampled_operator_launches": {k: {"launches": v[0], "avg_us": round(1e3 * v[1] / max(v[0], 1), 3)}
                                       for k, v in mixed["families"].items() if v[0]},
         "gpu_launches": mixed["launches"],
-        "roofline": {"bound": "hbm", "kernel": f"ebe_kernel<3,split,{'float' if vb == 4 else 'double'}> (element operator)",
+        "roofline": {"bound": "hbm",
+                     "kernel": (f"ebe_df_pipe_kernel<3,{'float' if vb == 4 else 'double'}> (split-precision element "
+                                "operator; ebe_df_tma_kernel for classes above 64 MB of rows)"),
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None,
                      "traffic": MEASURED_TRAFFIC.get(args.workload) if args.solve == "mixed" else None,

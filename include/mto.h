@@ -25,8 +25,11 @@
  *    DOF = 2*node + component.  An edge carries order min(p_left, p_right) (minimum rule).
  *  - Pointers documented "device" are caller-owned device memory on the handle's device; "host"
  *    pointers are caller-owned host memory.  The handle owns its tables and workspace.
- *  - All device work is enqueued on the handle's stream.  Calls that return host scalars
- *    (iterations, residuals, compliance) synchronise that stream before returning.
+ *  - Device work is ordered on the caller's stream: each call's work starts after the work
+ *    already queued there and the caller's stream waits for it (CUDA events; internally the
+ *    handle runs on its own non-blocking stream, where the PCG iterations replay as CUDA
+ *    graphs).  Calls that return host scalars (iterations, residuals, compliance) synchronise
+ *    before returning.
  *  - Every call returns an mto_status.  On failure the outputs are unspecified and
  *    mto_last_error(h) gives a message.  Device-side failures (non-convergence, non-finite
  *    values, bounded waits that expire) are reported through status words read back by the
@@ -140,8 +143,9 @@ typedef struct {
   int32_t p_max, d_max;
 } mto_indicator_opts;
 
-/* Create a handle bound to CUDA device `device` and CUDA stream `stream` (a cudaStream_t; NULL
- * means the legacy default stream).  The handle allocates nothing on the device until mto_setup. */
+/* Create a handle bound to CUDA device `device` and the caller's CUDA stream `stream` (a
+ * cudaStream_t; NULL means the legacy default stream).  The handle creates its own non-blocking
+ * stream and a few small buffers; meshes allocate their tables in mto_setup. */
 mto_status mto_create(mto_handle* h, int device, void* stream);
 
 /* Free the handle and all device memory it owns.  Accepts NULL. */

@@ -61,3 +61,15 @@ int main(void) {
     want = [ctypes.sizeof(mto.Material), ctypes.sizeof(mto.SolveOpts), ctypes.sizeof(mto.IndicatorOpts),
             mto.SolveOpts.max_iter.offset, mto.IndicatorOpts.alpha_qr.offset, mto.IndicatorOpts.d_max.offset]
     assert got == want
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """No CPU fallback: loading a missing library raises instead of degrading."""
+    import paper_1811_09821_gb300 as mto
+    saved = mto._lib
+    mto._lib = None
+    try:
+        with pytest.raises(OSError):
+            mto.load_library(str(tmp_path / "libmto_missing.so"))
+    finally:
+        mto._lib = saved
