@@ -140,7 +140,7 @@ def _connected_threshold(s, vol, seed_mask):
 def _sigmoid_volume(s, vol, width=0.35, floor=1e-3):
     """Smooth densities in [floor, 1]: a logistic of s with its offset bisected to mean ``vol``."""
     lo, hi = -10.0, 10.0
-    for _ in range(200):
+    for _ in range(64):   # the interval of 20 is below one ulp after ~60 halvings
         t = 0.5 * (lo + hi)
         r = np.clip(1.0 / (1.0 + np.exp(-(s - t) / width)), floor, 1.0)
         if r.mean() > vol:
