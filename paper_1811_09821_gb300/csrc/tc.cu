@@ -12,8 +12,9 @@
 // and all pairs of one level g = i + j share the weight 2^-7g: each level accumulates its (at most
 // 7) slice GEMMs in one FP32 TMEM accumulator exactly (sums below 2^23).  Levels g = 2..9 are
 // kept (the dropped levels weigh below 2^-47 of the row/column scale); the epilogue adds the
-// levels from the smallest in FP64 (the FP64 matrices) and, for the mixed build, with FP32
-// TwoSum into the hi/lo pair, and rescales by sigma_e tau_pos (powers of two, exact).
+// levels from the smallest with FP32 TwoSum into a hi/lo pair (FP32 pipes), rescales by
+// sigma_e tau_pos (powers of two, exact) and stores hi + lo as the FP64 matrix and, for the
+// mixed build, the pair itself.
 //
 // One CTA (4 warps) per 128 elements: the A slices (7 x 128 x K) are formed in shared memory from
 // rho once; the CTA then walks the N tiles of 64 positions: B slices copied to shared memory, one
@@ -189,23 +190,28 @@ __global__ void __launch_bounds__(128, 1) tc_build_kernel(
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
 
-  // A slices: this thread's element row, moduli E_s scaled by sigma_e and cut into 7 x 7 bits
+  // A slices: this thread's element row, moduli E_s scaled by sigma_e and cut into 7 x 7 bits.
+  // E is monotone in rho, so sigma_e comes from the largest density (one E per element); q = 3
+  // takes products instead of pow (GB300's FP64 pipes made the per-subcell pow the bottleneck).
   {
     const int k = base + t;
-    double m = 0.0;
-    int64_t off = 0;
     const bool act = k < n;
+    const bool cube = q == 3.0;
+    auto modulus = [&](double r) { return Emin + (cube ? r * r * r : pow(r, q)) * (E0 - Emin); };
+    int64_t off = 0;
+    double rmax = 0.0;
     if (act) {
       off = design_off[elem[k]];
-      for (int s = 0; s < S; ++s) m = fmax(m, Emin + pow(rho[off + s], q) * (E0 - Emin));
+      for (int s = 0; s < S; ++s) rmax = fmax(rmax, rho[off + s]);
     }
+    const double m = act ? modulus(rmax) : 0.0;
     int ex = 0;
     if (m > 0.0) frexp(m, &ex);
     const double sc = ldexp(1.0, -ex);
     sigma_s[t] = m > 0.0 ? ldexpf(1.0f, ex) : 0.0f;
     for (int s = 0; s < kpad; ++s) {
       double v = 0.0;
-      if (act && s < S) v = (Emin + pow(rho[off + s], q) * (E0 - Emin)) * sc;   // [0, 1)
+      if (act && s < S) v = modulus(rho[off + s]) * sc;   // [0, 1)
       const unsigned long long V = (unsigned long long)(v * 562949953421312.0);
       for (int i = 0; i < kSlices; ++i) {
         const float a = (float)((V >> (49 - kSliceBits * (i + 1))) & 127ull);
@@ -275,12 +281,10 @@ __global__ void __launch_bounds__(128, 1) tc_build_kernel(
 #pragma unroll 1
     for (int ch = 0; ch < kTN / 16; ++ch) {
       float sh[16], slo[16];
-      double sd[16];
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         sh[c] = 0.0f;
         slo[c] = 0.0f;
-        sd[c] = 0.0;
       }
 #pragma unroll 1
       for (int g = kLevels - 1; g >= 0; --g) {
@@ -289,11 +293,7 @@ __global__ void __launch_bounds__(128, 1) tc_build_kernel(
         tmem_wait_ld();
         const float wgt = ldexpf(1.0f, -kSliceBits * (g + 2));
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const float t = __uint_as_float(v[c]) * wgt;   // exact: integer below 2^23 times 2^-7g
-          sd[c] += (double)t;                             // FP64 sum of the levels (the K64 output)
-          if (Kh) two_sum(sh[c], slo[c], t);              // FP32 pair (the split output)
-        }
+        for (int c = 0; c < 16; ++c) two_sum(sh[c], slo[c], __uint_as_float(v[c]) * wgt);   // exact terms
       }
       if (act) {
         const int pos0 = tile * kTN + ch * 16;
@@ -302,11 +302,11 @@ __global__ void __launch_bounds__(128, 1) tc_build_kernel(
           const int pos = pos0 + c;
           if (pos >= L) break;
           const float sc = sig * __ldg(tau + pos);
+          const float hi = sh[c] + slo[c];
+          const float lo = slo[c] - (hi - sh[c]);
           const size_t o = (size_t)sl * L + pos;
-          K64[o] = sd[c] * (double)sc;
+          K64[o] = (double)(hi * sc) + (double)(lo * sc);
           if (Kh) {
-            const float hi = sh[c] + slo[c];
-            const float lo = slo[c] - (hi - sh[c]);
             Kh[o] = hi * sc;
             Kl[o] = lo * sc;
           }
