@@ -316,3 +316,39 @@ def load_case(handle, load):
 
 def material(E0=1.0, Emin=1e-9, nu=0.3, q=3.0):
     return Material(E0, Emin, nu, q)
+
+
+class ComplianceFn(torch.autograd.Function):
+    """Compliance C(rho) = f^T u(rho) as a differentiable torch function.
+
+    forward: mto_build_elements + mto_solve, C = f^T u by mto_compliance_noalloc (the library's
+    kernels); keeps u.  backward: the adjoint of
+    the self-adjoint compliance problem is lambda = -u, so dC/drho_s = -E'(rho_s) u_e^T K0_s u_e is
+    one mto_sensitivity launch on the stored u (no per-subcell products are kept).
+    Use through ``compliance(handle, rho, f, mat, ...)``."""
+
+    @staticmethod
+    def forward(ctx, rho, handle, f, mat, precision, solve_opts):
+        handle.build_elements(rho, mat, precision)
+        u = torch.zeros(handle.ndof, dtype=torch.float64, device=rho.device)
+        handle.solve(f, u, precision=precision, **solve_opts)
+        ctx.handle, ctx.mat = handle, mat
+        ctx.save_for_backward(rho, f, u)
+        c = torch.empty((), dtype=torch.float64, device=rho.device)
+        st = compliance_noalloc(f, u, c, device=handle.device.index or 0, stream=handle.stream)
+        if st != 0:
+            raise MTOError(st, "mto_compliance_noalloc failed")
+        return c
+
+    @staticmethod
+    def backward(ctx, grad_c):
+        rho, f, u = ctx.saved_tensors
+        dc = torch.empty_like(rho)
+        ctx.handle.sensitivity(u, f, rho, ctx.mat, dc, precision=MTO_FP64, want_C=False)
+        return grad_c * dc, None, None, None, None, None
+
+
+def compliance(handle, rho, f, mat, precision=MTO_MIXED, **solve_opts):
+    """Differentiable compliance of the design rho (device float64, packed) on a set-up handle with
+    supports: C = f^T u with K(rho) u = f; ``C.backward()`` fills ``rho.grad`` with dC/drho."""
+    return ComplianceFn.apply(rho, handle, f, mat, precision, solve_opts)

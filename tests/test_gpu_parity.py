@@ -340,3 +340,19 @@ def test_errors_are_reported_not_trapped(mto):
     it, rr = h.solve(f0, u)
     assert it == 0 and float(u.abs().max()) == 0.0
     h.close()
+
+
+def test_autograd_compliance_matches_oracle(mto):
+    """The autograd wrapper: C from the forward (build + solve) and rho.grad from the backward (one
+    sensitivity launch on the stored u) against the oracle's C and dC/drho."""
+    o = oracle_results("dp_cantilever_40x20")
+    pr = o["pr"]
+    h, fixed, f, mat, rho = gpu_setup(mto, pr)
+    r = rho.clone().requires_grad_(True)
+    C = mto.compliance(h, r, f, mat, precision=mto.MTO_MIXED, rtol=1e-10, norm=mto.NORM_JACOBI,
+                       max_iter=40000, precond=mto.PREC_MG, raise_on_noconv=False)
+    C.backward()
+    assert abs(float(C.detach()) - o["C"]) < 1e-8 * abs(o["C"])
+    g = r.grad.cpu().numpy()
+    assert np.abs(g - o["dc"]).max() < 1e-6 * np.abs(o["dc"]).max()
+    h.close()
