@@ -22,7 +22,7 @@ and DOF = 2*node + component.
 """
 import numpy as np
 
-from .basis import gll_nodes, lagrange
+from .basis import gauss_legendre, gll_nodes, lagrange
 
 
 class DPMesh:
@@ -200,4 +200,41 @@ def mbb_bc(mesh):
     fixed = np.sort(np.concatenate([2 * left, [2 * mesh.vertex(mesh.nelx, 0) + 1]]))
     f = np.zeros(mesh.ndof)
     f[2 * mesh.vertex(0, mesh.nely) + 1] = -1.0
+    return fixed, f
+
+
+def side_edges(mesh, side):
+    """The boundary edges of one side in order (0 = left, 1 = right, 2 = bottom, 3 = top): a list of
+    (global nodes in parameter order, edge order p_E, edge length)."""
+    nx, ny = mesh.nelx, mesh.nely
+    if side in (0, 1):
+        ix = 0 if side == 0 else nx
+        return [mesh._edge_nodes_v(ix, iy) + (mesh.hy,) for iy in range(ny)]
+    iy = 0 if side == 2 else ny
+    return [mesh._edge_nodes_h(ix, iy) + (mesh.hx,) for ix in range(nx)]
+
+
+def side_load(mesh, side, comp, traction):
+    """Consistent nodal loads of a uniform traction (force per unit length, component ``comp``)
+    on one side of the domain: f_k = traction * integral over the side of N_k ds, summed over the
+    boundary edges.  On an edge of order p_E the trace of N_k is the Lagrange polynomial l_k of
+    the edge's GLL nodes; its integral is taken with a (p_E + 1)-point Gauss-Legendre rule (exact
+    for degree p_E).  Returns the load vector [ndof]."""
+    f = np.zeros(mesh.ndof)
+    for nodes, pE, length in side_edges(mesh, side):
+        g, w = gauss_legendre(pE + 1)
+        L = lagrange(gll_nodes(pE), g)          # L[k, j] = l_k(g_j)
+        for k, node in enumerate(nodes):
+            f[2 * node + comp] += traction * 0.5 * length * float(L[k] @ w)
+    return f
+
+
+def distributed_cantilever_bc(mesh, total=1.0):
+    """Cantilever with a distributed load (Sec. 4.1, Fig. 6a): left edge clamped, a uniform
+    downward traction on the top edge.  The paper's F = 0.5 N/L on a 2L-wide top edge is a total
+    load of 1 N; here the traction is -total / (nelx hx), so the total load is ``total``.
+    Returns (fixed DOFs, load vector)."""
+    left = mesh.side_nodes(0)
+    fixed = np.sort(np.concatenate([2 * left, 2 * left + 1]))
+    f = side_load(mesh, 3, 1, -total / (mesh.nelx * mesh.hx))
     return fixed, f
