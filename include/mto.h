@@ -172,6 +172,14 @@ mto_status mto_setup(mto_handle h, int32_t nelx, int32_t nely, double hx, double
  * Errors: MTO_EINVAL for an index outside 0..ndof-1. */
 mto_status mto_set_supports(mto_handle h, const int64_t* fixed, int64_t n);
 
+/* Linear springs to ground, for the compliant-mechanism problem of Sec. 4.1 (Fig. 6b: k_in at the
+ * input DOF, k_out at the output DOF): the operator of every later solve and apply becomes
+ * K + sum_i k_i e_{d_i} e_{d_i}^T (also in the Jacobi diagonal and the multigrid fine level).
+ * dofs: host int64[n] global DOFs; k: host double[n] > 0 (stiffnesses on one DOF add up).
+ * Replaces earlier springs; n = 0 removes them.  mto_setup clears them.  At most 1024.
+ * Errors: MTO_EINVAL for a DOF out of range or k <= 0.  Synchronises. */
+mto_status mto_set_springs(mto_handle h, const int64_t* dofs, const double* k, int64_t n);
+
 /* Global DOF of component `comp` (0 = x, 1 = y) at mesh vertex (ix, iy), 0 <= ix <= nelx,
  * 0 <= iy <= nely.  Host output. */
 mto_status mto_vertex_dof(mto_handle h, int32_t ix, int32_t iy, int32_t comp, int64_t* dof);
@@ -181,6 +189,29 @@ mto_status mto_vertex_dof(mto_handle h, int32_t ix, int32_t iy, int32_t comp, in
  * capacity `cap`; *count receives the number of DOFs (call with cap = 0 to size the buffer). */
 mto_status mto_side_dofs(mto_handle h, int32_t side, int32_t comp, int64_t* out, int64_t cap,
                          int64_t* count);
+
+/* Global DOFs of component `comp` (0 = x, 1 = y) of the nodes of one mesh edge, in parameter order
+ * (start vertex, the interior nodes of the edge's order, end vertex): dir 0 is the horizontal edge
+ * from vertex (ix, iy) to (ix + 1, iy), dir 1 the vertical edge from (ix, iy) to (ix, iy + 1).
+ * Node lookup for loads and supports anywhere on the mesh (vertex and edge nodes).  Host output
+ * of capacity `cap`; *count receives p_E + 1, p_E the edge's order (minimum rule).
+ * Errors: MTO_EINVAL for an edge outside the mesh. */
+mto_status mto_edge_dofs(mto_handle h, int32_t dir, int32_t ix, int32_t iy, int32_t comp, int64_t* out,
+                         int64_t cap, int64_t* count);
+
+/* Consistent nodal loads of a uniform traction on one side of the domain (the distributed load of
+ * Sec. 4.1, Fig. 6a): for every node k of side `side` (0 = left, 1 = right, 2 = bottom, 3 = top)
+ * f[2k + comp] += traction * (integral over the side of N_k ds).  On a boundary edge of order p_E
+ * a node's trace is a Lagrange polynomial of the edge's Gauss-Lobatto-Legendre nodes, whose
+ * integral is the GLL weight times half the edge length.  traction: force per unit length;
+ * f: device double[ndof], accumulated into.  Synchronises. */
+mto_status mto_side_load(mto_handle h, int32_t side, int32_t comp, double traction, double* f);
+
+/* As mto_side_dofs, restricted to the nodes whose coordinate along the side (x for the bottom and
+ * top sides, y for the left and right sides, from the domain corner at the origin) lies in
+ * [s0, s1]: partial supports such as the corner clamps of the force inverter (Sec. 4.1, Fig. 6b). */
+mto_status mto_side_dofs_in(mto_handle h, int32_t side, int32_t comp, double s0, double s1, int64_t* out,
+                            int64_t cap, int64_t* count);
 
 /* Inspection of the numbering (for tests and tools): for element e, fills per local node
  * (row-major, (p_e+1)^2 nodes) up to 8 (global node, weight) pairs: nodes[ln*8 + k],
@@ -212,6 +243,12 @@ mto_status mto_element_matrix(mto_handle h, int64_t e, double* packed);
 #define MTO_BUILD_SIMT 1
 mto_status mto_set_build_path(mto_handle h, int32_t path);
 
+/* Compliance C = f^T u (Eq. 1 with z = f) of a solved displacement, reduced in the handle's own
+ * workspace (fixed order: repeated calls give identical results).  f, u: device double[ndof].
+ * C_dev: device double (may be NULL) receives C on the stream; C: host double (may be NULL;
+ * then no synchronisation).  At least one of the two must be given. */
+mto_status mto_compliance(mto_handle h, const double* f, const double* u, double* C_dev, double* C);
+
 /* Step (b): solve K u = f on the free DOFs (u = 0 on supports) with the options above, using the
  * matrices of the last mto_build_elements.  f: device double[ndof]; u: device double[ndof]
  * (initial guess when opts->warm_start, overwritten with the solution).  *iters receives the
@@ -225,6 +262,33 @@ mto_status mto_solve(mto_handle h, const double* f, double* u, const mto_solve_o
  * matrices of the last build.  x, y: device double[ndof].  Asynchronous. */
 mto_status mto_apply(mto_handle h, const double* x, double* y);
 
+/* y = K x with a chosen operator (tests and tools), over all DOFs like mto_apply.  op:
+ *   MTO_OP_FP64   the FP64 element matrices on the FP64 pipes (plain FP64 path, refinement residuals);
+ *   MTO_OP_SPLIT  the split-precision pair on the FP32 pipes with FP64 vectors: exactly the kernels the
+ *                 inner PCG of MTO_MIXED solves launches (needs the MTO_MIXED build).
+ * x, y: device double[ndof].  *xKx (host, may be NULL: then asynchronous) receives x^T y as the
+ * operator launches reduce it for CG (per order class, summed in class order).  Synchronises when
+ * xKx is given. */
+#define MTO_OP_FP64 0
+#define MTO_OP_SPLIT 1
+mto_status mto_apply_operator(mto_handle h, int32_t op, const double* x, double* y, double* xKx);
+
+/* Kernel of the split-precision operator for orders with n_e <= 32 (p <= 3); orders above always use
+ * the generic kernel.  MTO_OPK_AUTO (default): the register-pipelined persistent kernel, or the
+ * bulk-copy staged kernel for classes whose split rows exceed 64 MB; MTO_OPK_PIPE / MTO_OPK_STAGED
+ * force one of them; MTO_OPK_GENERIC the plain one-pass kernel.  Applies to later solves and
+ * mto_apply_operator calls (captured iteration graphs are discarded).  Synchronises the stream. */
+#define MTO_OPK_AUTO -1
+#define MTO_OPK_PIPE 0
+#define MTO_OPK_STAGED 1
+#define MTO_OPK_GENERIC 2
+mto_status mto_set_operator_kernel(mto_handle h, int32_t kernel);
+
+/* Inspection (tests, tools): the split-precision pair of element e after an MTO_MIXED build, as two
+ * packed upper triangles (row-major, i <= j): hi[c] = fl32(K_e[c]), lo[c] = fl32(K_e[c] - hi[c]).
+ * Host outputs of n_e (n_e + 1) / 2 floats each.  Allocates a small device buffer; synchronises. */
+mto_status mto_element_matrix_split(mto_handle h, int64_t e, float* hi, float* lo);
+
 /* Step (c): compliance C = f^T u (Eq. 1 with z = f) and the design sensitivities
  * dc[s] = -E'(rho_s) u_e^T K0_s u_e, E'(rho) = q rho^(q-1) (E0 - Emin): the adjoint of the
  * self-adjoint compliance problem is -u.  u, f: device double[ndof]; rho, dc: device
@@ -233,6 +297,36 @@ mto_status mto_apply(mto_handle h, const double* x, double* y);
  * element's rigid-body motion. */
 mto_status mto_sensitivity(mto_handle h, const double* u, const double* f, const double* rho,
                            const mto_material* mat, int32_t precision, double* dc, double* C);
+
+/* Design transfer after a dp map update (Sec. 3.3; the paper does not say how design values move
+ * to new design points): with the handle set up on the new maps, rho_new (device, packed for the
+ * handle's current d map) receives for every new subcell the area-weighted mean of the old
+ * subcells of the same element it overlaps; an element whose count did not change keeps its
+ * values.  d_old: host int32[nel] per-axis counts of the old layout; rho_old: device, packed for
+ * d_old.  Keeps every element's material volume.  Synchronises. */
+mto_status mto_transfer_design(mto_handle h, const int32_t* d_old, const double* rho_old, double* rho_new);
+
+/* The P2 density filter (Sec. 2.1, Eqs. 4-5) evaluated at the subcell centres:
+ * rho_f[s] = sum_t H_st rho[t] / sum_t H_st with H_st = radius - dist(c_s, c_t) over every subcell t of
+ * the mesh whose centre c_t lies within `radius` of c_s (across element edges; no volume weights,
+ * as printed).  The filtered densities are the physical densities that the build takes
+ * (K_e = sum_s E(rho_f[s]) K0_s); the paper uses radius = 0.3 h (Sec. 4.1).  rho, rho_f: device
+ * double[design_len], distinct.  radius in (0, 4 min(hx, hy)].  Asynchronous. */
+mto_status mto_filter(mto_handle h, double radius, const double* rho, double* rho_f);
+
+/* Adjoint of mto_filter (the chain rule of the sensitivities): g[t] = sum_s H_st g_f[s] / W_s with
+ * W_s = sum_k H_sk, i.e. dJ/drho from dJ/drho_f.  g_f, g: device double[design_len], distinct.
+ * Asynchronous. */
+mto_status mto_filter_adjoint(mto_handle h, double radius, const double* g_f, double* g);
+
+/* Step (c) for a general objective J = z^T u (Eq. 1; the force inverter of Sec. 4.1 has z = the
+ * unit vector of the output DOF): dJ/drho_s = -E'(rho_s) v_e^T K0_s u_e, where v is the adjoint
+ * field solving K v = z (call mto_solve with f = z; the operator, springs included, is
+ * symmetric).  For compliance z = f, so v = u and this equals mto_sensitivity.  u, v: device
+ * double[ndof]; rho, dc: device double[design_len].  FP64 quadrature after an FP64 removal of
+ * each field's element rigid motion.  Asynchronous. */
+mto_status mto_sensitivity_adjoint(mto_handle h, const double* u, const double* v, const double* rho,
+                                   const mto_material* mat, double* dc);
 
 /* Step (d): composite refinement indicator and dp map update (Sec. 3.2, 3.3).
  * u: device double[ndof] (the solved displacement), rho: device double[design_len].
@@ -293,8 +387,9 @@ mto_status mto_launch_count(mto_handle h, int64_t* count);
  * again.  The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call outside any stream
  * capture.  Calls that overlap in time on the same device (different streams, host threads)
- * share the array and race: order them on one stream or with events.  The summation order
- * depends only on n, so repeated calls give bit-identical results.  Asynchronous; returns
+ * share the array and race: order them on one stream or with events.  The address is kept for the
+ * life of the process: do not call this across a cudaDeviceReset.  The summation order depends
+ * only on n, so repeated calls give bit-identical results.  Asynchronous; returns
  * MTO_ECUDA when a CUDA call fails. */
 mto_status mto_compliance_noalloc(int32_t device, const double* f, const double* u, int64_t n, void* stream,
                                   double* C);

@@ -7,6 +7,7 @@
 
 Readings where the paper is silent or garbled are stated in each docstring.
 """
+import functools
 import math
 
 import numpy as np
@@ -32,6 +33,16 @@ def _edge_dn(p, side, t, hx, hy):
     return Ny
 
 
+@functools.lru_cache(maxsize=None)
+def _edge_dn_rule(p, side, pF, hx, hy):
+    """``_edge_dn`` at the (pF+1)-point Gauss nodes of an edge, with the weights (a pure function of
+    its small integer arguments, kept once per combination)."""
+    g, w = gauss_legendre(pF + 1)
+    dn = _edge_dn(p, side, g, hx, hy)
+    dn.setflags(write=False)
+    return dn, w
+
+
 def kelly(mesh, u):
     """Gamma^a_i = sum over faces F of element i of c_F * integral_F [du/dn]^2 ds (Eq. 9).
 
@@ -50,9 +61,8 @@ def kelly(mesh, u):
     def jump_integral(eA, sideA, eB, sideB, length):
         pA, pB = int(mesh.p[eA]), int(mesh.p[eB])
         pF = max(pA, pB)
-        g, w = gauss_legendre(pF + 1)
-        dA = _edge_dn(pA, sideA, g, mesh.hx, mesh.hy)
-        dB = _edge_dn(pB, sideB, g, mesh.hx, mesh.hy)
+        dA, w = _edge_dn_rule(pA, sideA, pF, mesh.hx, mesh.hy)
+        dB, _ = _edge_dn_rule(pB, sideB, pF, mesh.hx, mesh.hy)
         val = 0.0
         for c in range(2):
             jmp = dA.T @ ue[eA][c::2] - dB.T @ ue[eB][c::2]
@@ -122,6 +132,7 @@ def qr_fixed_local_dofs(p):
     return np.array([0, 1, 2 * p + 1])
 
 
+@functools.lru_cache(maxsize=None)
 def qr_load_transfer(p):
     """Matrix R with f^(p+1) = R f^(p) (reading of Sec. 3.2.3's load transfer).
 
@@ -133,7 +144,17 @@ def qr_load_transfer(p):
     """
     Mp = vector_dofs(scalar_mass(p, p))
     M1p = vector_dofs(scalar_mass(p + 1, p))
-    return M1p @ np.linalg.inv(Mp)
+    R = M1p @ np.linalg.inv(Mp)
+    R.setflags(write=False)
+    return R
+
+
+@functools.lru_cache(maxsize=None)
+def _prolong_vec(p):
+    """Vector-DOF nodal interpolation from order p to p + 1 (kept once per order)."""
+    T = vector_dofs(interpolation_matrix(p, p + 1))
+    T.setflags(write=False)
+    return T
 
 
 def qr_error_element(p, d, rho_e, ue, E0, Emin, nu, q, hx=1.0, hy=1.0, fixed=None):
@@ -155,7 +176,7 @@ def qr_error_element(p, d, rho_e, ue, E0, Emin, nu, q, hx=1.0, hy=1.0, fixed=Non
     K1 = np.tensordot(E, K0_table(p + 1, d, nu, hx, hy), axes=(0, 0))
     fp = Kp @ ue
     f1 = qr_load_transfer(p) @ fp
-    T = vector_dofs(interpolation_matrix(p, p + 1))
+    T = _prolong_vec(p)
     fx = qr_fixed_local_dofs(p + 1) if fixed is None else np.asarray(fixed)
     fr = np.setdiff1d(np.arange(K1.shape[0]), fx)
     u1 = np.zeros(K1.shape[0])

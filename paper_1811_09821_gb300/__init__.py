@@ -20,10 +20,13 @@ LIB_PATH = os.path.join(_HERE, "libmto.so")
 MTO_FP64, MTO_MIXED, MTO_MIXED32 = 0, 1, 2
 NORM_L2, NORM_JACOBI = 0, 1
 BUILD_TENSOR, BUILD_SIMT = 0, 1
+OP_FP64, OP_SPLIT = 0, 1
+OPK_AUTO, OPK_PIPE, OPK_STAGED, OPK_GENERIC = -1, 0, 1, 2
 PREC_JACOBI, PREC_SCHWARZ, PREC_MG = 0, 1, 2
 STATUS = {0: "MTO_OK", 1: "MTO_EINVAL", 2: "MTO_ENOMEM", 3: "MTO_ECUDA", 4: "MTO_ENOCONV", 5: "MTO_ENAN",
           6: "MTO_ETIMEOUT"}
 P_MAX, D_MAX = 6, 16
+MTO_P_MAX_NODES = P_MAX + 2
 
 
 class MTOError(RuntimeError):
@@ -61,7 +64,10 @@ SYMBOLS = ["mto_create", "mto_destroy", "mto_last_error", "mto_set_stream", "mto
            "mto_vertex_dof", "mto_side_dofs", "mto_element_nodes", "mto_element_matrix", "mto_build_elements", "mto_solve", "mto_apply",
            "mto_sensitivity", "mto_indicator", "mto_map_update", "mto_oc_update", "mto_timing_enable", "mto_timing_read",
            "mto_set_build_path",
-           "mto_memory", "mto_launch_count", "mto_compliance_noalloc"]
+           "mto_memory", "mto_launch_count", "mto_compliance_noalloc", "mto_compliance", "mto_apply_operator",
+           "mto_set_operator_kernel", "mto_element_matrix_split", "mto_edge_dofs", "mto_side_load",
+           "mto_set_springs", "mto_sensitivity_adjoint", "mto_side_dofs_in",
+           "mto_filter", "mto_filter_adjoint", "mto_transfer_design"]
 TIME_FAMILIES = {"apply32": 0, "apply64": 1, "build": 2, "sens": 3, "indicator": 4, "vector": 5, "applydf64": 6,
                  "precond": 7}
 
@@ -102,6 +108,18 @@ def load_library(path=LIB_PATH):
         "mto_memory": ([vp, P(i64)], ctypes.c_int),
         "mto_launch_count": ([vp, P(i64)], ctypes.c_int),
         "mto_compliance_noalloc": ([i32, vp, vp, i64, vp, vp], ctypes.c_int),
+        "mto_compliance": ([vp, vp, vp, vp, P(dbl)], ctypes.c_int),
+        "mto_edge_dofs": ([vp, i32, i32, i32, i32, P(i64), i64, P(i64)], ctypes.c_int),
+        "mto_side_load": ([vp, i32, i32, dbl, vp], ctypes.c_int),
+        "mto_set_springs": ([vp, P(i64), P(dbl), i64], ctypes.c_int),
+        "mto_side_dofs_in": ([vp, i32, i32, dbl, dbl, P(i64), i64, P(i64)], ctypes.c_int),
+        "mto_filter": ([vp, dbl, vp, vp], ctypes.c_int),
+        "mto_transfer_design": ([vp, P(i32), vp, vp], ctypes.c_int),
+        "mto_filter_adjoint": ([vp, dbl, vp, vp], ctypes.c_int),
+        "mto_sensitivity_adjoint": ([vp, vp, vp, vp, P(Material), vp], ctypes.c_int),
+        "mto_apply_operator": ([vp, i32, vp, vp, P(dbl)], ctypes.c_int),
+        "mto_set_operator_kernel": ([vp, i32], ctypes.c_int),
+        "mto_element_matrix_split": ([vp, i64, P(ctypes.c_float), P(ctypes.c_float)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -151,6 +169,7 @@ class Handle:
 
     # ---------------------------------------------------------------- mesh and supports
     def setup(self, nelx, nely, p, d, hx=1.0, hy=1.0):
+        self.hx, self.hy = hx, hy
         p = np.ascontiguousarray(p, dtype=np.int32)
         d = np.ascontiguousarray(d, dtype=np.int32)
         nd, dl = ctypes.c_int64(), ctypes.c_int64()
@@ -166,6 +185,13 @@ class Handle:
         self._check(self.L.mto_set_supports(self.h, fixed.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                             len(fixed)))
 
+    def set_springs(self, dofs, k):
+        """Springs to ground k_i at global DOFs dofs_i (operator K + sum k_i e e^T)."""
+        dofs = np.ascontiguousarray(dofs, dtype=np.int64)
+        k = np.ascontiguousarray(k, dtype=np.float64)
+        self._check(self.L.mto_set_springs(self.h, dofs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                           k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(dofs)))
+
     def vertex_dof(self, ix, iy, comp):
         out = ctypes.c_int64()
         self._check(self.L.mto_vertex_dof(self.h, ix, iy, comp, ctypes.byref(out)))
@@ -178,6 +204,31 @@ class Handle:
         self._check(self.L.mto_side_dofs(self.h, side, comp, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                          n.value, ctypes.byref(n)))
         return out
+
+    def side_dofs_in(self, side, comp, s0, s1):
+        """side_dofs restricted to nodes whose coordinate along the side lies in [s0, s1]."""
+        n = ctypes.c_int64()
+        self._check(self.L.mto_side_dofs_in(self.h, side, comp, s0, s1, None, 0, ctypes.byref(n)))
+        out = np.zeros(n.value, dtype=np.int64)
+        self._check(self.L.mto_side_dofs_in(self.h, side, comp, s0, s1,
+                                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n.value,
+                                            ctypes.byref(n)))
+        return out
+
+    def edge_dofs(self, direction, ix, iy, comp):
+        """DOFs (component comp) of the nodes of mesh edge (direction 0: horizontal from vertex
+        (ix, iy); 1: vertical), in parameter order."""
+        n = ctypes.c_int64()
+        out = np.zeros(MTO_P_MAX_NODES, dtype=np.int64)
+        self._check(self.L.mto_edge_dofs(self.h, direction, ix, iy, comp,
+                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(out),
+                                         ctypes.byref(n)))
+        return out[:n.value].copy()
+
+    def side_load(self, side, comp, traction, f):
+        """f += consistent nodal loads of a uniform traction on one side (device float64 [ndof])."""
+        self._check(self.L.mto_side_load(self.h, side, comp, traction, _ptr(f, torch.float64)))
+        return f
 
     def element_nodes(self, e):
         """Per local node of element e: list of (global node, weight) (minimum-rule map)."""
@@ -221,12 +272,68 @@ class Handle:
     def apply(self, x, y):
         self._check(self.L.mto_apply(self.h, _ptr(x, torch.float64), _ptr(y, torch.float64)))
 
+    def apply_operator(self, x, y, op=OP_FP64, want_xKx=True):
+        """y = K x with the FP64 matrices (OP_FP64) or the split-precision pair (OP_SPLIT, the inner
+        PCG's kernels); returns x^T K x as the launches reduce it (or None)."""
+        v = ctypes.c_double()
+        self._check(self.L.mto_apply_operator(self.h, op, _ptr(x, torch.float64), _ptr(y, torch.float64),
+                                              ctypes.byref(v) if want_xKx else None))
+        return v.value if want_xKx else None
+
+    def set_operator_kernel(self, kernel):
+        self._check(self.L.mto_set_operator_kernel(self.h, kernel))
+
+    def element_matrix_split(self, e, p):
+        """(hi, lo) packed upper triangles (float32) of element e's split-precision pair."""
+        ne = 2 * (p + 1) ** 2
+        P = ne * (ne + 1) // 2
+        hi, lo = np.zeros(P, np.float32), np.zeros(P, np.float32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        self._check(self.L.mto_element_matrix_split(self.h, e, hi.ctypes.data_as(fp), lo.ctypes.data_as(fp)))
+        return hi, lo
+
+    def compliance(self, f, u, out=None):
+        """C = f^T u in the handle's workspace: into the device scalar ``out`` (asynchronous) when
+        given, else returned as a float."""
+        if out is not None:
+            self._check(self.L.mto_compliance(self.h, _ptr(f, torch.float64), _ptr(u, torch.float64),
+                                              _ptr(out, torch.float64), None))
+            return out
+        C = ctypes.c_double()
+        self._check(self.L.mto_compliance(self.h, _ptr(f, torch.float64), _ptr(u, torch.float64), None,
+                                          ctypes.byref(C)))
+        return C.value
+
     def sensitivity(self, u, f, rho, mat, dc, precision=MTO_FP64, want_C=True):
         C = ctypes.c_double()
         self._check(self.L.mto_sensitivity(self.h, _ptr(u, torch.float64), _ptr(f, torch.float64),
                                            _ptr(rho, torch.float64), ctypes.byref(mat), precision,
                                            _ptr(dc, torch.float64), ctypes.byref(C) if want_C else None))
         return C.value if want_C else None
+
+    def transfer_design(self, d_old, rho_old, rho_new):
+        """rho_new (packed for the current maps) from rho_old packed for the per-element counts d_old."""
+        d_old = np.ascontiguousarray(d_old, dtype=np.int32)
+        self._check(self.L.mto_transfer_design(self.h, d_old.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                               _ptr(rho_old, torch.float64), _ptr(rho_new, torch.float64)))
+        return rho_new
+
+    def filter(self, rho, out, radius):
+        """out = P2-filtered densities of rho (Eqs. 4-5 at the subcell centres)."""
+        self._check(self.L.mto_filter(self.h, radius, _ptr(rho, torch.float64), _ptr(out, torch.float64)))
+        return out
+
+    def filter_adjoint(self, g_f, out, radius):
+        """out = dJ/drho from g_f = dJ/drho_f (the filter's transpose with its weight sums)."""
+        self._check(self.L.mto_filter_adjoint(self.h, radius, _ptr(g_f, torch.float64), _ptr(out, torch.float64)))
+        return out
+
+    def sensitivity_adjoint(self, u, v, rho, mat, dc):
+        """dJ/drho for J = z^T u with the adjoint v (K v = z): dc = -E' v_e^T K0 u_e."""
+        self._check(self.L.mto_sensitivity_adjoint(self.h, _ptr(u, torch.float64), _ptr(v, torch.float64),
+                                                   _ptr(rho, torch.float64), ctypes.byref(mat),
+                                                   _ptr(dc, torch.float64)))
+        return dc
 
     def indicator(self, u, rho, mat, opts=None, maps=True):
         opts = opts or IndicatorOpts.paper()
@@ -287,18 +394,30 @@ class Handle:
 
 
 def compliance_noalloc(f, u, out, n=None, device=0, stream=None):
-    """C = f^T u into out[0] (device float64) through mto_compliance_noalloc (no allocation; see
-    include/mto.h).  Returns the status code."""
+    """C = f^T u over the first n entries into out[0] (device float64) through
+    mto_compliance_noalloc, which allocates nothing (see include/mto.h: its fixed scratch is
+    shared by every caller on a device, so overlapping calls race).  f, u and out must be
+    contiguous float64 tensors on CUDA device ``device`` with n <= f.numel(), u.numel(); else
+    ValueError before any library call.  Returns the library's status code."""
+    n = int(f.numel() if n is None else n)
+    for name, t in (("f", f), ("u", u), ("out", out)):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_contiguous():
+            raise ValueError(f"compliance_noalloc: {name} must be a contiguous float64 tensor")
+        if not t.is_cuda or t.device.index != device:
+            raise ValueError(f"compliance_noalloc: {name} must live on cuda:{device}")
+    if out.numel() < 1 or n > f.numel() or n > u.numel():
+        raise ValueError("compliance_noalloc: n exceeds the length of f or u, or out is empty")
     L = load_library()
     st = stream.cuda_stream if stream is not None else torch.cuda.current_stream(device).cuda_stream
-    return L.mto_compliance_noalloc(device, f.data_ptr(), u.data_ptr(), int(f.numel() if n is None else n),
-                                    ctypes.c_void_p(st), out.data_ptr())
+    return L.mto_compliance_noalloc(device, f.data_ptr(), u.data_ptr(), n, ctypes.c_void_p(st), out.data_ptr())
 
 
 def load_case(handle, load):
     """Supports and load vector of a named load case, placed with the library's own numbering.
 
     cantilever: left edge clamped, F = -1 (y) at vertex (nelx, nely/2) (Sec. 4.1, Fig. 3a);
+    cantilever_distributed: left edge clamped, a uniform downward traction of total 1 on the top
+    edge (Sec. 4.1, Fig. 6a);
     mbb: u_x = 0 on the left edge, u_y = 0 at vertex (nelx, 0), F = -1 (y) at vertex (0, nely).
     Returns (fixed DOFs as numpy int64, f as a CUDA float64 tensor)."""
     nx, ny = handle.nelx, handle.nely
@@ -306,12 +425,34 @@ def load_case(handle, load):
     if load == "cantilever":
         fixed = handle.side_dofs(0, -1)
         f[handle.vertex_dof(nx, ny // 2, 1)] = -1.0
+    elif load == "cantilever_distributed":
+        # Sec. 4.1, Fig. 6a: F = 0.5 N/L on the 2L top edge = a total downward load of 1
+        fixed = handle.side_dofs(0, -1)
+        handle.side_load(3, 1, -1.0 / (nx * handle.hx), f)
     elif load == "mbb":
         fixed = np.concatenate([handle.side_dofs(0, 0), [handle.vertex_dof(nx, 0, 1)]]).astype(np.int64)
         f[handle.vertex_dof(0, ny, 1)] = -1.0
     else:
         raise ValueError(load)
     return np.sort(fixed), f
+
+
+def inverter_case(handle, k_in=1.0, k_out=1e-3, f_in=1.0, clamp=0.01):
+    """The force inverter of Sec. 4.1 (Fig. 6b) placed with the library's numbering: both components
+    held along the left edge within clamp * L of its two corners, f_in (+x) at the mid-height vertex
+    of the left edge with a spring k_in, the output u_x at the mid-height vertex of the right edge
+    with a spring k_out (set on the handle).  Returns (fixed DOFs, f, z) with J = z^T u."""
+    nx, ny = handle.nelx, handle.nely
+    L = ny * handle.hy
+    fixed = np.union1d(handle.side_dofs_in(0, -1, -1.0, clamp * L + 1e-12),
+                       handle.side_dofs_in(0, -1, L - clamp * L - 1e-12, L + 1.0)).astype(np.int64)
+    din, dout = handle.vertex_dof(0, ny // 2, 0), handle.vertex_dof(nx, ny // 2, 0)
+    f = torch.zeros(handle.ndof, dtype=torch.float64, device=handle.device)
+    z = torch.zeros_like(f)
+    f[din] = f_in
+    z[dout] = 1.0
+    handle.set_springs([din, dout], [k_in, k_out])
+    return fixed, f, z
 
 
 def material(E0=1.0, Emin=1e-9, nu=0.3, q=3.0):
@@ -321,8 +462,8 @@ def material(E0=1.0, Emin=1e-9, nu=0.3, q=3.0):
 class ComplianceFn(torch.autograd.Function):
     """Compliance C(rho) = f^T u(rho) as a differentiable torch function.
 
-    forward: mto_build_elements + mto_solve, C = f^T u by mto_compliance_noalloc (the library's
-    kernels); keeps u.  backward: the adjoint of
+    forward: mto_build_elements + mto_solve, C = f^T u by mto_compliance (a reduction in the
+    handle's own workspace, on the handle's stream); keeps u.  backward: the adjoint of
     the self-adjoint compliance problem is lambda = -u, so dC/drho_s = -E'(rho_s) u_e^T K0_s u_e is
     one mto_sensitivity launch on the stored u (no per-subcell products are kept).
     Use through ``compliance(handle, rho, f, mat, ...)``."""
@@ -335,9 +476,7 @@ class ComplianceFn(torch.autograd.Function):
         ctx.handle, ctx.mat = handle, mat
         ctx.save_for_backward(rho, f, u)
         c = torch.empty((), dtype=torch.float64, device=rho.device)
-        st = compliance_noalloc(f, u, c, device=handle.device.index or 0, stream=handle.stream)
-        if st != 0:
-            raise MTOError(st, "mto_compliance_noalloc failed")
+        handle.compliance(f, u, out=c)
         return c
 
     @staticmethod
@@ -346,6 +485,25 @@ class ComplianceFn(torch.autograd.Function):
         dc = torch.empty_like(rho)
         ctx.handle.sensitivity(u, f, rho, ctx.mat, dc, precision=MTO_FP64, want_C=False)
         return grad_c * dc, None, None, None, None, None
+
+
+class FilterFn(torch.autograd.Function):
+    """The P2 density filter (Sec. 2.1, Eqs. 4-5) as a differentiable torch function: forward
+    mto_filter, backward mto_filter_adjoint (the chain rule of the sensitivities)."""
+
+    @staticmethod
+    def forward(ctx, rho, handle, radius):
+        ctx.handle, ctx.radius = handle, radius
+        return handle.filter(rho, torch.empty_like(rho), radius)
+
+    @staticmethod
+    def backward(ctx, g):
+        return ctx.handle.filter_adjoint(g.contiguous(), torch.empty_like(g), ctx.radius), None, None
+
+
+def density_filter(handle, rho, radius):
+    """Differentiable P2-filtered densities of the design rho (device float64, packed)."""
+    return FilterFn.apply(rho, handle, radius)
 
 
 def compliance(handle, rho, f, mat, precision=MTO_MIXED, **solve_opts):

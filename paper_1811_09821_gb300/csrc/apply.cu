@@ -5,6 +5,7 @@
 //
 // Operator layout: one element per group of W lanes (one warp for Q3), element matrices in the
 // circulant-diagonal layout of mto_internal.cuh; see ebe_kernel.
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -571,7 +572,7 @@ void launch_ebe(mto_handle h, const PClass& c, const double* M64, const float* M
                 TX* y, Red red, const int* done, const ConvTest& cv) {
   constexpr int NE = 2 * (PO + 1) * (PO + 1);
   if constexpr (kDF && WarpShape<NE>::M == 1) {
-    if (!cv.res) {
+    if (!cv.res && h->op_kernel != 2) {
       const int warps = (c.n + WarpShape<NE>::G - 1) / WarpShape<NE>::G;
       // bulk-copy staging pays off when the rows stream from HBM (measured: 6.5 % faster on
       // 1 GB of rows, 6 % slower when they sit in L2), so by default it serves classes whose
@@ -603,6 +604,22 @@ void launch_ebe(mto_handle h, const PClass& c, const double* M64, const float* M
   }
   ebe_kernel<PO, kDF, TX><<<ebe_blocks_p<PO>(c.n), 256, 0, h->stream>>>(M64, Mh, Ml, c.L, c.n, c.gmap, h->cons_d, x,
                                                                         y, red, done, cv);
+}
+
+// y += S x for the springs to ground (distinct DOFs; launched after the element classes on the same
+// stream, so plain adds), with x^T S x as one more reduction result
+template <typename T>
+__global__ void __launch_bounds__(256) spring_kernel(int n, const int64_t* __restrict__ dof,
+                                                     const double* __restrict__ k, const T* __restrict__ x,
+                                                     T* __restrict__ y, Red red, const int* __restrict__ done) {
+  if (done && *done) return;
+  double dot = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double xv = (double)x[dof[i]];
+    y[dof[i]] += (T)(k[i] * xv);
+    dot += k[i] * xv * xv;
+  }
+  if (red.part) reduce_out(dot, red);
 }
 
 // reduction slot k of the CG buffers (launch j writes part + j * kPartStride, res[j], cnt[j])
@@ -659,6 +676,12 @@ mto_status apply_all(mto_handle h, int which, const T* x, T* y, int slot, const 
     }
     ++ci;
     MTO_TRY(mto_after_launch(h, "ebe_kernel"));
+  }
+  if (which == 0 && h->n_springs) {
+    spring_kernel<T><<<1, 256, 0, h->stream>>>(h->n_springs, h->spring_dof_d, h->spring_k_d, x, y,
+                                                 red_slot(h, slot, ci), done);
+    ++ci;
+    MTO_TRY(mto_after_launch(h, "spring_kernel"));
   }
   if (nres) *nres = ci;
   return MTO_OK;
@@ -916,7 +939,10 @@ mto_status cg_iteration(mto_handle h, const CGVecs<T>& v, int pc, int deg, int n
   const int64_t n = h->ndof;
   const int par = local & 1, nxt = par ^ 1;
   const bool jac = pc == MTO_PREC_JACOBI;
+  // r^T z comes from one result per class launch of the element-block preconditioner (which has no
+  // spring term), else from one launch; p^T K p from every operator launch (classes + springs)
   const int ng = pc == MTO_PREC_SCHWARZ ? nc : 1;
+  const int nop = nc + (h->n_springs ? 1 : 0);
   ConvTest none{};
   h->timing.sample = local == 0;   // sampled timing: the first operator launch of every chunk
   const mto_status sa = apply_all<T>(h, 0, v.p, v.q, kDel + par, h->flags, none);
@@ -926,12 +952,12 @@ mto_status cg_iteration(mto_handle h, const CGVecs<T>& v, int pc, int deg, int n
     TimedScope ts(h, F_VECTOR);
     if (!jac)
       cg_vector_kernel<T, false><<<kVecBlocks, 256, 0, h->stream>>>(
-          n, v.x, v.r, v.p, v.q, v.z, v.invd, res_slot(h, kGam + par), ng, res_slot(h, kDel + par), nc,
+          n, v.x, v.r, v.p, v.q, v.z, v.invd, res_slot(h, kGam + par), ng, res_slot(h, kDel + par), nop,
           red_slot(h, -1, 0), red_slot(h, kRR + nxt, 0), red_slot(h, kRD + nxt, 0), h->cg_base, local, h->flags,
           h->flags + 1);
     else
       cg_vector_kernel<T, true><<<kVecBlocks, 256, 0, h->stream>>>(
-          n, v.x, v.r, v.p, v.q, v.z, v.invd, res_slot(h, kGam + par), ng, res_slot(h, kDel + par), nc,
+          n, v.x, v.r, v.p, v.q, v.z, v.invd, res_slot(h, kGam + par), ng, res_slot(h, kDel + par), nop,
           red_slot(h, kGam + nxt, 0), red_slot(h, kRR + nxt, 0), red_slot(h, kRD + nxt, 0), h->cg_base, local,
           h->flags, h->flags + 1);
     MTO_TRY(mto_after_launch(h, "cg_vector_kernel"));
@@ -1073,6 +1099,26 @@ mto_status apply64(mto_handle h, const double* x, double* y) {
   return apply_all<double>(h, 0, x, y, -1, nullptr, none);
 }
 
+mto_status apply_operator(mto_handle h, int op, const double* x, double* y, double* xKx) {
+  ConvTest none{};
+  int nres = 0;
+  // a launch that ended a CG run early may have left a finished-block count behind
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->cg_cnt, 0, 64 * sizeof(unsigned), h->stream), "memset"));
+  h->inner_split = op == MTO_OP_SPLIT;
+  const mto_status st = apply_all<double>(h, 0, x, y, kGam, nullptr, none, &nres);
+  h->inner_split = false;
+  MTO_TRY(st);
+  if (!xKx) return MTO_OK;
+  MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->host_pinned, h->cg_res + 8 * kGam, nres * sizeof(double),
+                                            cudaMemcpyDeviceToHost, h->stream), "copy"));
+  MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
+  timing_harvest(h);
+  double s = 0.0;
+  for (int i = 0; i < nres; ++i) s += h->host_pinned[i];
+  *xKx = s;
+  return MTO_OK;
+}
+
 mto_status apply_fine(mto_handle h, const double* x, double* y, const int* done) {
   ConvTest none{};
   return apply_all<double>(h, 0, x, y, -1, done, none);
@@ -1126,10 +1172,16 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
   bool split = true;
   double rr_prev = -1.0, asked = 0.0;
   mto_status st = MTO_ENOCONV;
+  const auto t_start = std::chrono::steady_clock::now();
+  int last_it = 0;
   for (int outer = 0; outer <= max_outer; ++outer) {
     // FP64 residual with the FP64 element matrices
     h->inner_split = false;
     MTO_TRY(true_residual(h, f, u, nrm, &rr, &ff));
+    if (h->solve_log)
+      std::fprintf(stderr, "mto_solve: step %d inner_iters %d relres %.3e split %d wall_ms %.1f\n", outer, last_it,
+                   ff > 0 ? std::sqrt(rr / ff) : 0.0, (int)split,
+                   std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count());
     if (o->precision == MTO_MIXED && rr_prev > 0.0 && std::sqrt(rr / rr_prev) > 10.0 * asked) split = false;
     rr_prev = rr;
     if (!std::isfinite(rr)) {
@@ -1187,6 +1239,7 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
       }
     }
     total += it;
+    last_it = it;
   }
   if (iters_out) *iters_out = total;
   if (relres_out) *relres_out = ff > 0 ? std::sqrt(rr / ff) : 0.0;

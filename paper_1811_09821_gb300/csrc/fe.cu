@@ -408,6 +408,37 @@ mto_status element_matrix(mto_handle h, int64_t e, double* host_out) {
   return st;
 }
 
+__global__ void gather_element_split_kernel(int P, int L, const int2* __restrict__ dpos, int slot,
+                                           const float* __restrict__ Kh, const float* __restrict__ Kl,
+                                           float* __restrict__ out) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < P; c += gridDim.x * blockDim.x) {
+    const size_t o = (size_t)slot * L + dpos[c].x;
+    out[c] = Kh[o];
+    out[P + c] = Kl[o];
+  }
+}
+
+mto_status element_matrix_split(mto_handle h, int64_t e, float* hi, float* lo) {
+  const int p = h->p_host[e];
+  const PClass& c = h->pc[p];
+  if (!c.K32 || !c.K32lo) return mto_fail(h, MTO_EINVAL, "mto_element_matrix_split: no split-precision build");
+  int slot = 0;
+  MTO_TRY(mto_cuda_check(h, cudaMemcpy(&slot, h->slot_d + e, sizeof(int), cudaMemcpyDeviceToHost), "copy"));
+  float* tmp = nullptr;
+  MTO_TRY(mto_cuda_check(h, cudaMalloc(&tmp, sizeof(float) * 2 * c.P), "cudaMalloc"));
+  gather_element_split_kernel<<<(c.P + 255) / 256, 256, 0, h->stream>>>(c.P, c.L, c.dpos, slot, c.K32, c.K32lo,
+                                                                        tmp);
+  mto_status st = mto_after_launch(h, "gather_element_split_kernel");
+  if (st == MTO_OK)
+    st = mto_cuda_check(h, cudaMemcpyAsync(hi, tmp, sizeof(float) * c.P, cudaMemcpyDeviceToHost, h->stream), "copy");
+  if (st == MTO_OK)
+    st = mto_cuda_check(h, cudaMemcpyAsync(lo, tmp + c.P, sizeof(float) * c.P, cudaMemcpyDeviceToHost, h->stream),
+                        "copy");
+  if (st == MTO_OK) st = mto_cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+  cudaFree(tmp);
+  return st;
+}
+
 mto_status build_tables(mto_handle h) {
   for (auto* v : {&h->bc, &h->bc_qr}) {
     for (auto& b : *v) {
@@ -466,6 +497,12 @@ mto_status build_elements(mto_handle h, const double* rho, const mto_material* m
   return MTO_OK;
 }
 
+// springs to ground add their stiffness to the assembled diagonal (distinct DOFs, one thread each)
+__global__ void spring_diag_kernel(int n, const int64_t* __restrict__ dof, const double* __restrict__ k,
+                                   double* __restrict__ diag) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) diag[dof[i]] += k[i];
+}
+
 mto_status build_diagonal(mto_handle h, int precision) {
   (void)precision;
   TimedScope ts(h, F_BUILD);
@@ -483,6 +520,10 @@ mto_status build_diagonal(mto_handle h, int precision) {
       case 6: launch_diag<6>(h, c, diag); break;
     }
     MTO_TRY(mto_after_launch(h, "diag_kernel"));
+  }
+  if (h->n_springs) {
+    spring_diag_kernel<<<1, 32, 0, h->stream>>>(h->n_springs, h->spring_dof_d, h->spring_k_d, diag);
+    MTO_TRY(mto_after_launch(h, "spring_diag_kernel"));
   }
   invdiag_kernel<<<grid_for(h->ndof, 256), 256, 0, h->stream>>>(h->ndof, diag, h->invd64, h->invd32, h->flags);
   MTO_TRY(mto_after_launch(h, "invdiag_kernel"));

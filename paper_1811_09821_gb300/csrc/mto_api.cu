@@ -197,6 +197,10 @@ void release_mesh(mto_handle h) {
   h->fixed_host.clear();
   free_dev(h, h->fixed_d);
   h->n_fixed = 0;
+  free_dev(h, h->spring_dof_d);
+  free_dev(h, h->spring_k_d);
+  h->n_springs = 0;
+  free_dev(h, h->filt_W);
   h->bytes = h->base_bytes;
 }
 
@@ -269,6 +273,25 @@ int local_node_map(mto_handle h, int64_t e, int a, int b, int64_t* nodes, double
 
 }  // namespace
 
+namespace {
+// f[dof[k]] += val[k] (distinct DOFs)
+__global__ void scatter_add_kernel(int n, const int64_t* __restrict__ dof, const double* __restrict__ val,
+                                   double* __restrict__ f) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) f[dof[k]] += val[k];
+}
+
+// Gauss-Lobatto-Legendre weights of order p: w_k = 2 / (p (p + 1) P_p(z_k)^2)
+void gll_weights(int p, double* w) {
+  double z[kPMaxTab + 1];
+  gll_nodes(p, z);
+  for (int k = 0; k <= p; ++k) {
+    double pn, pn1;
+    legendre_pair(p, z[k], &pn, &pn1);
+    w[k] = 2.0 / (p * (p + 1) * pn * pn);
+  }
+}
+}  // namespace
+
 int mto::local_node_map_public(mto_handle h, int64_t e, int a, int b, int64_t* nodes, double* w) {
   return local_node_map(h, e, a, b, nodes, w);
 }
@@ -286,9 +309,13 @@ mto_status mto_create(mto_handle* out, int device, void* stream) {
   // MTO_NO_GRAPHS=1 launches the PCG iterations one kernel at a time instead of replaying captured
   // graphs (same kernels and arithmetic; for profilers that handle graphs poorly)
   if (const char* ng = std::getenv("MTO_NO_GRAPHS")) h->use_graphs = !(ng[0] == '1');
-  // MTO_OP_KERNEL=1 / 0 forces the bulk-copy staged / register-pipelined split operator
-  // (n_e <= 32); by default the staged one serves classes whose rows exceed 64 MB
-  if (const char* ok = std::getenv("MTO_OP_KERNEL")) h->op_kernel = ok[0] == '1' ? 1 : (ok[0] == '0' ? 0 : -1);
+  // MTO_SOLVE_LOG=1 prints, per refinement step of mto_solve, the inner iterations, the FP64
+  // relative residual and the host wall time to stderr (diagnostics; no effect on the arithmetic)
+  if (const char* sl = std::getenv("MTO_SOLVE_LOG")) h->solve_log = sl[0] == '1';
+  // MTO_OP_KERNEL=0 / 1 / 2 selects the split operator's kernel for n_e <= 32 as
+  // mto_set_operator_kernel does (register pipeline / bulk-copy staging / generic)
+  if (const char* ok = std::getenv("MTO_OP_KERNEL"))
+    h->op_kernel = (ok[0] >= '0' && ok[0] <= '2') ? ok[0] - '0' : -1;
   cudaSetDevice(device);
   if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
@@ -568,6 +595,46 @@ mto_status mto_set_supports(mto_handle h, const int64_t* fixed, int64_t n) {
   return MTO_OK;
 }
 
+mto_status mto_set_springs(mto_handle h, const int64_t* dofs, const double* k, int64_t n) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
+  if (!h->have_setup) return mto_fail(h, MTO_EINVAL, "mto_set_springs: call mto_setup first");
+  if (n < 0 || n > 1024 || (n > 0 && (!dofs || !k))) return mto_fail(h, MTO_EINVAL, "mto_set_springs: bad arguments");
+  std::vector<std::pair<int64_t, double>> sp;
+  for (int64_t i = 0; i < n; ++i) {
+    if (dofs[i] < 0 || dofs[i] >= h->ndof || !(k[i] > 0) || !std::isfinite(k[i]))
+      return mto_fail(h, MTO_EINVAL, "mto_set_springs: DOF out of range or stiffness not positive");
+    sp.push_back({dofs[i], k[i]});
+  }
+  // one entry per DOF (stiffnesses on the same DOF add up)
+  std::sort(sp.begin(), sp.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  std::vector<int64_t> d;
+  std::vector<double> kk;
+  for (const auto& e : sp) {
+    if (!d.empty() && d.back() == e.first) kk.back() += e.second;
+    else {
+      d.push_back(e.first);
+      kk.push_back(e.second);
+    }
+  }
+  cudaSetDevice(h->device);
+  MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "mto_set_springs"));
+  clear_graphs(h);   // captured iterations hold the previous operator
+  free_dev(h, h->spring_dof_d);
+  free_dev(h, h->spring_k_d);
+  h->n_springs = (int)d.size();
+  if (h->n_springs) {
+    MTO_TRY(mto_alloc(h, &h->spring_dof_d, d.size()));
+    MTO_TRY(mto_alloc(h, &h->spring_k_d, kk.size()));
+    MTO_TRY(mto_cuda_check(h, cudaMemcpy(h->spring_dof_d, d.data(), d.size() * sizeof(int64_t), cudaMemcpyHostToDevice), "upload"));
+    MTO_TRY(mto_cuda_check(h, cudaMemcpy(h->spring_k_d, kk.data(), kk.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
+  }
+  h->schwarz_valid = false;
+  h->mg_valid = false;
+  if (h->built_precision >= 0 && h->have_supports) MTO_TRY(build_diagonal(h, h->built_precision));
+  return MTO_OK;
+}
+
 mto_status mto_vertex_dof(mto_handle h, int32_t ix, int32_t iy, int32_t comp, int64_t* dof) {
   if (!h || !h->have_setup || !dof) return mto_fail(h, MTO_EINVAL, "mto_vertex_dof: bad arguments");
   if (ix < 0 || ix > h->nelx || iy < 0 || iy > h->nely || comp < 0 || comp > 1)
@@ -576,30 +643,33 @@ mto_status mto_vertex_dof(mto_handle h, int32_t ix, int32_t iy, int32_t comp, in
   return MTO_OK;
 }
 
-mto_status mto_side_dofs(mto_handle h, int32_t side, int32_t comp, int64_t* out, int64_t cap, int64_t* count) {
+mto_status mto_side_dofs_in(mto_handle h, int32_t side, int32_t comp, double s0, double s1, int64_t* out,
+                            int64_t cap, int64_t* count) {
   if (!h || !h->have_setup || !count) return mto_fail(h, MTO_EINVAL, "mto_side_dofs: bad arguments");
   if (side < 0 || side > 3 || comp < -1 || comp > 1) return mto_fail(h, MTO_EINVAL, "mto_side_dofs: bad side/comp");
+  // nodes of the side in order with their coordinate along it (GLL positions of each edge's order)
   std::vector<int64_t> nodes;
+  std::vector<double> pos;
   int64_t en[kPMaxTab + 2];
-  if (side <= 1) {
-    int ix = side == 0 ? 0 : h->nelx;
-    for (int iy = 0; iy < h->nely; ++iy) {
-      int pE = edge_nodes(h, 1, ix, iy, en);
-      for (int k = 0; k < pE; ++k) nodes.push_back(en[k]);
+  double z[kPMaxTab + 1];
+  const bool vert = side <= 1;
+  const int nE = vert ? h->nely : h->nelx;
+  const double len = vert ? h->hy : h->hx;
+  for (int t = 0; t < nE; ++t) {
+    const int pE = vert ? edge_nodes(h, 1, side == 0 ? 0 : h->nelx, t, en) : edge_nodes(h, 0, t, side == 2 ? 0 : h->nely, en);
+    gll_nodes(pE, z);
+    for (int k = 0; k < pE; ++k) {
+      nodes.push_back(en[k]);
+      pos.push_back((t + 0.5 * (1.0 + z[k])) * len);
     }
-    nodes.push_back(vertex_id(h, ix, h->nely));
-  } else {
-    int iy = side == 2 ? 0 : h->nely;
-    for (int ix = 0; ix < h->nelx; ++ix) {
-      int pE = edge_nodes(h, 0, ix, iy, en);
-      for (int k = 0; k < pE; ++k) nodes.push_back(en[k]);
-    }
-    nodes.push_back(vertex_id(h, h->nelx, iy));
   }
+  nodes.push_back(vert ? vertex_id(h, side == 0 ? 0 : h->nelx, h->nely) : vertex_id(h, h->nelx, side == 2 ? 0 : h->nely));
+  pos.push_back(nE * len);
   std::vector<int64_t> dofs;
-  for (int64_t nd : nodes) {
-    if (comp != 1) dofs.push_back(2 * nd);
-    if (comp != 0) dofs.push_back(2 * nd + 1);
+  for (size_t i = 0; i < nodes.size(); ++i) {
+    if (!(pos[i] >= s0 && pos[i] <= s1)) continue;
+    if (comp != 1) dofs.push_back(2 * nodes[i]);
+    if (comp != 0) dofs.push_back(2 * nodes[i] + 1);
   }
   std::sort(dofs.begin(), dofs.end());
   dofs.erase(std::unique(dofs.begin(), dofs.end()), dofs.end());
@@ -610,6 +680,73 @@ mto_status mto_side_dofs(mto_handle h, int32_t side, int32_t comp, int64_t* out,
     std::copy(dofs.begin(), dofs.begin() + m, out);
   }
   return MTO_OK;
+}
+
+mto_status mto_side_dofs(mto_handle h, int32_t side, int32_t comp, int64_t* out, int64_t cap, int64_t* count) {
+  return mto_side_dofs_in(h, side, comp, -HUGE_VAL, HUGE_VAL, out, cap, count);
+}
+
+mto_status mto_edge_dofs(mto_handle h, int32_t dir, int32_t ix, int32_t iy, int32_t comp, int64_t* out, int64_t cap,
+                         int64_t* count) {
+  if (!h || !h->have_setup || !count || comp < 0 || comp > 1 || (dir != 0 && dir != 1))
+    return mto_fail(h, MTO_EINVAL, "mto_edge_dofs: bad arguments");
+  if (dir == 0 ? (ix < 0 || ix >= h->nelx || iy < 0 || iy > h->nely) : (ix < 0 || ix > h->nelx || iy < 0 || iy >= h->nely))
+    return mto_fail(h, MTO_EINVAL, "mto_edge_dofs: edge out of range");
+  int64_t en[kPMaxTab + 2];
+  const int pE = edge_nodes(h, dir, ix, iy, en);
+  *count = pE + 1;
+  if (cap > 0) {
+    if (!out) return mto_fail(h, MTO_EINVAL, "mto_edge_dofs: null output");
+    for (int k = 0; k <= pE && k < cap; ++k) out[k] = 2 * en[k] + comp;
+  }
+  return MTO_OK;
+}
+
+mto_status mto_side_load(mto_handle h, int32_t side, int32_t comp, double traction, double* f) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
+  if (!h->have_setup || !f || side < 0 || side > 3 || comp < 0 || comp > 1 || !std::isfinite(traction))
+    return mto_fail(h, MTO_EINVAL, "mto_side_load: bad arguments");
+  cudaSetDevice(h->device);
+  // accumulate per node on the host (vertices are shared by two edges), then one scatter
+  std::vector<std::pair<int64_t, double>> acc;
+  const bool vert = side <= 1;
+  const int nE = vert ? h->nely : h->nelx;
+  const double len = vert ? h->hy : h->hx;
+  for (int t = 0; t < nE; ++t) {
+    int64_t en[kPMaxTab + 2];
+    const int pE = vert ? edge_nodes(h, 1, side == 0 ? 0 : h->nelx, t, en) : edge_nodes(h, 0, t, side == 2 ? 0 : h->nely, en);
+    double w[kPMaxTab + 1];
+    gll_weights(pE, w);
+    for (int k = 0; k <= pE; ++k) acc.push_back({2 * en[k] + comp, traction * 0.5 * len * w[k]});
+  }
+  std::sort(acc.begin(), acc.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  std::vector<int64_t> dofs;
+  std::vector<double> vals;
+  for (const auto& kv : acc) {
+    if (!dofs.empty() && dofs.back() == kv.first) vals.back() += kv.second;
+    else {
+      dofs.push_back(kv.first);
+      vals.push_back(kv.second);
+    }
+  }
+  const int n = (int)dofs.size();
+  int64_t* d_dof = nullptr;
+  double* d_val = nullptr;
+  MTO_TRY(mto_cuda_check(h, cudaMalloc(&d_dof, n * sizeof(int64_t)), "cudaMalloc"));
+  mto_status st = mto_cuda_check(h, cudaMalloc(&d_val, n * sizeof(double)), "cudaMalloc");
+  if (st == MTO_OK)
+    st = mto_cuda_check(h, cudaMemcpyAsync(d_dof, dofs.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream), "copy");
+  if (st == MTO_OK)
+    st = mto_cuda_check(h, cudaMemcpyAsync(d_val, vals.data(), n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy");
+  if (st == MTO_OK) {
+    scatter_add_kernel<<<(n + 255) / 256, 256, 0, h->stream>>>(n, d_dof, d_val, f);
+    st = mto_after_launch(h, "scatter_add_kernel");
+  }
+  if (st == MTO_OK) st = mto_cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+  cudaFree(d_dof);
+  cudaFree(d_val);
+  return st;
 }
 
 mto_status mto_element_nodes(mto_handle h, int64_t e, int64_t* nodes, double* weights, int32_t* counts) {
@@ -678,6 +815,58 @@ mto_status mto_apply(mto_handle h, const double* x, double* y) {
   return apply64(h, x, y);
 }
 
+mto_status mto_compliance(mto_handle h, const double* f, const double* u, double* C_dev, double* C) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
+  if (!h->have_setup || !f || !u || (!C_dev && !C)) return mto_fail(h, MTO_EINVAL, "mto_compliance: bad arguments");
+  cudaSetDevice(h->device);
+  double* out = C_dev ? C_dev : h->red + 9;
+  MTO_TRY(dot64(h, f, u, h->ndof, out));
+  if (!C) return MTO_OK;
+  MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->host_pinned + 40, out, sizeof(double), cudaMemcpyDeviceToHost,
+                                            h->stream), "copy"));
+  MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
+  *C = h->host_pinned[40];
+  return MTO_OK;
+}
+
+mto_status mto_apply_operator(mto_handle h, int32_t op, const double* x, double* y, double* xKx) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
+  if (!h->have_setup || !x || !y) return mto_fail(h, MTO_EINVAL, "mto_apply_operator: bad arguments");
+  if (op != MTO_OP_FP64 && op != MTO_OP_SPLIT) return mto_fail(h, MTO_EINVAL, "mto_apply_operator: bad operator");
+  if (h->built_precision < 0) return mto_fail(h, MTO_EINVAL, "mto_apply_operator: call mto_build_elements first");
+  if (op == MTO_OP_SPLIT && h->built_precision != MTO_MIXED)
+    return mto_fail(h, MTO_EINVAL, "mto_apply_operator: the split operator needs the MTO_MIXED build");
+  cudaSetDevice(h->device);
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(y, 0, h->ndof * sizeof(double), h->stream), "mto_apply_operator"));
+  return apply_operator(h, op, x, y, xKx);
+}
+
+mto_status mto_set_operator_kernel(mto_handle h, int32_t kernel) {
+  if (!h) return MTO_EINVAL;
+  if (kernel < MTO_OPK_AUTO || kernel > MTO_OPK_GENERIC)
+    return mto_fail(h, MTO_EINVAL, "mto_set_operator_kernel: bad kernel");
+  if (kernel != h->op_kernel) {
+    cudaSetDevice(h->device);
+    MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "mto_set_operator_kernel"));
+    clear_graphs(h);   // captured iterations hold the previous kernel
+  }
+  h->op_kernel = kernel;
+  return MTO_OK;
+}
+
+mto_status mto_element_matrix_split(mto_handle h, int64_t e, float* hi, float* lo) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
+  if (!h->have_setup || !hi || !lo || e < 0 || e >= h->nel)
+    return mto_fail(h, MTO_EINVAL, "mto_element_matrix_split: bad arguments");
+  if (h->built_precision != MTO_MIXED)
+    return mto_fail(h, MTO_EINVAL, "mto_element_matrix_split: call mto_build_elements with MTO_MIXED first");
+  cudaSetDevice(h->device);
+  return element_matrix_split(h, e, hi, lo);
+}
+
 mto_status mto_sensitivity(mto_handle h, const double* u, const double* f, const double* rho,
                            const mto_material* mat, int32_t precision, double* dc, double* C) {
   if (!h) return MTO_EINVAL;
@@ -687,6 +876,45 @@ mto_status mto_sensitivity(mto_handle h, const double* u, const double* f, const
   if (precision != MTO_FP64 && precision != MTO_MIXED) return mto_fail(h, MTO_EINVAL, "mto_sensitivity: bad precision");
   cudaSetDevice(h->device);
   return sensitivity(h, u, f, rho, mat, precision, dc, C);
+}
+
+mto_status mto_transfer_design(mto_handle h, const int32_t* d_old, const double* rho_old, double* rho_new) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
+  if (!h->have_setup || !d_old || !rho_old || !rho_new || rho_old == rho_new)
+    return mto_fail(h, MTO_EINVAL, "mto_transfer_design: bad arguments");
+  cudaSetDevice(h->device);
+  return transfer_design(h, d_old, rho_old, rho_new);
+}
+
+mto_status mto_filter(mto_handle h, double radius, const double* rho, double* rho_f) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
+  if (!h->have_setup || !rho || !rho_f || rho == rho_f || !(radius > 0) || !std::isfinite(radius))
+    return mto_fail(h, MTO_EINVAL, "mto_filter: bad arguments");
+  if (radius > 4.0 * std::min(h->hx, h->hy)) return mto_fail(h, MTO_EINVAL, "mto_filter: radius above 4 elements");
+  cudaSetDevice(h->device);
+  return density_filter(h, radius, rho, rho_f, false);
+}
+
+mto_status mto_filter_adjoint(mto_handle h, double radius, const double* g_f, double* g) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
+  if (!h->have_setup || !g_f || !g || g == g_f || !(radius > 0) || !std::isfinite(radius))
+    return mto_fail(h, MTO_EINVAL, "mto_filter_adjoint: bad arguments");
+  if (radius > 4.0 * std::min(h->hx, h->hy)) return mto_fail(h, MTO_EINVAL, "mto_filter_adjoint: radius above 4 elements");
+  cudaSetDevice(h->device);
+  return density_filter(h, radius, g_f, g, true);
+}
+
+mto_status mto_sensitivity_adjoint(mto_handle h, const double* u, const double* v, const double* rho,
+                                   const mto_material* mat, double* dc) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
+  if (!h->have_setup || !u || !v || !rho || !mat || !dc)
+    return mto_fail(h, MTO_EINVAL, "mto_sensitivity_adjoint: bad arguments");
+  cudaSetDevice(h->device);
+  return sensitivity_adjoint(h, u, v, rho, mat, dc);
 }
 
 mto_status mto_indicator(mto_handle h, const double* u, const double* rho, const mto_material* mat,

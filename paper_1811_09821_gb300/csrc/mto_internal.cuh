@@ -170,6 +170,10 @@ struct mto_handle_s {
   int* slot_d = nullptr;                       // [nel] slot of each element within its order class
   int64_t* fixed_d = nullptr;                  // [n_fixed] supported DOFs
   int64_t n_fixed = 0;
+  double* filt_W = nullptr;                    // [design_len] density-filter weight sums (adjoint)
+  int64_t* spring_dof_d = nullptr;             // [n_springs] DOFs with a spring to ground (K + k e e^T)
+  double* spring_k_d = nullptr;                // [n_springs] their stiffness
+  int n_springs = 0;
   int64_t base_bytes = 0;                      // device bytes held independently of the mesh
 
   // solver workspace
@@ -189,7 +193,8 @@ struct mto_handle_s {
   bool schwarz_valid = false;
   bool inner_split = false;                    // operator applies use the split pair (mixed inner solves)
   int op_kernel = -1;                          // split operator, n_e <= 32: 0 register pipeline, 1 bulk-copy
-                                               // staging, -1 by the size of the class's rows
+                                               // staging, 2 the generic per-chunk kernel, -1 by the size
+                                               // of the class's rows
   // multigrid preconditioner: levels 1.. (Q1), fine-level transfer tables and work vectors
   std::vector<mto::MGLevel> mg;
   bool mg_ok = false, mg_valid = false;
@@ -212,6 +217,7 @@ struct mto_handle_s {
   double* mg_res = nullptr;
   int build_path = MTO_BUILD_SIMT;
   bool use_graphs = true;
+  bool solve_log = false;                      // MTO_SOLVE_LOG=1: one stderr line per refinement step
   std::vector<mto::GraphEntry*> graphs;
   double* red = nullptr;                       // misc reduction scratch [64]
   int* flags = nullptr;                        // [0] iterations when done, [1] error code, [2..] misc
@@ -409,6 +415,7 @@ mto_status build_sens_tables(mto_handle h);
 mto_status build_elements(mto_handle h, const double* rho, const mto_material* m, int precision);
 mto_status build_diagonal(mto_handle h, int precision);
 mto_status element_matrix(mto_handle h, int64_t e, double* host_out);
+mto_status element_matrix_split(mto_handle h, int64_t e, float* hi, float* lo);
 mto_status build_schwarz(mto_handle h);                                 // element-block preconditioner
 // mto_api.cu: (node, weight) list of local node (a, b) of element e (minimum-rule constraints)
 int local_node_map_public(mto_handle h, int64_t e, int a, int b, int64_t* nodes, double* w);
@@ -425,11 +432,17 @@ mto_status tc_build_class(mto_handle h, const BClass& b, const double* rho, cons
 int ebe_blocks(int p, int n);                                           // grid of one operator launch
 // apply.cu
 mto_status apply64(mto_handle h, const double* x, double* y);        // y += K x (FP64 vectors)
+mto_status apply_operator(mto_handle h, int op, const double* x, double* y, double* xKx);   // mto_apply_operator
 mto_status apply_fine(mto_handle h, const double* x, double* y, const int* done);   // same, early exit
 mto_status apply_q1(mto_handle h, const MGLevel& l, const double* x, double* y, const int* done);
 mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts* o, int32_t* iters,
                  double* relres);
 // sens.cu
+// filter.cu
+mto_status density_filter(mto_handle h, double R, const double* x, double* out, bool adjoint);
+mto_status transfer_design(mto_handle h, const int* d_old_host, const double* rho_old, double* rho_new);
+mto_status sensitivity_adjoint(mto_handle h, const double* u, const double* v, const double* rho,
+                               const mto_material* m, double* dc);
 mto_status sensitivity(mto_handle h, const double* u, const double* f, const double* rho,
                        const mto_material* m, int precision, double* dc, double* C);
 // ind.cu

@@ -28,8 +28,9 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// One block per 2048 consecutive entries; the last block to finish sums the partials in index
-// order (so the result depends only on n, not on scheduling) and writes *C.
+// One block per 2048 consecutive entries; the last block to finish sums the partials in a fixed
+// order that depends only on n (strided per thread, then a shuffle tree), not on scheduling, and
+// writes *C.
 __global__ void __launch_bounds__(kThreads) dot_noalloc_kernel(int64_t n, const double* __restrict__ f,
                                                                 const double* __restrict__ u,
                                                                 double* __restrict__ scratch,
@@ -82,7 +83,8 @@ extern "C" mto_status mto_compliance_noalloc(int32_t device, const double* f, co
   mto_status st = MTO_OK;
   double* scratch = nullptr;
   {
-    // once per device, with that device current: the scratch array's device address
+    // once per device, with that device current: the scratch array's device address (kept for
+    // the life of the process, so the library must not be used across a cudaDeviceReset)
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_ptr[device]) {
       void* p = nullptr;

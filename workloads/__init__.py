@@ -22,6 +22,8 @@ SEED_BASE = 181109821
 # load cases: how the supports and the point load are placed (the DOF numbering is each side's own)
 CANTILEVER = "cantilever"   # left edge clamped (u_x = u_y = 0); F = -1 in y at vertex (nelx, nely/2)
 MBB = "mbb"                 # u_x = 0 on the left edge; u_y = 0 at vertex (nelx, 0); F = -1 in y at (0, nely)
+CANTILEVER_DISTRIBUTED = "cantilever_distributed"   # left edge clamped; uniform downward traction on
+                                                    # the top edge, total 1 (Sec. 4.1, Fig. 6a)
 
 
 @dataclass
@@ -138,16 +140,36 @@ def _connected_threshold(s, vol, seed_mask):
 
 
 def _sigmoid_volume(s, vol, width=0.35, floor=1e-3):
-    """Smooth densities in [floor, 1]: a logistic of s with its offset bisected to mean ``vol``."""
+    """Smooth densities in [floor, 1]: a logistic of s with its offset chosen so the mean is ``vol``.
+
+    The offset is bisected on a strided 1/97 subsample of the cells, then refined by Newton steps
+    on the whole field (the mean is smooth and monotone in the offset) until the step falls below
+    1e-15."""
+    es = np.exp(-s / width).ravel()     # exp(-(s - t)/w) = exp(-s/w) exp(t/w): one exponential per cell
+
+    def dens(t, e):
+        r = 1.0 / (1.0 + e * np.exp(t / width))
+        return np.clip(r, floor, 1.0), r
+
+    sub = es[::97]
     lo, hi = -10.0, 10.0
     for _ in range(64):   # the interval of 20 is below one ulp after ~60 halvings
         t = 0.5 * (lo + hi)
-        r = np.clip(1.0 / (1.0 + np.exp(-(s - t) / width)), floor, 1.0)
-        if r.mean() > vol:
+        if dens(t, sub)[0].mean() > vol:
             lo = t
         else:
             hi = t
-    return r
+    t = 0.5 * (lo + hi)
+    for _ in range(12):
+        rc, r = dens(t, es)
+        g = rc.mean() - vol
+        # d r / d t = -r (1 - r) / w where the clip is inactive
+        dg = -np.mean(np.where((r > floor) & (r < 1.0), r * (1.0 - r), 0.0)) / width
+        step = g / dg
+        t -= step
+        if abs(step) < 1e-15:
+            break
+    return dens(t, es)[0].reshape(s.shape)
 
 
 def cantilever_small(nelx=20, nely=10, p=2, d=4, seed_index=1):
