@@ -2,21 +2,30 @@
 """Benchmark of the dp-adaptive MTO hot path on GB300.
 
 Metric: TO iterations/s (solve + sensitivity) and MDOF x PCG-iterations/s, mixed precision vs the
-plain FP64 GPU path.  One step = one pass of the whole hot path over one design: element build
-(step a), PCG solve to the stated residual from a zero start (b), compliance and sensitivities (c)
-and the composite indicator with the dp map update (d).
+plain FP64 GPU path.
 
-Default workload: the 160 x 80 MBB half-beam, Q3 elements with 8 x 8 design subcells (1280 x 640
-density field), a seeded binary design at volume fraction 0.3, Emin = 1e-9 E0, relative residual
-1e-8 (l2).  Both paths run the same steps; `value` is the mixed path.
+Default workload: the large MBB half-beam, 1024 x 512 Q3 elements with 8 x 8 design subcells
+(8192 x 4096 density field, 9,446,402 DOFs), smooth seeded densities at volume fraction 0.2,
+Emin = 1e-9 E0, quoted on 20 optimality-criteria iterations.  One step is one TO iteration of one
+optimization run, through the whole hot path: element build (step a), PCG solve warm-started from
+the previous displacement to a relative compliance accuracy of 1e-8 (b), sensitivities (c), the
+composite indicator with the dp map update (d) and the OC design update.  The warm-up steps are
+the run's first iterations (the first solve starts from zero); the timed steps continue the same
+run.  ``value`` is the mixed path (split-precision operator in the inner PCG); the same run in
+plain FP64 is timed beside it, and the accuracy of both is checked after the timed region by an
+FP64 re-solve on the same design.
+
+``--mode pass`` repeats one pass over a fixed design instead (the 160 x 80 binary beam).
 
 Multi-GPU: every rank solves its own replica (independent problems, no data-path collective);
 value = total steps of all ranks / max over ranks of the timed wall.  The oracle (CPU, FP64) is
-timed on a bounded sample as `cpu_baseline`; `--impl reference` times only the oracle.
+timed on a bounded sample as ``cpu_baseline``; ``--impl reference`` times only the oracle.
 """
 import argparse
+import functools
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -28,47 +37,64 @@ sys.path.insert(0, ROOT)
 
 METRIC = "TO iterations/s (solve+sensitivity) & MDOF·PCG-iter/s, mixed vs plain FP64 GPU"
 UNIT = "TO-iter/s"
-DEFAULT_WORKLOAD = "mbb_160x80_p3_d8"
-# DRAM bytes (read + write) per launch of the split operator ebe_df_pipe_kernel<3,double> on this
-# workload inside the solve, from one ncu capture with warm caches (mean of 3 launches); to be
-# re-taken whenever that kernel changes
-MEASURED_TRAFFIC = {"mbb_160x80_p3_d8": 55921408 + 72619}
-SAMPLE_WORKLOAD = {"mbb_160x80_p3_d8": "mbb_40x20_p3_d8", "dp_cantilever_320x160": "dp_cantilever_40x20",
-                   "cantilever_20x10_p2_d4": "cantilever_20x10_p2_d4", "mbb_40x20_p3_d8": "mbb_40x20_p3_d8",
-                   "mbb_1024x512_p3_d8": "mbb_40x20_p3_d8", "mbb_480x240_p3_d8": "mbb_40x20_p3_d8"}
+DEFAULT_WORKLOAD = "mbb_1024x512_p3_d8"
+# the bounded sample the CPU oracle is timed on for each workload (same generator recipe)
+SAMPLE_WORKLOAD = {"mbb_1024x512_p3_d8": "mbb_64x32_p3_d8", "mbb_160x80_p3_d8": "mbb_40x20_p3_d8",
+                   "dp_cantilever_320x160": "dp_cantilever_40x20", "cantilever_20x10_p2_d4": "cantilever_20x10_p2_d4",
+                   "mbb_40x20_p3_d8": "mbb_40x20_p3_d8", "mbb_480x240_p3_d8": "mbb_40x20_p3_d8",
+                   "mbb_64x32_p3_d8": "mbb_64x32_p3_d8"}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--rtol", type=float, default=1e-8)
-    ap.add_argument("--precond", default="mg", choices=["schwarz", "jacobi", "mg"])
+    ap.add_argument("--mode", default=None, choices=["oc", "pass"],
+                    help="oc: steps are iterations of one optimization run (default for the large beam); "
+                         "pass: repeated passes over one fixed design (default for the other workloads)")
+    ap.add_argument("--rtol", type=float, default=1e-8, help="relative compliance accuracy of every solve")
     ap.add_argument("--mg-degree", type=int, default=4, help="Chebyshev degree of the multigrid smoothing")
-    ap.add_argument("--solve", default="mixed", choices=["mixed", "mixed32"],
-                    help="mixed: FP64 refinement around inner PCG on the split-precision operator with FP64 "
-                         "vectors; mixed32: the same with FP32 inner vectors")
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--oc-iters", type=int, default=0,
-                    help="instead of repeated passes over one design, time one optimization run of this "
-                         "many optimality-criteria iterations (each: build, warm-started mixed solve, "
-                         "sensitivity, OC update of the design; the 1024x512 beam is quoted at 20)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 # ------------------------------------------------------------------------------------ CPU oracle
+def cpu_model():
+    """Host CPU model and core count (the oracle runs single-threaded on it)."""
+    name = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if not name:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.strip().lower().startswith("model name"):
+                    name = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return f"{name or platform.processor() or 'unknown'} ({platform.machine()}, {os.cpu_count()} cores on the host)"
+
+
 def oracle_step_script(workload):
-    """Python source that times one full oracle pass (build, assemble, exact solve, sensitivity,
-    indicators, map update) on `workload` and prints JSON."""
+    """Python source that times one oracle TO iteration (build, assemble, exact solve, sensitivity,
+    indicators, map update, OC update) on `workload` and prints JSON."""
     return f"""
 import json, sys, time
 sys.path.insert(0, {ROOT!r})
+import numpy as np
 import workloads as W
-from oracle import mesh as om, solve as osv, sensitivity as ose, indicators as oi
+from oracle import mesh as om, solve as osv, sensitivity as ose, indicators as oi, oc as ooc
 pr = W.named({workload!r})
 t0 = time.perf_counter()
 m = om.DPMesh(pr.nelx, pr.nely, pr.p, pr.d)
@@ -82,14 +108,16 @@ t2 = time.perf_counter()
 ga = oi.kelly(m, u); gd = oi.gamma_d(m, pr.rho); eq = oi.qr_error(m, u, pr.rho, pr.E0, pr.Emin, pr.nu, pr.q)
 oi.map_update(pr.nelx, pr.nely, pr.p, ga, gd, eq)
 t3 = time.perf_counter()
-print(json.dumps(dict(seconds=t3 - t0, build_solve=t1 - t0, sens=t2 - t1, indicator=t3 - t2,
+ooc.oc_update(pr.rho, dc, ooc.subcell_areas(m), float(np.mean(pr.rho)) * m.nel)
+t4 = time.perf_counter()
+print(json.dumps(dict(seconds=t4 - t0, build_solve=t1 - t0, sens=t2 - t1, indicator=t3 - t2, oc=t4 - t3,
                       free_dofs=int(m.ndof - len(fixed)), C=C)))
 """
 
 
 def run_oracle_sample(workload, steps=1):
     """Time the oracle single-threaded (BLAS/OpenMP pinned to 1 thread) on a bounded sample of the
-    workload; returns (seconds per pass, info)."""
+    workload; returns (median seconds per pass, info of the last pass)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     res = []
     for _ in range(steps):
@@ -101,6 +129,7 @@ def run_oracle_sample(workload, steps=1):
     return statistics.median(x["seconds"] for x in res), res[-1]
 
 
+@functools.lru_cache(maxsize=None)
 def free_dofs_of(workload):
     import workloads as W
     from oracle import mesh as om
@@ -110,17 +139,23 @@ def free_dofs_of(workload):
     return int(m.ndof - len(fixed))
 
 
-def cpu_baseline(workload, steps=1):
-    """Oracle on the bounded sample, scaled to the workload by free DOFs (the oracle's cost grows
-    at least linearly with the DOFs, so the scaled rate is an upper bound on its full-size rate)."""
+def oracle_rate(workload, steps=1):
+    """(scaled TO-iter/s, measured seconds per sample step, description).  The oracle's TO iteration
+    on the sample is timed; its rate is scaled to the workload by free DOFs, which is optimistic for
+    the oracle at full size (its sparse factorisation grows faster than linearly)."""
     sample = SAMPLE_WORKLOAD.get(workload, workload)
     sec, info = run_oracle_sample(sample, steps)
     scale = info["free_dofs"] / free_dofs_of(workload)
-    value = scale / sec
-    return dict(value=value, unit=UNIT, cores=1, kind="oracle",
-                sample=f"{sample}: one full oracle pass (assemble, equilibrated sparse LU + refinement, "
-                       f"sensitivity, indicators, map update) in {sec:.2f} s single-threaded, scaled by free "
-                       f"DOFs {info['free_dofs']}/{free_dofs_of(workload)}")
+    desc = (f"{sample}: one oracle TO iteration (assemble, equilibrated sparse LU + refinement, sensitivity, "
+            f"indicators, map update, OC) timed single-threaded: median {sec:.2f} s of {steps}; the rate is "
+            f"scaled to {workload} by free DOFs {info['free_dofs']}/{free_dofs_of(workload)} (optimistic for "
+            f"the oracle); CPU {cpu_model()}")
+    return scale / sec, sec, desc
+
+
+def cpu_baseline(workload, steps=1):
+    value, sec, desc = oracle_rate(workload, steps)
+    return dict(value=value, unit=UNIT, cores=1, kind="oracle", sample=desc, sample_seconds_per_step=sec)
 
 
 # ------------------------------------------------------------------------------------ clocks
@@ -202,183 +237,177 @@ def whole_job_rate(world, steps, max_ms):
     return world * steps / (max_ms * 1e-3)
 
 
-def run_oc_loop(args, rank, world, local_rank):
-    """One optimization run: args.oc_iters iterations of build, mixed solve (warm-started from the
-    previous displacement), FP64 sensitivity and OC update (volume fraction of the initial design,
-    move 0.2, eta 0.5), timed as a whole after args.warmup untimed iterations on a copy."""
-    import numpy as np
-    import torch
-    import paper_1811_09821_gb300 as mto
-    import workloads as W
+def operator_bytes(pr, ndof):
+    """Algorithmic bytes of one split-operator launch: per element the hi/lo pair of its matrix in
+    the circulant-diagonal row ((n_e/2 + 1) n_e entries, 2 x 4 bytes) and its node map (4 bytes per
+    node); per DOF one FP64 read of x and one FP64 write of y."""
+    nn = [(int(p) + 1) ** 2 for p in pr.p]
+    return sum(8 * (n + 1) * (2 * n) + 4 * n for n in nn) + 16 * ndof
 
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    pr = W.named(args.workload)
-    stream = torch.cuda.Stream(dev)
-    torch.cuda.set_stream(stream)
-    h = mto.Handle(local_rank, stream=stream)
-    ndof, dlen = h.setup(pr.nelx, pr.nely, pr.p, pr.d)
-    fixed, f = mto.load_case(h, pr.load)
-    h.set_supports(fixed)
-    mat = mto.material(pr.E0, pr.Emin, pr.nu, pr.q)
-    vol = float(np.mean(pr.rho))
-    pc = {"schwarz": mto.PREC_SCHWARZ, "jacobi": mto.PREC_JACOBI, "mg": mto.PREC_MG}[args.precond]
 
-    def run(iters):
-        rho = torch.tensor(pr.rho, dtype=torch.float64, device=dev)
-        rho_new = torch.empty_like(rho)
-        u = torch.zeros(ndof, dtype=torch.float64, device=dev)
-        dc = torch.zeros(dlen, dtype=torch.float64, device=dev)
-        hist, its = [], 0
-        for k in range(iters):
-            h.build_elements(rho, mat, mto.MTO_MIXED)
-            it, _ = h.solve(f, u, precision=mto.MTO_MIXED, rtol=args.rtol, max_iter=400000, check_every=32,
-                            precond=pc, mg_degree=args.mg_degree, warm_start=k > 0)
-            its += it
-            hist.append(h.sensitivity(u, f, rho, mat, dc, precision=mto.MTO_FP64))
-            h.oc_update(rho, dc, vol, rho_new, want_lambda=False)
-            rho, rho_new = rho_new, rho
-        return hist, its
+class Run:
+    """One problem instance on the GPU with the state of an optimization run."""
 
-    if args.warmup:
-        run(min(args.warmup, 2))
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local_rank) as clk:
-        e0.record(stream)
-        hist, its = run(args.oc_iters)
-        e1.record(stream)
+    def __init__(self, mto, W, pr, dev, stream, local_rank, args):
+        import numpy as np
+        import torch
+        self.mto, self.torch, self.args = mto, torch, args
+        self.pr, self.dev, self.stream = pr, dev, stream
+        self.h = mto.Handle(local_rank, stream=stream)
+        self.ndof, self.dlen = self.h.setup(pr.nelx, pr.nely, pr.p, pr.d)
+        self.fixed, self.f = mto.load_case(self.h, pr.load)
+        self.h.set_supports(self.fixed)
+        self.nfree = self.ndof - len(self.fixed)
+        self.mat = mto.material(pr.E0, pr.Emin, pr.nu, pr.q)
+        self.vol = float(np.mean(pr.rho))
+        self.rho0 = torch.tensor(pr.rho, dtype=torch.float64, device=dev)
+        self.reset()
+
+    def reset(self):
+        t = self.torch
+        self.rho = self.rho0.clone()
+        self.rho_new = t.empty_like(self.rho)
+        self.u = t.zeros(self.ndof, dtype=t.float64, device=self.dev)
+        self.dc = t.zeros(self.dlen, dtype=t.float64, device=self.dev)
+        self.k = 0
+
+    def step(self, prec, advance=True):
+        """One pass of the hot path: build, solve, sensitivity, indicator + map update, OC update.
+        advance: continue the optimization run (the next design is the OC update), else keep the
+        design."""
+        mto, h = self.mto, self.h
+        h.build_elements(self.rho, self.mat, prec)
+        it, rr = h.solve(self.f, self.u, precision=prec, rtol=self.args.rtol, norm=mto.NORM_ENERGY,
+                         max_iter=400000, check_every=32, precond=mto.PREC_MG, mg_degree=self.args.mg_degree,
+                         warm_start=advance and self.k > 0)
+        h.sensitivity(self.u, self.f, self.rho, self.mat, self.dc, precision=mto.MTO_FP64, want_C=False)
+        h.indicator(self.u, self.rho, self.mat)
+        h.oc_update(self.rho, self.dc, self.vol, self.rho_new, want_lambda=False)
+        if advance:
+            self.rho, self.rho_new = self.rho_new, self.rho
+            self.k += 1
+        return it
+
+    def compliance(self, rho):
+        return self.h.compliance_energy(self.u, self.f, rho, self.mat)
+
+
+def timed_steps(run, prec, steps, warmup, advance, flush):
+    """warmup untimed steps then `steps` steps timed with CUDA events on the run's stream (L2 flushed
+    before each).  Returns dict(ms, iters, launches, families, last) with the design and the solved
+    displacement of the last timed step kept for the accuracy check."""
+    torch = run.torch
+    for _ in range(warmup):
+        run.step(prec, advance)
+    torch.cuda.synchronize(run.dev)
+    run.h.timing_enable("sampled")
+    l0 = run.h.launch_count()
+    total_ms, iters = 0.0, 0
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(run.stream)
+        rho_in = run.rho
+        it = run.step(prec, advance)
+        e1.record(run.stream)
         e1.synchronize()
-    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
-    h.close()
-    return {
-        "metric": METRIC, "value": whole_job_rate(world, args.oc_iters, ms), "unit": UNIT, "n_gpus": world,
-        "steps": args.oc_iters, "warmup": args.warmup, "ms_per_step": ms / args.oc_iters, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32x2 split operator (f32 pipes) in inner PCG, f64 vectors/refinement/dots/compliance",
-        "data": "synthetic",
-        "config": {"workload": args.workload, "nelx": pr.nelx, "nely": pr.nely, "p": int(pr.p[0]), "d": int(pr.d[0]),
-                   "design_values": dlen, "rtol": args.rtol, "precond": args.precond, "solve": "mixed",
-                   "oc_iterations": args.oc_iters, "volume_fraction": vol, "parallelism": f"replicas x{world}"},
-        "pcg_iters_total": its, "compliance_history": hist, "clocks": clk.summary(),
-    }
+        total_ms += e0.elapsed_time(e1)
+        iters += it
+    launches = run.h.launch_count() - l0
+    tm = run.h.timing_read()
+    run.h.timing_enable(False)
+    last = dict(rho=rho_in.clone(), u=run.u.clone())   # the last step's design (before its update) and u
+    return dict(ms=total_ms, iters=iters, launches=launches, families=tm, last=last)
+
+
+def accuracy_check(run, last, prec):
+    """The compliance (energy form) of a timed step's own solution against an FP64 re-solve on the
+    same design to 1e-2 of the bench tolerance, warm-started from it.  Returns a dict."""
+    mto, h = run.mto, run.h
+    rho, u = last["rho"], last["u"].clone()
+    C = h.compliance_energy(u, run.f, rho, run.mat)
+    h.build_elements(rho, run.mat, mto.MTO_FP64)
+    it, _ = h.solve(run.f, u, precision=mto.MTO_FP64, rtol=run.args.rtol * 1e-2, norm=mto.NORM_ENERGY,
+                    max_iter=400000, check_every=32, precond=mto.PREC_MG, mg_degree=run.args.mg_degree,
+                    warm_start=True)
+    Cr = h.compliance_energy(u, run.f, rho, run.mat)
+    return {"path": "mixed" if prec == mto.MTO_MIXED else "fp64", "C": C, "C_fp64_ref": Cr,
+            "rel_err": abs(C - Cr) / abs(Cr), "ref_iters": it}
 
 
 def run_gpu(args, rank, world, local_rank):
-    import numpy as np
     import torch
     import paper_1811_09821_gb300 as mto
     import workloads as W
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    t_gen = time.perf_counter()
     pr = W.named(args.workload)
+    t_gen = time.perf_counter() - t_gen
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    h = mto.Handle(local_rank, stream=stream)
-    ndof, dlen = h.setup(pr.nelx, pr.nely, pr.p, pr.d)
-    fixed, f = mto.load_case(h, pr.load)
-    h.set_supports(fixed)
-    nfree = ndof - len(fixed)
-    mat = mto.material(pr.E0, pr.Emin, pr.nu, pr.q)
-    rho = torch.tensor(pr.rho, dtype=torch.float64, device=dev)
-    u = torch.zeros(ndof, dtype=torch.float64, device=dev)
-    dc = torch.zeros(dlen, dtype=torch.float64, device=dev)
-    rho_new = torch.zeros(dlen, dtype=torch.float64, device=dev)
-    vol = float(np.mean(pr.rho))
+    run = Run(mto, W, pr, dev, stream, local_rank, args)
+    advance = args.mode == "oc"
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
-
-    pc = {"schwarz": mto.PREC_SCHWARZ, "jacobi": mto.PREC_JACOBI, "mg": mto.PREC_MG}[args.precond]
-
-    def step(prec):
-        h.build_elements(rho, mat, prec)
-        sprec = mto.MTO_FP64 if prec == mto.MTO_FP64 else (mto.MTO_MIXED if args.solve == "mixed" else mto.MTO_MIXED32)
-        it, rr = h.solve(f, u, precision=sprec, rtol=args.rtol, max_iter=400000, check_every=32, precond=pc,
-                         mg_degree=args.mg_degree)
-        h.sensitivity(u, f, rho, mat, dc, precision=mto.MTO_FP64, want_C=False)
-        h.indicator(u, rho, mat)
-        h.oc_update(rho, dc, vol, rho_new, want_lambda=False)
-        return it, rr
-
-    def timed(prec, steps, warmup):
-        for _ in range(warmup):
-            step(prec)
-        torch.cuda.synchronize(dev)
-        h.timing_enable("sampled")          # events around one operator launch per chunk of iterations
-        l0 = h.launch_count()
-        total_ms, iters, rrs = 0.0, 0, []
-        for _ in range(steps):
-            flush.fill_(1.0)                     # L2 flush outside the timed step
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            it, rr = step(prec)
-            e1.record(stream)
-            e1.synchronize()
-            total_ms += e0.elapsed_time(e1)
-            iters += it
-            rrs.append(rr)
-        tm = h.timing_read()
-        h.timing_enable(False)
-        return dict(ms=total_ms, iters=iters, relres=max(rrs), launches=h.launch_count() - l0, families=tm)
 
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local_rank) as clk:
-        wall0 = time.perf_counter()
-        mixed = timed(mto.MTO_MIXED, args.steps, args.warmup)
-        wall1 = time.perf_counter()
+        mixed = timed_steps(run, mto.MTO_MIXED, args.steps, args.warmup, advance, flush)
     torch.cuda.synchronize(dev)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     mixed_ms_max = max_over_ranks(mixed["ms"], world, dev)
-    C_mixed = h.sensitivity(u, f, rho, mat, dc, precision=mto.MTO_FP64)
+    steps = args.steps
 
-    fp64 = None
-    if not args.no_fp64:
-        fp64 = timed(mto.MTO_FP64, max(1, min(args.steps, 3)), 1)
-        C_fp64 = h.sensitivity(u, f, rho, mat, dc, precision=mto.MTO_FP64)
-
-    # end to end through the public API with host buffers: pinned rho and f in, u and dc out
-    rho_h = torch.tensor(pr.rho, dtype=torch.float64).pin_memory()
-    f_h = f.cpu().pin_memory()
-    u_h = torch.empty(ndof, dtype=torch.float64).pin_memory()
-    dc_h = torch.empty(dlen, dtype=torch.float64).pin_memory()
+    # end to end through the public API with host buffers: design and load in, displacement and
+    # sensitivities out, every step (the mixed path, continuing the same run)
+    rho_h = run.rho.cpu().pin_memory()
+    f_h = run.f.cpu().pin_memory()
+    u_h = torch.empty(run.ndof, dtype=torch.float64).pin_memory()
+    dc_h = torch.empty(run.dlen, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(steps, 3))
     e2e_ms = 0.0
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         flush.fill_(1.0)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        rho.copy_(rho_h, non_blocking=True)
-        f.copy_(f_h, non_blocking=True)
-        step(mto.MTO_MIXED)
-        u_h.copy_(u, non_blocking=True)
-        dc_h.copy_(dc, non_blocking=True)
+        run.rho.copy_(rho_h, non_blocking=True)
+        run.f.copy_(f_h, non_blocking=True)
+        run.step(mto.MTO_MIXED, advance)
+        u_h.copy_(run.u, non_blocking=True)
+        dc_h.copy_(run.dc, non_blocking=True)
+        rho_h.copy_(run.rho, non_blocking=True)      # the updated design returns to the host
         torch.cuda.synchronize(dev)
         e2e_ms += (time.perf_counter() - t0) * 1e3
 
+    fp64 = None
+    if not args.no_fp64:
+        run.reset()
+        fsteps = max(1, min(steps, args.fp64_steps))
+        fp64 = timed_steps(run, mto.MTO_FP64, fsteps, args.warmup, advance, flush)
+
+    # accuracy of both paths on their last timed step: the step's own solution against an FP64
+    # re-solve on the same design
+    checks = [accuracy_check(run, mixed["last"], mto.MTO_MIXED)]
+    if fp64:
+        checks.append(accuracy_check(run, fp64["last"], mto.MTO_FP64))
+
     peaks = measured_peaks()
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    fam = "apply32" if args.solve == "mixed32" else "applydf64"
-    n_apply, apply_ms = mixed["families"][fam]
-    # algorithmic bytes of one operator launch: the split-precision pair of the element matrix in
-    # its circulant-diagonal row ((n_e/2 + 1) n_e entries, 2 x 4 bytes; 544 for Q3) and the node map
-    # per element, one read of x and one write of y per DOF (4 bytes FP32, 8 bytes FP64 vectors)
-    vb = 4 if args.solve == "mixed32" else 8
-    nn = [(int(p) + 1) ** 2 for p in pr.p]
-    kbytes = sum(8 * ((2 * n) // 2 + 1) * (2 * n) + 4 * n for n in nn)
-    bytes_per_launch = kbytes + 2 * vb * ndof
+    hbm = peaks.get("hbm_gbs")
+    n_apply, apply_ms = mixed["families"]["applydf64"]
+    bytes_per_launch = operator_bytes(pr, run.ndof)
     ncls = len(set(int(p) for p in pr.p))
     avg_ms = apply_ms / max(n_apply, 1) * ncls     # one apply = ncls class launches
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9 if n_apply else None
-    steps = args.steps
+    big = (len(pr.p) * ((2 * (int(pr.p[0]) + 1) ** 2) // 2 + 1) * 2 * (int(pr.p[0]) + 1) ** 2 * 8) > (64 << 20)
+    kernel = ("ebe_df_tma_kernel<3,double> (split-precision element operator, bulk-copy staged rows)" if big else
+              "ebe_df_pipe_kernel<3,double> (split-precision element operator, register-pipelined rows)")
     out = {
         "metric": METRIC,
         "value": whole_job_rate(world, steps, mixed_ms_max),
@@ -390,49 +419,54 @@ def run_gpu(args, rank, world, local_rank):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": ("f32x2 split operator (f32 pipes) in inner PCG, f64 vectors/refinement/dots/compliance"
-                  if args.solve == "mixed" else "f32 inner PCG + f64 refinement/dots/compliance"),
+        "dtype": "f32x2 split operator (f32 pipes) in the inner PCG; f64 vectors, dots, refinement, compliance",
         "data": "synthetic",
         "config": {"workload": args.workload, "nelx": pr.nelx, "nely": pr.nely, "p": int(pr.p[0]),
-                   "d": int(pr.d[0]), "free_dofs": nfree, "design_values": dlen, "rtol": args.rtol,
-                   "residual_norm": "l2", "precond": args.precond, "solve": args.solve,
-                   "l2_flush": "512 MB write between timed steps",
+                   "d": int(pr.d[0]), "free_dofs": run.nfree, "design_values": run.dlen,
+                   "mode": args.mode, "step": ("one TO iteration of one optimization run (build, warm-started "
+                                               "solve, sensitivity, indicator + map update, OC update); warm-up = "
+                                               "its first iterations" if advance else
+                                               "one pass over the fixed design from a zero start"),
+                   "solve_accuracy": f"relative compliance error {args.rtol:g} (energy test)",
+                   "precond": "multigrid", "l2_flush": "512 MB write before each timed step",
                    "parallelism": f"replicas x{world}"},
-        "mdof_pcg_iter_per_s": nfree * mixed["iters"] / (mixed["ms"] * 1e-3) / 1e6,
+        "mdof_pcg_iter_per_s": run.nfree * mixed["iters"] / (mixed["ms"] * 1e-3) / 1e6,
         "pcg_iters_per_step": mixed["iters"] / steps,
-        "relres": mixed["relres"],
         "sampled_operator_launches": {k: {"launches": v[0], "avg_us": round(1e3 * v[1] / max(v[0], 1), 3)}
                                       for k, v in mixed["families"].items() if v[0]},
         "gpu_launches": mixed["launches"],
-        "roofline": {"bound": "hbm",
-                     "kernel": (f"ebe_df_pipe_kernel<3,{'float' if vb == 4 else 'double'}> (split-precision element "
-                                "operator; ebe_df_tma_kernel for classes above 64 MB of rows)"),
-                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None,
-                     "traffic": MEASURED_TRAFFIC.get(args.workload) if args.solve == "mixed" else None,
-                     "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_ms * 1e3,
-                     "note": "peak = measured HBM copy; the element rows stream from DRAM on every launch "
-                             "(the multigrid cycle between launches evicts them from L2)"},
+        "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if (achieved and hbm) else None,
+                     "traffic": None,
+                     "traffic_note": "DRAM bytes per launch are taken by ncu and summarised under profiles/ "
+                                     "(not measured inside this run)",
+                     "peak_note": "measured HBM copy of MEASURED_PEAKS.json" if hbm else "no measured peak file",
+                     "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_ms * 1e3},
+        "accuracy": checks,
         "clocks": clk.summary(),
-        "e2e": {"value": world * steps / (e2e_ms * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": 8 * (dlen + ndof), "d2h_bytes_per_step": 8 * (ndof + dlen)},
+        "e2e": {"value": world * e2e_steps / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": 8 * (run.dlen + run.ndof),
+                "d2h_bytes_per_step": 8 * (run.ndof + (2 * run.dlen if advance else run.dlen))},
+        "host_generation_s": t_gen,
     }
     if fp64:
-        out["fp64_path"] = {"value": fp64["ms"] and (max(1, min(steps, 3)) / (fp64["ms"] * 1e-3)), "unit": UNIT,
-                            "ms_per_step": fp64["ms"] / max(1, min(steps, 3)),
-                            "mdof_pcg_iter_per_s": nfree * fp64["iters"] / (fp64["ms"] * 1e-3) / 1e6,
-                            "pcg_iters_per_step": fp64["iters"] / max(1, min(steps, 3)),
-                            "relres": fp64["relres"],
-                            "sampled_operator_launches": {k: {"launches": v[0], "avg_us": round(1e3 * v[1] / max(v[0], 1), 3)}
+        fsteps = max(1, min(steps, args.fp64_steps))
+        out["fp64_path"] = {"value": fsteps / (fp64["ms"] * 1e-3), "unit": UNIT, "steps": fsteps,
+                            "ms_per_step": fp64["ms"] / fsteps,
+                            "mdof_pcg_iter_per_s": run.nfree * fp64["iters"] / (fp64["ms"] * 1e-3) / 1e6,
+                            "pcg_iters_per_step": fp64["iters"] / fsteps,
+                            "sampled_operator_launches": {k: {"launches": v[0],
+                                                              "avg_us": round(1e3 * v[1] / max(v[0], 1), 3)}
                                                           for k, v in fp64["families"].items() if v[0]}}
         out["speedup_vs_fp64"] = out["value"] / world / out["fp64_path"]["value"]
-        out["C_rel_diff_mixed_vs_fp64"] = abs(C_mixed - C_fp64) / abs(C_fp64)
-    h.close()
+    run.h.close()
     return out
 
 
-def main():
-    args = parse()
+def main(argv=None):
+    args = parse(argv)
+    if args.mode is None:
+        args.mode = "oc" if args.workload == DEFAULT_WORKLOAD else "pass"
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -442,24 +476,20 @@ def main():
         sample = SAMPLE_WORKLOAD.get(args.workload, args.workload)
         for _ in range(args.warmup):
             run_oracle_sample(sample, 1)
-        t0 = time.perf_counter()
-        sec, info = run_oracle_sample(sample, args.steps)
+        value, sec, desc = oracle_rate(args.workload, args.steps)
         import workloads as W
         pr = W.named(args.workload)
-        nfree = free_dofs_of(args.workload)
-        scale = info["free_dofs"] / nfree
-        value = scale / sec
         print(json.dumps({
             "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "nelx": pr.nelx, "nely": pr.nely, "p": int(pr.p[0]),
-                       "d": int(pr.d[0]), "free_dofs": nfree, "design_values": int(len(pr.rho)),
-                       "rtol": args.rtol, "residual_norm": "l2", "sample": sample,
+                       "d": int(pr.d[0]), "free_dofs": free_dofs_of(args.workload),
+                       "design_values": int(len(pr.rho)), "sample": sample,
                        "parallelism": "rank 0 only (host cores)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{sample}, median of {args.steps} single-threaded oracle passes "
-                                       f"({sec:.2f} s each), scaled by free DOFs"},
+            "note": "ms_per_step is the measured time of one oracle step on the sample; value is that rate "
+                    "scaled to the workload by free DOFs",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }), flush=True)
         return 0
@@ -467,11 +497,6 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    if args.oc_iters > 0:
-        out = run_oc_loop(args, rank, world, local_rank)
-        if rank == 0:
-            print(json.dumps(out), flush=True)
-        return 0
     out = run_gpu(args, rank, world, local_rank)
     if rank == 0:
         if not args.no_cpu:

@@ -89,9 +89,20 @@ typedef struct {
  *  max_outer   limit on refinement steps (<= 0: 50).
  *  warm_start  nonzero: u on entry is the initial guess (else zero).
  *  check_every PCG iterations between host convergence checks (>= 1).
- *  norm        residual norm of the stopping tests: MTO_NORM_L2 (||r||_2 / ||f||_2) or
- *              MTO_NORM_JACOBI (sqrt(r^T D^-1 r / f^T D^-1 f), D = diag(K)); the scaled norm also
- *              weighs the rows of nearly void regions (stiffness ~ Emin), which the l2 norm ignores.
+ *  norm        stopping test: MTO_NORM_L2 (||r||_2 / ||f||_2 <= rtol) or MTO_NORM_JACOBI
+ *              (sqrt(r^T D^-1 r / f^T D^-1 f) <= rtol, D = diag(K); the scaled norm also weighs the
+ *              rows of nearly void regions, stiffness ~ Emin, which the l2 norm ignores), or
+ *              MTO_NORM_ENERGY: compliance accuracy, (C* - C(u)) / C <= rtol for the energy form
+ *              C(u) = 2 f^T u - u^T K u of Eq. 1's compliance (its error is ||u* - u||_K^2).  One
+ *              correction solve from the residual of the start vector; CG from zero gains
+ *              alpha_i r_i^T z_i of energy per iteration and the remaining gains are the error;
+ *              they are extrapolated from the sums of the last two windows of 32 gains (S_last,
+ *              S_prev: error ~ S_last / (1 - S_last / S_prev)) and the stop is taken when that is
+ *              below rtol / 4 times the compliance estimate (a margin for uneven decay).  rtol is then a relative compliance
+ *              error (not squared); *relres still reports the l2 residual.
+ *              Needs FP64 vectors (MTO_FP64 or MTO_MIXED).  At 10^7 DOFs and stiffness contrasts
+ *              of 1e9 the l2 residual of an FP64 evaluation floors near 1e-7, so l2 tolerances
+ *              below that cannot be met there, while compliance accuracy can.
  *  precond     MTO_PREC_JACOBI (point Jacobi), MTO_PREC_SCHWARZ (element-block additive Schwarz:
  *              per element the inverse of K_e plus the neighbours' share of the assembled diagonal,
  *              which captures the near-null modes of solid/void elements) or MTO_PREC_MG (one
@@ -101,7 +112,7 @@ typedef struct {
  *              halve down to a coarsest grid of at most 2048 DOFs, else MTO_EINVAL).
  *  inner_max   mixed solves: cap on the iterations of one inner solve (<= 0: none).
  *  mg_degree   MTO_PREC_MG only: Chebyshev degree of each pre- and post-smoothing on the fine
- *              level (<= 0: 4; at most 16); the Q1 levels use degree 2.
+ *              level (<= 0: 4; at most 16); the Q1 levels use degree 4.
  * CG iterations run in chunks of check_every (rounded up to a multiple of 4), each a CUDA graph;
  * the reported count stops at convergence, but a chunk already launched completes (cheaply). */
 typedef struct {
@@ -124,6 +135,7 @@ typedef struct {
 
 #define MTO_NORM_L2 0
 #define MTO_NORM_JACOBI 1
+#define MTO_NORM_ENERGY 2
 
 /* Indicator / map-update options (Sec. 3.2, 3.3; values of the paper in brackets).
  *  cycle           adaptive cycle index k~, from 1                                    [1, 2, ...]
@@ -249,6 +261,17 @@ mto_status mto_set_build_path(mto_handle h, int32_t path);
  * then no synchronisation).  At least one of the two must be given. */
 mto_status mto_compliance(mto_handle h, const double* f, const double* u, double* C_dev, double* C);
 
+/* Compliance of an approximate displacement in its energy form (Eq. 1 with z = f):
+ * C(u) = 2 f^T u - u^T K(rho) u, which equals f^T u at the exact solution and differs from the exact
+ * compliance by ||u* - u||_K^2 (second order), so it carries the accuracy that the
+ * MTO_NORM_ENERGY solve test controls; f^T u alone is only first-order accurate after a
+ * warm-started solve.  u^T K u is summed from element energies sum_s E(rho_s) u_e^T K0_s u_e
+ * (each after removing the element's rigid motion in FP64; no global cancellation), in a fixed
+ * order.  u, f: device double[ndof]; rho: device double[design_len] (the densities of the build);
+ * C: host double.  Synchronises. */
+mto_status mto_compliance_energy(mto_handle h, const double* u, const double* f, const double* rho,
+                                 const mto_material* mat, double* C);
+
 /* Step (b): solve K u = f on the free DOFs (u = 0 on supports) with the options above, using the
  * matrices of the last mto_build_elements.  f: device double[ndof]; u: device double[ndof]
  * (initial guess when opts->warm_start, overwritten with the solution).  *iters receives the
@@ -257,6 +280,29 @@ mto_status mto_compliance(mto_handle h, const double* f, const double* u, double
  * MTO_ENAN on a breakdown.  Synchronises the stream. */
 mto_status mto_solve(mto_handle h, const double* f, double* u, const mto_solve_opts* opts,
                      int32_t* iters, double* relres);
+
+/* Batched calls over n independent instances (one handle each, all on one device; the handles may
+ * differ in mesh size, orders, design counts and load case).  Every instance keeps its own stream,
+ * workspace and captured CG iteration graphs, so the instances run concurrently on the GPU:
+ *  - mto_build_elements_batched: the builds of all instances, asynchronous (rho[i]: device,
+ *    instance i's packed design).
+ *  - mto_solve_batched: the solves of all instances, advanced together.  The refinement loop of
+ *    each (FP64 or MTO_MIXED; the options apply to all, see mto_solve_opts) is kept as a
+ *    resumable state; each round launches every unfinished instance's next step (its next chunk
+ *    of CG iterations as one CUDA graph launch, or its next residual) on its own stream and then
+ *    synchronises once for all, so the host waits once per round instead of once per chunk per
+ *    instance.  f[i], u[i]: device double[ndof_i].  iters, relres: host [n] (may be NULL);
+ *    status: host mto_status[n] (may be NULL) per instance.  Returns MTO_OK when every instance
+ *    converged, else the first failing status (the others still ran to completion).  Handles
+ *    must be distinct.  Synchronises.
+ *  - mto_sensitivity_batched: step (c) of all instances (FP64); C: host double[n] (may be NULL:
+ *    then asynchronous). */
+mto_status mto_build_elements_batched(mto_handle* hs, int32_t n, const double* const* rho, const mto_material* mat,
+                                      int32_t precision);
+mto_status mto_solve_batched(mto_handle* hs, int32_t n, const double* const* f, double* const* u,
+                             const mto_solve_opts* opts, int32_t* iters, double* relres, mto_status* status);
+mto_status mto_sensitivity_batched(mto_handle* hs, int32_t n, const double* const* u, const double* const* f,
+                                   const double* const* rho, const mto_material* mat, double* const* dc, double* C);
 
 /* y = K x on all DOFs (the assembled operator including supported rows), FP64, with the FP64
  * matrices of the last build.  x, y: device double[ndof].  Asynchronous. */
@@ -283,6 +329,17 @@ mto_status mto_apply_operator(mto_handle h, int32_t op, const double* x, double*
 #define MTO_OPK_STAGED 1
 #define MTO_OPK_GENERIC 2
 mto_status mto_set_operator_kernel(mto_handle h, int32_t kernel);
+
+/* Autotuner (project-written): for every order class with n_e <= 32 times the split operator's three
+ * kernels (register pipeline, bulk-copy staging, generic; CUDA events over 5 launches on the
+ * class's own rows after 2 warm-up launches) and keeps the fastest for that class in the handle;
+ * the choice is also cached process-wide by (device, order, element count), so later handles with
+ * a class of the same size reuse it without timing.  Needs an MTO_MIXED build (it overwrites
+ * internal work vectors only).  choice: host int32[MTO_P_MAX + 1] (may be NULL) receives per order
+ * the chosen MTO_OPK_* (-2 where not tuned); us: host double[3 (MTO_P_MAX + 1)] (may be NULL) the
+ * measured microseconds per launch of each kernel.  mto_set_operator_kernel overrides it.
+ * Synchronises. */
+mto_status mto_autotune(mto_handle h, int32_t* choice, double* us);
 
 /* Inspection (tests, tools): the split-precision pair of element e after an MTO_MIXED build, as two
  * packed upper triangles (row-major, i <= j): hi[c] = fl32(K_e[c]), lo[c] = fl32(K_e[c] - hi[c]).

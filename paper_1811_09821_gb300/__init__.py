@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmto.so")
 
 MTO_FP64, MTO_MIXED, MTO_MIXED32 = 0, 1, 2
-NORM_L2, NORM_JACOBI = 0, 1
+NORM_L2, NORM_JACOBI, NORM_ENERGY = 0, 1, 2
 BUILD_TENSOR, BUILD_SIMT = 0, 1
 OP_FP64, OP_SPLIT = 0, 1
 OPK_AUTO, OPK_PIPE, OPK_STAGED, OPK_GENERIC = -1, 0, 1, 2
@@ -67,7 +67,8 @@ SYMBOLS = ["mto_create", "mto_destroy", "mto_last_error", "mto_set_stream", "mto
            "mto_memory", "mto_launch_count", "mto_compliance_noalloc", "mto_compliance", "mto_apply_operator",
            "mto_set_operator_kernel", "mto_element_matrix_split", "mto_edge_dofs", "mto_side_load",
            "mto_set_springs", "mto_sensitivity_adjoint", "mto_side_dofs_in",
-           "mto_filter", "mto_filter_adjoint", "mto_transfer_design"]
+           "mto_filter", "mto_filter_adjoint", "mto_transfer_design", "mto_compliance_energy",
+           "mto_autotune", "mto_build_elements_batched", "mto_solve_batched", "mto_sensitivity_batched"]
 TIME_FAMILIES = {"apply32": 0, "apply64": 1, "build": 2, "sens": 3, "indicator": 4, "vector": 5, "applydf64": 6,
                  "precond": 7}
 
@@ -115,6 +116,11 @@ def load_library(path=LIB_PATH):
         "mto_side_dofs_in": ([vp, i32, i32, dbl, dbl, P(i64), i64, P(i64)], ctypes.c_int),
         "mto_filter": ([vp, dbl, vp, vp], ctypes.c_int),
         "mto_transfer_design": ([vp, P(i32), vp, vp], ctypes.c_int),
+        "mto_compliance_energy": ([vp, vp, vp, vp, P(Material), P(dbl)], ctypes.c_int),
+        "mto_autotune": ([vp, P(i32), P(dbl)], ctypes.c_int),
+        "mto_build_elements_batched": ([P(vp), i32, P(vp), P(Material), i32], ctypes.c_int),
+        "mto_solve_batched": ([P(vp), i32, P(vp), P(vp), P(SolveOpts), P(i32), P(dbl), P(i32)], ctypes.c_int),
+        "mto_sensitivity_batched": ([P(vp), i32, P(vp), P(vp), P(vp), P(Material), P(vp), P(dbl)], ctypes.c_int),
         "mto_filter_adjoint": ([vp, dbl, vp, vp], ctypes.c_int),
         "mto_sensitivity_adjoint": ([vp, vp, vp, vp, P(Material), vp], ctypes.c_int),
         "mto_apply_operator": ([vp, i32, vp, vp, P(dbl)], ctypes.c_int),
@@ -280,6 +286,15 @@ class Handle:
                                               ctypes.byref(v) if want_xKx else None))
         return v.value if want_xKx else None
 
+    def autotune(self):
+        """Time the split operator's kernels per order class and keep the fastest; returns
+        {p: (chosen kernel, [us pipe, us staged, us generic])} for the tuned classes."""
+        ch = np.zeros(P_MAX + 1, np.int32)
+        us = np.zeros(3 * (P_MAX + 1))
+        self._check(self.L.mto_autotune(self.h, ch.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                        us.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return {p: (int(ch[p]), us[3 * p:3 * p + 3].tolist()) for p in range(1, P_MAX + 1) if ch[p] >= -1}
+
     def set_operator_kernel(self, kernel):
         self._check(self.L.mto_set_operator_kernel(self.h, kernel))
 
@@ -291,6 +306,13 @@ class Handle:
         fp = ctypes.POINTER(ctypes.c_float)
         self._check(self.L.mto_element_matrix_split(self.h, e, hi.ctypes.data_as(fp), lo.ctypes.data_as(fp)))
         return hi, lo
+
+    def compliance_energy(self, u, f, rho, mat):
+        """C(u) = 2 f^T u - u^T K(rho) u from element energies (second-order accurate in u's error)."""
+        C = ctypes.c_double()
+        self._check(self.L.mto_compliance_energy(self.h, _ptr(u, torch.float64), _ptr(f, torch.float64),
+                                                 _ptr(rho, torch.float64), ctypes.byref(mat), ctypes.byref(C)))
+        return C.value
 
     def compliance(self, f, u, out=None):
         """C = f^T u in the handle's workspace: into the device scalar ``out`` (asynchronous) when
@@ -410,6 +432,66 @@ def compliance_noalloc(f, u, out, n=None, device=0, stream=None):
     L = load_library()
     st = stream.cuda_stream if stream is not None else torch.cuda.current_stream(device).cuda_stream
     return L.mto_compliance_noalloc(device, f.data_ptr(), u.data_ptr(), n, ctypes.c_void_p(st), out.data_ptr())
+
+
+def _ptrs(ts, dtype=torch.float64):
+    arr = (ctypes.c_void_p * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = _ptr(t, dtype).value
+    return arr
+
+
+def _handles(hs):
+    arr = (ctypes.c_void_p * len(hs))()
+    for i, h in enumerate(hs):
+        arr[i] = h.h.value
+    return arr
+
+
+def _check_batch(L, hs, st):
+    if st != 0:
+        msgs = [h.L.mto_last_error(h.h).decode() for h in hs]
+        raise MTOError(st, "; ".join(m for m in msgs if m) or "batched call failed")
+
+
+def build_elements_batched(handles, rhos, mat, precision=MTO_MIXED):
+    """Step (a) of every instance (asynchronous, each on its handle's stream)."""
+    L = load_library()
+    _check_batch(L, handles, L.mto_build_elements_batched(_handles(handles), len(handles), _ptrs(rhos),
+                                                          ctypes.byref(mat), precision))
+
+
+def solve_batched(handles, fs, us, precision=MTO_MIXED, rtol=1e-8, inner_rtol=0.0, max_iter=200000, max_outer=50,
+                  warm_start=False, check_every=32, norm=NORM_ENERGY, precond=PREC_MG, inner_max=0, mg_degree=0,
+                  raise_on_error=True):
+    """Step (b) of every instance, advanced together (mto_solve_batched).  Returns (iterations,
+    relative residuals, statuses) as numpy arrays."""
+    L = load_library()
+    n = len(handles)
+    o = SolveOpts(precision, rtol, inner_rtol, max_iter, max_outer, int(bool(warm_start)), check_every, norm,
+                  precond, inner_max, mg_degree)
+    it = np.zeros(n, np.int32)
+    rr = np.zeros(n)
+    stt = np.zeros(n, np.int32)
+    st = L.mto_solve_batched(_handles(handles), n, _ptrs(fs), _ptrs(us), ctypes.byref(o),
+                             it.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                             rr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             stt.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if raise_on_error:
+        _check_batch(L, handles, st)
+    return it, rr, stt
+
+
+def sensitivity_batched(handles, us, fs, rhos, mat, dcs, want_C=True):
+    """Step (c) of every instance; returns the compliances f^T u (numpy) when want_C."""
+    L = load_library()
+    n = len(handles)
+    C = np.zeros(n)
+    _check_batch(L, handles, L.mto_sensitivity_batched(_handles(handles), n, _ptrs(us), _ptrs(fs), _ptrs(rhos),
+                                                       ctypes.byref(mat), _ptrs(dcs),
+                                                       C.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                                                       if want_C else None))
+    return C if want_C else None
 
 
 def load_case(handle, load):

@@ -17,7 +17,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import (MTO_FP64, MTO_MIXED, PREC_MG, Handle, IndicatorOpts, load_case, material)
+from . import (MTO_FP64, MTO_MIXED, NORM_ENERGY, PREC_MG, Handle, IndicatorOpts, load_case, material)
 
 
 @dataclass
@@ -42,8 +42,10 @@ def converged(J_prev, J_cur, cycle, dJ1=0.04, gamma=0.6):
 
 
 def run(nelx, nely, p, d, rho, load, volfrac, cycles=4, max_iters=60, radius=0.0, precision=MTO_MIXED,
-        rtol=1e-8, dJ1=0.04, gamma=0.6, move=0.2, eta=0.5, mat=None, device=0, keep=False, p_max=5, d_max=64):
+        rtol=1e-9, dJ1=0.04, gamma=0.6, move=0.2, eta=0.5, mat=None, device=0, keep=False, p_max=5, d_max=64):
     """dp-adaptive compliance minimisation.  rho: initial packed design (numpy) for the maps p, d.
+    Each solve is warm-started and stops at the relative compliance accuracy rtol
+    (MTO_NORM_ENERGY); J is the compliance in its energy form (mto_compliance_energy).
     Returns the list of Cycle records; with keep=True each record holds the cycle's last state
     (u, rho, filtered rho, f) as device tensors."""
     mat = mat or material()
@@ -67,10 +69,11 @@ def run(nelx, nely, p, d, rho, load, volfrac, cycles=4, max_iters=60, radius=0.0
             if radius > 0:
                 h.filter(rho_t, rho_f, radius)
             h.build_elements(rho_f, mat, precision)
-            it, _ = h.solve(f, u, precision=precision, rtol=rtol, max_iter=400000, check_every=16,
-                            precond=PREC_MG, warm_start=its > 0)
+            it, _ = h.solve(f, u, precision=precision, rtol=rtol, norm=NORM_ENERGY, max_iter=400000,
+                            check_every=16, precond=PREC_MG, warm_start=its > 0)
             pcg += it
-            J.append(h.sensitivity(u, f, rho_f, mat, dc_f, precision=MTO_FP64))
+            h.sensitivity(u, f, rho_f, mat, dc_f, precision=MTO_FP64, want_C=False)
+            J.append(h.compliance_energy(u, f, rho_f, mat))
             if len(J) > 1 and converged(J[-2], J[-1], k, dJ1, gamma):
                 break
             if its >= max_iters:

@@ -5,8 +5,11 @@
 //
 // Operator layout: one element per group of W lanes (one warp for Q3), element matrices in the
 // circulant-diagonal layout of mto_internal.cuh; see ebe_kernel.
+#include <array>
 #include <chrono>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 
@@ -134,7 +137,25 @@ struct ConvTest {
   int local;           // iteration within the chunk
   int* done;
   int* err;
+  const double* eng;   // energy test (compliance accuracy) instead of the residual test: see EnergyLog
 };
+
+// Compliance-accuracy stopping test.  CG on K d = r from d = 0 gains t_i = alpha_i gamma_i of
+// energy per iteration (gamma_i = r_i^T z_i), and ||d* - d_k||_K^2 = sum_{i >= k} t_i, which is
+// the compliance error C* - (2 f^T u - u^T K u) of u = u_0 + d_k (Hestenes-Stiefel; the error
+// estimates of Strakos and Tichy 2002).  On these problems the gains decay slowly and unevenly, so
+// the remaining sum is extrapolated from the last two windows of kEnergyWin gains: with S_last,
+// S_prev their sums and q = S_last / S_prev < 1, the error is taken as S_last / (1 - q) (the
+// window itself plus a geometric tail); the test stops when that falls below a quarter of tol
+// times the compliance estimate C(u_0) + sum_i t_i, C(u_0) = 2 f^T u_0 - u_0^T K u_0 =
+// f^T u_0 + u_0^T r_0 (the quarter: measured against FP64 re-solves, the extrapolation alone
+// stopped up to ~3x short of tol when the decay of the gains changed pace).
+// Layout of the device array: [0] running sum, [1] C(u_0), [2 .. 2 + 2 kEnergyWin) the gains of
+// the last 2 kEnergyWin iterations by iteration index, [2 + 2 kEnergyWin] the squared l2 residual
+// that ends the run regardless (1e-26 ||f||^2).
+constexpr int kEnergyWin = 32;
+constexpr int kEnergyRing = 2 * kEnergyWin;
+constexpr double kEnergySafety = 0.25;   // the gains decay unevenly: the estimate must be 4x below tol
 
 template <int PO, bool kDF, typename TX>
 __global__ void __launch_bounds__(256) ebe_kernel(const double* __restrict__ K64, const float* __restrict__ Kh,
@@ -571,14 +592,15 @@ template <int PO, bool kDF, typename TX>
 void launch_ebe(mto_handle h, const PClass& c, const double* M64, const float* Mh, const float* Ml, const TX* x,
                 TX* y, Red red, const int* done, const ConvTest& cv) {
   constexpr int NE = 2 * (PO + 1) * (PO + 1);
+  const int opk = h->op_kernel_cls[PO] >= -1 ? h->op_kernel_cls[PO] : h->op_kernel;   // per-class choice first
   if constexpr (kDF && WarpShape<NE>::M == 1) {
-    if (!cv.res && h->op_kernel != 2) {
+    if (!cv.res && opk != 2) {
       const int warps = (c.n + WarpShape<NE>::G - 1) / WarpShape<NE>::G;
       // bulk-copy staging pays off when the rows stream from HBM (measured: 6.5 % faster on
       // 1 GB of rows, 6 % slower when they sit in L2), so by default it serves classes whose
       // split rows exceed 64 MB
       const bool big = (size_t)c.n * c.L * 2 * sizeof(float) > ((size_t)64 << 20);
-      if (h->op_kernel == 1 || (h->op_kernel < 0 && big)) {
+      if (opk == 1 || (opk < 0 && big)) {
         // bulk-copy staging: persistent, as many 8-warp blocks per SM as the shared memory holds
         const size_t smem = tma_smem_bytes(c.L, WarpShape<NE>::G);
         const int per_sm = smem > 0 ? (int)((227u * 1024u) / smem) : 1;
@@ -704,7 +726,7 @@ __global__ void __launch_bounds__(256) cg_vector_kernel(
     int64_t n, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, T* __restrict__ q, T* __restrict__ z,
     const T* __restrict__ invd, const double* __restrict__ gin, int ng, const double* __restrict__ pin, int np,
     Red gout, Red rrout, Red rdout, const int* __restrict__ base, int local, int* __restrict__ done,
-    int* __restrict__ err) {
+    int* __restrict__ err, double* __restrict__ eng) {
   if (*done) return;
   // the step length once per block (an FP64 division per thread costs more than the vector pass
   // on GB300's FP64 pipes)
@@ -716,6 +738,11 @@ __global__ void __launch_bounds__(256) cg_vector_kernel(
     const double a = rz / pq;
     s_stop = (!(pq > 0.0) || !isfinite(a)) ? (rz != 0.0 ? 2 : 1) : 0;
     s_alpha = a;
+    if (eng && blockIdx.x == 0 && !s_stop) {   // energy gained by this step: alpha_i gamma_i
+      const int it = *base + local;
+      eng[2 + it % kEnergyRing] = a * rz;
+      eng[0] += a * rz;
+    }
   }
   __syncthreads();
   const double alpha = s_alpha;
@@ -760,7 +787,28 @@ __global__ void __launch_bounds__(256) cg_direction_kernel(
   __shared__ int s_stop;
   if (threadIdx.x == 0) {
     const double crit = sum_res(cv.res, cv.n);
-    s_stop = !(crit > cv.tol2 * *cv.ref) ? (crit == crit ? 1 : 2) : 0;   // converged, or a NaN residual
+    if (cv.eng) {
+      // compliance accuracy: the extrapolated remaining energy against tol x the compliance estimate
+      const int it = *cv.base + cv.local;
+      int conv = 0;
+      if (it + 1 >= kEnergyRing) {
+        double s_last = 0.0, s_prev = 0.0;
+        for (int k = 0; k < kEnergyWin; ++k) {
+          s_last += __ldcg(cv.eng + 2 + (it - k) % kEnergyRing);
+          s_prev += __ldcg(cv.eng + 2 + (it - kEnergyWin - k) % kEnergyRing);
+        }
+        const double q = s_last / s_prev;
+        const double cref = __ldcg(cv.eng + 1) + __ldcg(cv.eng);
+        conv = q < 1.0 && s_last <= (1.0 - q) * kEnergySafety * cv.tol2 * cref;
+      }
+      // a residual at the floor of FP64 ends the run however few iterations it took (the energy
+      // test needs two windows; a well-conditioned correction converges sooner, and iterating on
+      // rounding noise would break down)
+      conv = conv || crit <= __ldcg(cv.eng + 2 + kEnergyRing);
+      s_stop = !(crit == crit) ? 2 : ((conv || crit == 0.0) ? 1 : 0);
+    } else {
+      s_stop = !(crit > cv.tol2 * *cv.ref) ? (crit == crit ? 1 : 2) : 0;   // converged, or a NaN residual
+    }
     s_beta = s_stop ? 0.0 : sum_res(gnew, ng) / sum_res(gold, ng);
   }
   __syncthreads();
@@ -803,6 +851,10 @@ template <typename T>
 __global__ void __launch_bounds__(256) copy_kernel(int64_t n, const T* __restrict__ a, T* __restrict__ b) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
     b[j] = a[j];
+}
+
+__global__ void add2_kernel(const double* a, const double* b, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = *a + *b;
 }
 
 __global__ void advance_kernel(int* base, int by) {
@@ -891,7 +943,10 @@ __global__ void sum1_kernel(const double* __restrict__ part, int nb, double* __r
   if (threadIdx.x == 0) *out = v;
 }
 
-constexpr int kVecBlocks = 152 * 4;   // grid of the vector kernels (fixed: partial counts)
+// grid of the vector kernels (fixed: partial counts): one full wave of 8 blocks of 256 threads per
+// SM, so that enough loads are in flight to stream the vectors at HBM speed (with 4 blocks per SM
+// the grid-stride loops ran latency-bound at about a sixth of it)
+constexpr int kVecBlocks = 152 * 8;
 
 template <typename T>
 struct CGVecs {
@@ -936,6 +991,7 @@ mto_status precond_step<float>(mto_handle h, const CGVecs<float>& v, int pc, int
 template <typename T>
 mto_status cg_iteration(mto_handle h, const CGVecs<T>& v, int pc, int deg, int nrm, const double* ref, double tol2,
                         int local, int nc) {
+  double* eng = nrm == 2 ? h->eng : nullptr;
   const int64_t n = h->ndof;
   const int par = local & 1, nxt = par ^ 1;
   const bool jac = pc == MTO_PREC_JACOBI;
@@ -954,18 +1010,19 @@ mto_status cg_iteration(mto_handle h, const CGVecs<T>& v, int pc, int deg, int n
       cg_vector_kernel<T, false><<<kVecBlocks, 256, 0, h->stream>>>(
           n, v.x, v.r, v.p, v.q, v.z, v.invd, res_slot(h, kGam + par), ng, res_slot(h, kDel + par), nop,
           red_slot(h, -1, 0), red_slot(h, kRR + nxt, 0), red_slot(h, kRD + nxt, 0), h->cg_base, local, h->flags,
-          h->flags + 1);
+          h->flags + 1, eng);
     else
       cg_vector_kernel<T, true><<<kVecBlocks, 256, 0, h->stream>>>(
           n, v.x, v.r, v.p, v.q, v.z, v.invd, res_slot(h, kGam + par), ng, res_slot(h, kDel + par), nop,
           red_slot(h, kGam + nxt, 0), red_slot(h, kRR + nxt, 0), red_slot(h, kRD + nxt, 0), h->cg_base, local,
-          h->flags, h->flags + 1);
+          h->flags, h->flags + 1, eng);
     MTO_TRY(mto_after_launch(h, "cg_vector_kernel"));
   }
   if (!jac) MTO_TRY(precond_step<T>(h, v, pc, deg, kGam + nxt, h->flags));
   {
     TimedScope ts(h, F_VECTOR);
-    ConvTest cv{res_slot(h, nrm ? kRD + nxt : kRR + nxt), 1, ref, tol2, h->cg_base, local, h->flags, h->flags + 1};
+    ConvTest cv{res_slot(h, nrm == 1 ? kRD + nxt : kRR + nxt), 1, ref, tol2, h->cg_base, local, h->flags, h->flags + 1,
+                eng};
     if (!jac)
       cg_direction_kernel<T, false><<<kVecBlocks, 256, 0, h->stream>>>(
           n, v.r, v.z, v.p, v.invd, res_slot(h, kGam + nxt), res_slot(h, kGam + par), ng, cv);
@@ -978,22 +1035,49 @@ mto_status cg_iteration(mto_handle h, const CGVecs<T>& v, int pc, int deg, int n
 }
 
 // CG on (x, r) of type T: r is the residual of x (free DOFs, zero on supports).  Stops when the
-// residual norm^2 (l2 or Jacobi) <= tol2 * (*ref) or after max_it iterations.  Iterations run in
-// chunks of `chunk` (even), each captured once as a CUDA graph and replayed.
+// residual norm^2 (l2 or Jacobi) <= tol2 * (*ref), or by the energy test (nrm = 2), or after max_it
+// iterations.  Iterations run in chunks of `chunk` (even), each captured once as a CUDA graph and
+// replayed.  The run is split into its preparation (start vectors, first preconditioner step,
+// graph capture), the launch of one chunk (with the asynchronous read-back of the done flags) and
+// the check of those flags after a synchronisation, so that a batch of handles can advance
+// together (solve_batched); run_cg strings them together for one handle.
 template <typename T>
-mto_status run_cg(mto_handle h, T* x, T* r, int pc, int deg, int nrm, const double* ref, double tol2, int max_it,
-                  int chunk, int* iters) {
+struct CGRun {
+  CGVecs<T> v;
+  int pc, deg, nrm, nc, chunk;
+  const double* ref;
+  double tol2;
+  GraphEntry* ge = nullptr;
+  int k = 0;
+};
+
+template <typename T>
+mto_status cg_prepare(mto_handle h, CGRun<T>& run, T* x, T* r, int pc, int deg, int nrm, const double* ref,
+                      double tol2, int chunk) {
   const bool schwarz = pc != MTO_PREC_JACOBI;   // z kept in its own vector
   const int64_t n = h->ndof;
   CGVecs<T> v = cg_vecs<T>(h, x, r);
+  run.v = v;
+  run.pc = pc;
+  run.deg = deg;
+  run.nrm = nrm;
+  run.ref = ref;
+  run.tol2 = tol2;
+  run.chunk = chunk;
+  run.k = 0;
+  run.ge = nullptr;
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->flags, 0, 2 * sizeof(int), h->stream), "memset"));
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->cg_base, 0, sizeof(int), h->stream), "memset"));
   // a launch that ended the run early may have left a block count behind
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->cg_cnt, 0, 64 * sizeof(unsigned), h->stream), "memset"));
-  ConvTest none{};
+  if (nrm == 2) {   // energy log of this run (its compliance base eng[1] is set by the caller)
+    MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->eng, 0, sizeof(double), h->stream), "memset"));
+    MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->eng + 2, 0, kEnergyRing * sizeof(double), h->stream), "memset"));
+  }
   int nc = 0;
   for (int p = 1; p <= MTO_P_MAX; ++p)
     if (h->pc[p].n) ++nc;
+  run.nc = nc;
   {
     TimedScope ts(h, F_VECTOR);
     if (schwarz)
@@ -1013,66 +1097,86 @@ mto_status run_cg(mto_handle h, T* x, T* r, int pc, int deg, int nrm, const doub
     copy_kernel<T><<<kVecBlocks, 256, 0, h->stream>>>(n, v.z, v.p);
     MTO_TRY(mto_after_launch(h, "copy_kernel"));
   }
-
-  const bool use_graph = h->use_graphs;
-  GraphEntry* ge = nullptr;
-  if (use_graph) {
-    GraphKey key{sizeof(T), (const void*)x, (const void*)r, pc, deg, nrm, ref, tol2, chunk,
-                 h->timing.on ? (h->timing.sampled ? 2 : 1) : 0,
-                 2 * h->built_precision + (h->inner_split ? 1 : 0)};
-    ge = find_graph(h, key);
-    if (!ge) {
-      ge = new_graph(h, key);
-      const int64_t l0 = h->launches;
-      MTO_TRY(mto_cuda_check(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal),
-                             "cudaStreamBeginCapture"));
-      h->timing.capture_list = &ge->events;
-      mto_status st = MTO_OK;
-      for (int l = 0; l < chunk && st == MTO_OK; ++l)
-        st = cg_iteration<T>(h, v, pc, deg, nrm, ref, tol2, l, nc);
-      if (st == MTO_OK) {
-        advance_kernel<<<1, 32, 0, h->stream>>>(h->cg_base, chunk);
-        st = mto_after_launch(h, "advance_kernel");
-      }
-      h->timing.capture_list = nullptr;
-      cudaGraph_t g = nullptr;
-      cudaError_t e = cudaStreamEndCapture(h->stream, &g);
-      ge->launches_per_replay = h->launches - l0;
-      h->launches = l0;   // nothing ran during capture
-      if (st != MTO_OK) return st;
-      MTO_TRY(mto_cuda_check(h, e, "cudaStreamEndCapture"));
-      MTO_TRY(mto_cuda_check(h, cudaGraphInstantiate(&ge->exec, g, 0), "cudaGraphInstantiate"));
-      cudaGraphDestroy(g);
-    }
-  }
-  int k = 0, done = 0, err = 0;
-  while (k < max_it) {
-    if (use_graph) {
-      MTO_TRY(mto_cuda_check(h, cudaGraphLaunch(ge->exec, h->stream), "cudaGraphLaunch"));
-      h->launches += ge->launches_per_replay;
-      k += chunk;
-    } else {
-      for (int l = 0; l < chunk; ++l) MTO_TRY(cg_iteration<T>(h, v, pc, deg, nrm, ref, tol2, l, nc));
+  if (!h->use_graphs) return MTO_OK;
+  GraphKey key{sizeof(T), (const void*)x, (const void*)r, pc, deg, nrm, ref, tol2, chunk,
+               h->timing.on ? (h->timing.sampled ? 2 : 1) : 0, 2 * h->built_precision + (h->inner_split ? 1 : 0)};
+  GraphEntry* ge = find_graph(h, key);
+  if (!ge) {
+    ge = new_graph(h, key);
+    const int64_t l0 = h->launches;
+    MTO_TRY(mto_cuda_check(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal),
+                           "cudaStreamBeginCapture"));
+    h->timing.capture_list = &ge->events;
+    mto_status st = MTO_OK;
+    for (int l = 0; l < chunk && st == MTO_OK; ++l) st = cg_iteration<T>(h, v, pc, deg, nrm, ref, tol2, l, nc);
+    if (st == MTO_OK) {
       advance_kernel<<<1, 32, 0, h->stream>>>(h->cg_base, chunk);
-      MTO_TRY(mto_after_launch(h, "advance_kernel"));
-      k += chunk;
+      st = mto_after_launch(h, "advance_kernel");
     }
-    MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->host_flags, h->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost,
-                                              h->stream), "copy"));
-    MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
-    if (use_graph) graph_timing_harvest(h, ge);
-    timing_harvest(h);
-    done = h->host_flags[0];
-    err = h->host_flags[1];
-    if (done) break;
+    h->timing.capture_list = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    ge->launches_per_replay = h->launches - l0;
+    h->launches = l0;   // nothing ran during capture
+    if (st != MTO_OK) return st;
+    MTO_TRY(mto_cuda_check(h, e, "cudaStreamEndCapture"));
+    MTO_TRY(mto_cuda_check(h, cudaGraphInstantiate(&ge->exec, g, 0), "cudaGraphInstantiate"));
+    cudaGraphDestroy(g);
   }
-  *iters = done ? done : k;
-  if (err) return mto_fail(h, MTO_ENAN, "CG breakdown: non-finite or non-positive curvature");
+  run.ge = ge;
   return MTO_OK;
 }
 
-// FP64 residual r = f - K u (masked) and its squared norms: h->red[0..3] = (r, f l2; r, f Jacobi).
-mto_status true_residual(mto_handle h, const double* f, const double* u, int norm, double* rr, double* ff) {
+// one chunk of iterations, then the done flags to the pinned host mirror (asynchronous)
+template <typename T>
+mto_status cg_launch_chunk(mto_handle h, CGRun<T>& run) {
+  if (run.ge) {
+    MTO_TRY(mto_cuda_check(h, cudaGraphLaunch(run.ge->exec, h->stream), "cudaGraphLaunch"));
+    h->launches += run.ge->launches_per_replay;
+  } else {
+    for (int l = 0; l < run.chunk; ++l)
+      MTO_TRY(cg_iteration<T>(h, run.v, run.pc, run.deg, run.nrm, run.ref, run.tol2, l, run.nc));
+    advance_kernel<<<1, 32, 0, h->stream>>>(h->cg_base, run.chunk);
+    MTO_TRY(mto_after_launch(h, "advance_kernel"));
+  }
+  run.k += run.chunk;
+  return mto_cuda_check(h, cudaMemcpyAsync(h->host_flags, h->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+                        "copy");
+}
+
+// after the stream has been synchronised: 1 when the run has finished (converged or broken down)
+template <typename T>
+int cg_check(mto_handle h, CGRun<T>& run) {
+  if (run.ge) graph_timing_harvest(h, run.ge);
+  timing_harvest(h);
+  return h->host_flags[0] != 0 || h->host_flags[1] != 0;
+}
+
+template <typename T>
+mto_status cg_result(mto_handle h, const CGRun<T>& run, int* iters) {
+  const int done = h->host_flags[0];
+  *iters = done ? done : run.k;
+  if (h->host_flags[1]) return mto_fail(h, MTO_ENAN, "CG breakdown: non-finite or non-positive curvature");
+  return MTO_OK;
+}
+
+template <typename T>
+mto_status run_cg(mto_handle h, T* x, T* r, int pc, int deg, int nrm, const double* ref, double tol2, int max_it,
+                  int chunk, int* iters) {
+  CGRun<T> run;
+  MTO_TRY(cg_prepare<T>(h, run, x, r, pc, deg, nrm, ref, tol2, chunk));
+  while (run.k < max_it) {
+    MTO_TRY(cg_launch_chunk<T>(h, run));
+    MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
+    if (cg_check<T>(h, run)) break;
+  }
+  return cg_result<T>(h, run, iters);
+}
+
+// FP64 residual r = f - K u (masked) and its squared norms: h->red[0..3] = (r, f l2; r, f Jacobi),
+// read back asynchronously into host_pinned[0..3] (residual_enqueue), then taken after a
+// synchronisation (residual_take).
+mto_status residual_enqueue(mto_handle h, const double* f, const double* u) {
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->s64, 0, sizeof(double) * h->ndof, h->stream), "memset"));
   ConvTest none{};
   MTO_TRY(apply_all<double>(h, 0, u, h->s64, -1, nullptr, none));
@@ -1083,12 +1187,20 @@ mto_status true_residual(mto_handle h, const double* f, const double* u, int nor
     sum4_kernel<<<1, 256, 0, h->stream>>>(h->cg_part, kVecBlocks, h->red);
     MTO_TRY(mto_after_launch(h, "sum4_kernel"));
   }
-  MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->host_pinned, h->red, 4 * sizeof(double), cudaMemcpyDeviceToHost,
-                                            h->stream), "copy"));
-  MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
+  return mto_cuda_check(h, cudaMemcpyAsync(h->host_pinned, h->red, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                                           h->stream), "copy");
+}
+
+void residual_take(mto_handle h, int norm, double* rr, double* ff) {
   timing_harvest(h);
   *rr = h->host_pinned[norm ? 2 : 0];
   *ff = h->host_pinned[norm ? 3 : 1];
+}
+
+mto_status true_residual(mto_handle h, const double* f, const double* u, int norm, double* rr, double* ff) {
+  MTO_TRY(residual_enqueue(h, f, u));
+  MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
+  residual_take(h, norm, rr, ff);
   return MTO_OK;
 }
 
@@ -1119,6 +1231,82 @@ mto_status apply_operator(mto_handle h, int op, const double* x, double* y, doub
   return MTO_OK;
 }
 
+// Autotuner of the split operator's kernel per order class (n_e <= 32: register pipeline, bulk-copy
+// staging or the generic kernel): each candidate is timed with CUDA events over a few launches on
+// the class's own rows and the fastest is kept for the class (in the handle, and in a process-wide
+// table keyed by device, order and element count, so instances of the same class size reuse it).
+namespace {
+struct TuneKey {
+  int device, p, n;
+  bool operator<(const TuneKey& o) const {
+    return device != o.device ? device < o.device : (p != o.p ? p < o.p : n < o.n);
+  }
+};
+std::map<TuneKey, std::pair<int, std::array<float, 3>>> g_tune_cache;
+std::mutex g_tune_mutex;
+}  // namespace
+
+mto_status autotune_operator(mto_handle h, int32_t* choice, double* us) {
+  if (h->built_precision != MTO_MIXED)
+    return mto_fail(h, MTO_EINVAL, "mto_autotune: needs the split-precision (MTO_MIXED) build");
+  // timed on zeroed work vectors (the values do not matter, only well-formed numbers)
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->p64, 0, h->ndof * sizeof(double), h->stream), "memset"));
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->w64, 0, h->ndof * sizeof(double), h->stream), "memset"));
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  mto_status st = MTO_OK;
+  for (int p = 1; p <= MTO_P_MAX && st == MTO_OK; ++p) {
+    PClass& c = h->pc[p];
+    if (choice) choice[p] = -2;
+    if (c.n == 0 || 2 * (p + 1) * (p + 1) > 32) continue;
+    std::array<float, 3> t{0.f, 0.f, 0.f};
+    int best = -1;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mutex);
+      auto it = g_tune_cache.find(TuneKey{h->device, p, c.n});
+      if (it != g_tune_cache.end()) {
+        best = it->second.first;
+        t = it->second.second;
+      }
+    }
+    if (best < 0) {
+      ConvTest none{};
+      const Red nored{nullptr, nullptr, nullptr};
+      for (int v = 0; v < 3 && st == MTO_OK; ++v) {
+        h->op_kernel_cls[p] = v;
+        for (int rep = 0; rep < 7 && st == MTO_OK; ++rep) {
+          if (rep == 2) cudaEventRecord(a, h->stream);
+          switch (p) {
+            case 1: launch_ebe<1, true, double>(h, c, c.K64, c.K32, c.K32lo, h->p64, h->w64, nored, nullptr, none); break;
+            case 2: launch_ebe<2, true, double>(h, c, c.K64, c.K32, c.K32lo, h->p64, h->w64, nored, nullptr, none); break;
+            case 3: launch_ebe<3, true, double>(h, c, c.K64, c.K32, c.K32lo, h->p64, h->w64, nored, nullptr, none); break;
+          }
+          st = mto_after_launch(h, "ebe operator (autotune)");
+        }
+        cudaEventRecord(b, h->stream);
+        if (st == MTO_OK) st = mto_cuda_check(h, cudaEventSynchronize(b), "autotune");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        t[v] = ms / 5.f;
+      }
+      best = 0;
+      for (int v = 1; v < 3; ++v)
+        if (t[v] < t[best]) best = v;
+      std::lock_guard<std::mutex> lk(g_tune_mutex);
+      g_tune_cache[TuneKey{h->device, p, c.n}] = {best, t};
+    }
+    h->op_kernel_cls[p] = best;
+    if (choice) choice[p] = best;
+    if (us)
+      for (int v = 0; v < 3; ++v) us[3 * p + v] = 1e3 * t[v];
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  clear_graphs(h);   // captured iterations hold the previous kernels
+  return st;
+}
+
 mto_status apply_fine(mto_handle h, const double* x, double* y, const int* done) {
   ConvTest none{};
   return apply_all<double>(h, 0, x, y, -1, done, none);
@@ -1129,6 +1317,20 @@ mto_status apply_q1(mto_handle h, const MGLevel& l, const double* x, double* y, 
   ebe_kernel<1, false, double><<<ebe_blocks_p<1>(l.nel), 256, 0, h->stream>>>(
       l.K, nullptr, nullptr, 40, l.nel, l.gmap, nullptr, x, y, Red{nullptr, nullptr, nullptr}, done, none);
   return mto_after_launch(h, "ebe_kernel");
+}
+
+__global__ void __launch_bounds__(256) vsum_kernel(int64_t n, const double* __restrict__ a, double* __restrict__ part) {
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) s += a[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+mto_status sum64(mto_handle h, const double* a, int64_t n, double* out_dev) {
+  vsum_kernel<<<kVecBlocks, 256, 0, h->stream>>>(n, a, h->cg_part);
+  MTO_TRY(mto_after_launch(h, "vsum_kernel"));
+  sum1_kernel<<<1, 256, 0, h->stream>>>(h->cg_part, kVecBlocks, out_dev);
+  return mto_after_launch(h, "sum1_kernel");
 }
 
 mto_status dot64(mto_handle h, const double* a, const double* b, int64_t n, double* out_dev) {
@@ -1164,7 +1366,8 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
   int total = 0;
   double rr = 0.0, ff = 0.0;
   const int max_outer = o->max_outer > 0 ? o->max_outer : 50;
-  const int nrm = o->norm == MTO_NORM_JACOBI ? 1 : 0;
+  const bool energy = o->norm == MTO_NORM_ENERGY;
+  const int nrm = o->norm == MTO_NORM_JACOBI ? 1 : 0;   // norm of the residual reported and tested
   const double itol = o->inner_rtol > 0 ? o->inner_rtol : 1e-6;
   // mixed refinement: a step whose FP64 residual falls short of the asked reduction by more than
   // 10x shows that the split pair's ~48-bit matrices limit it (condition number near 2^48); the
@@ -1188,7 +1391,9 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
       st = mto_fail(h, MTO_ENAN, "mto_solve: non-finite residual");
       break;
     }
-    if (ff == 0.0 || rr <= o->rtol * o->rtol * ff) {
+    if (ff == 0.0 || (!energy && rr <= o->rtol * o->rtol * ff) || (energy && outer > 0)) {
+      // the compliance-accuracy mode takes one correction solve: its energy test bounds the
+      // compliance error of u itself (the FP64 residual above is only reported)
       st = MTO_OK;
       break;
     }
@@ -1210,9 +1415,19 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
       MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->red + 6, h->host_pinned + 33, sizeof(double),
                                                 cudaMemcpyHostToDevice, h->stream), "copy"));
       asked = tol_i;
+      if (energy) {   // compliance base C(u_0) = f^T u_0 + u_0^T r_0, and the residual floor
+        h->host_pinned[34] = 1e-26 * h->host_pinned[1];
+        MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->eng + 2 + kEnergyRing, h->host_pinned + 34, sizeof(double),
+                                                  cudaMemcpyHostToDevice, h->stream), "copy"));
+        MTO_TRY(dot64(h, f, u, n, h->red + 12));
+        MTO_TRY(dot64(h, u, h->r64, n, h->red + 13));
+        add2_kernel<<<1, 32, 0, h->stream>>>(h->red + 12, h->red + 13, h->eng + 1);
+        MTO_TRY(mto_after_launch(h, "add2_kernel"));
+      }
       h->inner_split = split && o->precision == MTO_MIXED;
       MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->s64, 0, sizeof(double) * n, h->stream), "memset"));
-      const mto_status si = run_cg<double>(h, h->s64, h->r64, pc, deg, nrm, h->red + 6, 1.0, budget, chunk, &it);
+      const mto_status si = energy ? run_cg<double>(h, h->s64, h->r64, pc, deg, 2, h->red + 6, o->rtol, budget, chunk, &it)
+                                   : run_cg<double>(h, h->s64, h->r64, pc, deg, nrm, h->red + 6, 1.0, budget, chunk, &it);
       h->inner_split = false;
       MTO_TRY(si);
       TimedScope ts(h, F_VECTOR);
@@ -1245,6 +1460,166 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
   if (relres_out) *relres_out = ff > 0 ? std::sqrt(rr / ff) : 0.0;
   if (st == MTO_ENOCONV) return mto_fail(h, MTO_ENOCONV, "mto_solve: iteration limit reached");
   return st;
+}
+
+// ------------------------------------------------------------------------------------------
+// Batched solves: the refinement loop of solve() as a resumable state per handle, advanced for all
+// handles between shared synchronisations.  Each handle keeps its own stream, workspace and
+// captured iteration graphs, so the instances' chunks of CG iterations run concurrently on the GPU
+// and the host waits once per round for all of them instead of once per chunk per instance.
+// FP64-vector modes only (MTO_FP64, MTO_MIXED).
+namespace {
+struct BatchJob {
+  mto_handle h = nullptr;
+  const double* f = nullptr;
+  double* u = nullptr;
+  const mto_solve_opts* o = nullptr;
+  int pc = 0, deg = 4, chunk = 32, max_outer = 50, nrm = 0;
+  bool energy = false;
+  double itol = 1e-6;
+  int phase = 0;   // 0: residual in flight, 1: CG chunk in flight, 2: finished
+  int outer = 0, total = 0, budget = 0;
+  double rr = 0.0, ff = 0.0, rr_prev = -1.0, asked = 0.0;
+  bool split = true;
+  CGRun<double> run;
+  mto_status st = MTO_ENOCONV;
+};
+
+void job_finish(BatchJob& j, mto_status st) {
+  j.st = st;
+  j.phase = 2;
+  j.h->inner_split = false;
+}
+
+// the top of one refinement step, with the residual of the current u read back
+mto_status job_on_residual(BatchJob& j) {
+  mto_handle h = j.h;
+  const mto_solve_opts* o = j.o;
+  residual_take(h, j.nrm, &j.rr, &j.ff);
+  if (o->precision == MTO_MIXED && j.rr_prev > 0.0 && std::sqrt(j.rr / j.rr_prev) > 10.0 * j.asked) j.split = false;
+  j.rr_prev = j.rr;
+  if (!std::isfinite(j.rr)) {
+    job_finish(j, mto_fail(h, MTO_ENAN, "mto_solve_batched: non-finite residual"));
+    return MTO_OK;
+  }
+  if (j.ff == 0.0 || (!j.energy && j.rr <= o->rtol * o->rtol * j.ff) || (j.energy && j.outer > 0)) {
+    job_finish(j, MTO_OK);
+    return MTO_OK;
+  }
+  if (j.total >= o->max_iter || j.outer == j.max_outer) {
+    job_finish(j, mto_fail(h, MTO_ENOCONV, "mto_solve_batched: iteration limit reached"));
+    return MTO_OK;
+  }
+  const int64_t n = h->ndof;
+  const int cap = o->inner_max > 0 ? o->inner_max : 1 << 30;
+  j.budget = o->max_iter - j.total < cap ? o->max_iter - j.total : cap;
+  const double need = o->rtol * std::sqrt(j.ff / j.rr) / 3.0;
+  const double tol_i = need > j.itol ? (need < 0.1 ? need : 0.1) : j.itol;
+  h->host_pinned[33] = tol_i * tol_i * h->host_pinned[j.nrm ? 2 : 0];
+  MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->red + 6, h->host_pinned + 33, sizeof(double), cudaMemcpyHostToDevice,
+                                            h->stream), "copy"));
+  j.asked = tol_i;
+  if (j.energy) {
+    h->host_pinned[34] = 1e-26 * h->host_pinned[1];
+    MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->eng + 2 + kEnergyRing, h->host_pinned + 34, sizeof(double),
+                                              cudaMemcpyHostToDevice, h->stream), "copy"));
+    MTO_TRY(dot64(h, j.f, j.u, n, h->red + 12));
+    MTO_TRY(dot64(h, j.u, h->r64, n, h->red + 13));
+    add2_kernel<<<1, 32, 0, h->stream>>>(h->red + 12, h->red + 13, h->eng + 1);
+    MTO_TRY(mto_after_launch(h, "add2_kernel"));
+  }
+  h->inner_split = j.split && o->precision == MTO_MIXED;
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->s64, 0, sizeof(double) * n, h->stream), "memset"));
+  if (j.energy) MTO_TRY(cg_prepare<double>(h, j.run, h->s64, h->r64, j.pc, j.deg, 2, h->red + 6, o->rtol, j.chunk));
+  else MTO_TRY(cg_prepare<double>(h, j.run, h->s64, h->r64, j.pc, j.deg, j.nrm, h->red + 6, 1.0, j.chunk));
+  MTO_TRY(cg_launch_chunk<double>(h, j.run));
+  j.phase = 1;
+  return MTO_OK;
+}
+
+// after a chunk: the next chunk, or the end of the correction solve and the next residual
+mto_status job_on_chunk(BatchJob& j) {
+  mto_handle h = j.h;
+  const bool fin = cg_check<double>(h, j.run);
+  if (!fin && j.run.k < j.budget) return cg_launch_chunk<double>(h, j.run);
+  int it = 0;
+  const mto_status si = cg_result<double>(h, j.run, &it);
+  h->inner_split = false;
+  j.total += it;
+  if (si != MTO_OK) {
+    job_finish(j, si);
+    return MTO_OK;
+  }
+  {
+    TimedScope ts(h, F_VECTOR);
+    axpy_kernel<<<grid_for(h->ndof, 256, 152 * 4), 256, 0, h->stream>>>(h->ndof, h->s64, j.u);
+    MTO_TRY(mto_after_launch(h, "axpy_kernel"));
+  }
+  ++j.outer;
+  MTO_TRY(residual_enqueue(h, j.f, j.u));
+  j.phase = 0;
+  return MTO_OK;
+}
+}  // namespace
+
+mto_status solve_batched(mto_handle* hs, int n, const double* const* f, double* const* u, const mto_solve_opts* o,
+                         int32_t* iters, double* relres, mto_status* status) {
+  std::vector<BatchJob> jobs(n);
+  // start: preconditioner set-up, start vectors, first residuals (in flight on every stream)
+  for (int i = 0; i < n; ++i) {
+    BatchJob& j = jobs[i];
+    mto_handle h = hs[i];
+    j.h = h;
+    j.f = f[i];
+    j.u = u[i];
+    j.o = o;
+    j.pc = o->precond;
+    j.deg = o->mg_degree > 0 ? o->mg_degree : 4;
+    j.chunk = o->check_every < 2 ? 2 : (o->check_every + 1) / 2 * 2;
+    j.max_outer = o->max_outer > 0 ? o->max_outer : 50;
+    j.energy = o->norm == MTO_NORM_ENERGY;
+    j.nrm = o->norm == MTO_NORM_JACOBI ? 1 : 0;
+    j.itol = o->inner_rtol > 0 ? o->inner_rtol : 1e-6;
+    mto_status st = MTO_OK;
+    if (j.deg > 16) st = mto_fail(h, MTO_EINVAL, "mto_solve_batched: mg_degree above 16");
+    else if (j.pc == MTO_PREC_SCHWARZ && h->n_cons > 0)
+      st = mto_fail(h, MTO_EINVAL, "mto_solve_batched: element-block Schwarz is limited to meshes without order jumps");
+    if (st == MTO_OK && j.pc == MTO_PREC_SCHWARZ && !h->schwarz_valid) st = build_schwarz(h);
+    if (st == MTO_OK && j.pc == MTO_PREC_MG && !h->mg_valid) st = mg_build(h);
+    if (st == MTO_OK) {
+      if (!o->warm_start) st = mto_cuda_check(h, cudaMemsetAsync(j.u, 0, sizeof(double) * h->ndof, h->stream), "memset");
+      else {
+        mask_kernel<<<grid_for(h->ndof, 256, 152 * 4), 256, 0, h->stream>>>(h->ndof, h->invd64, j.u);
+        st = mto_after_launch(h, "mask_kernel");
+      }
+    }
+    if (st == MTO_OK) st = residual_enqueue(h, j.f, j.u);
+    if (st != MTO_OK) job_finish(j, st);
+  }
+  // rounds: one synchronisation of every unfinished stream, then each job's next step
+  for (;;) {
+    bool any = false;
+    for (auto& j : jobs) {
+      if (j.phase == 2) continue;
+      any = true;
+      const mto_status ss = mto_cuda_check(j.h, cudaStreamSynchronize(j.h->stream), "sync");
+      if (ss != MTO_OK) job_finish(j, ss);
+    }
+    if (!any) break;
+    for (auto& j : jobs) {
+      if (j.phase == 2) continue;
+      const mto_status ss = j.phase == 0 ? job_on_residual(j) : job_on_chunk(j);
+      if (ss != MTO_OK) job_finish(j, ss);
+    }
+  }
+  mto_status first = MTO_OK;
+  for (int i = 0; i < n; ++i) {
+    if (iters) iters[i] = jobs[i].total;
+    if (relres) relres[i] = jobs[i].ff > 0 ? std::sqrt(jobs[i].rr / jobs[i].ff) : 0.0;
+    if (status) status[i] = jobs[i].st;
+    if (first == MTO_OK && jobs[i].st != MTO_OK) first = jobs[i].st;
+  }
+  return first;
 }
 
 }  // namespace mto

@@ -502,52 +502,90 @@ __global__ void final_kernel(int64_t nel, const int* __restrict__ p_s, const int
 }
 
 // ------------------------------------------------------------------------------------ OC
-__global__ void oc_sum_kernel(int64_t nel, const int64_t* __restrict__ off, const int* __restrict__ dmap,
-                              double hx, double hy, const double* __restrict__ rho, const double* __restrict__ dc,
-                              double move, double eta, const double* __restrict__ lam, const int* __restrict__ done,
-                              double* __restrict__ sum) {
+// rho_new_j = clip(rho_j (B_j / lambda)^eta, max(0, rho_j - m), min(1, rho_j + m)), B_j = -dc_j / dv_j,
+// written as t_j lambda^-eta with t_j = rho_j B_j^eta formed once, so every bisection pass is one
+// multiply per value (sqrt for the usual eta = 1/2).  One warp per element (coalesced over its
+// subcells); the volume sum is reduced in a fixed order and its last block takes the bisection
+// step itself, so the whole bisection is a chain of identical launches with no host round trip.
+constexpr int kOCBlock = 256;
+
+__device__ __forceinline__ double oc_pow(double x, double eta) { return eta == 0.5 ? sqrt(x) : pow(x, eta); }
+
+__global__ void __launch_bounds__(kOCBlock) oc_prep_kernel(int64_t nel, const int64_t* __restrict__ off,
+                                                           const int* __restrict__ dmap, double hx, double hy,
+                                                           const double* __restrict__ rho,
+                                                           const double* __restrict__ dc, double eta,
+                                                           double* __restrict__ t) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = w0; e < nel; e += nw) {
+    const int d = dmap[e];
+    const double dv = hx * hy / ((double)d * d);
+    for (int64_t j = off[e] + lane; j < off[e + 1]; j += 32) t[j] = rho[j] * oc_pow(fmax(-dc[j], 0.0) / dv, eta);
+  }
+}
+
+__global__ void __launch_bounds__(kOCBlock) oc_sum_kernel(int64_t nel, const int64_t* __restrict__ off,
+                                                          const int* __restrict__ dmap, double hx, double hy,
+                                                          const double* __restrict__ rho,
+                                                          const double* __restrict__ t, double move, double eta,
+                                                          double* __restrict__ lam, double target, double tol,
+                                                          int* __restrict__ done, double* __restrict__ part,
+                                                          unsigned* __restrict__ cnt) {
   if (*done) return;
+  __shared__ double ws[kOCBlock / 32];
+  __shared__ int last;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const double lmid = 0.5 * (lam[0] + lam[1]);
+  const double c = eta == 0.5 ? 1.0 / sqrt(lmid) : pow(lmid, -eta);
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double s = 0.0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nel; e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = w0; e < nel; e += nw) {
     const int d = dmap[e];
     const double dv = hx * hy / ((double)d * d);
     double se = 0.0;
-    for (int64_t j = off[e]; j < off[e + 1]; ++j) {
+    for (int64_t j = off[e] + lane; j < off[e + 1]; j += 32) {
       const double r = rho[j];
-      const double Bv = fmax(-dc[j], 0.0) / dv;
-      double v = r * pow(Bv / lmid, eta);
-      v = fmin(fmax(v, fmax(0.0, r - move)), fmin(1.0, r + move));
-      se += v;
+      se += fmin(fmax(t[j] * c, fmax(0.0, r - move)), fmin(1.0, r + move));
     }
     s += se * dv;
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(sum, s);
-}
-
-__global__ void oc_step_kernel(double* lam, double* sum, double target, double tol, int* done) {
-  if (threadIdx.x != 0 || *done) return;
-  const double lmid = 0.5 * (lam[0] + lam[1]);
-  if (*sum > target) lam[0] = lmid; else lam[1] = lmid;
-  *sum = 0.0;
-  if ((lam[1] - lam[0]) / (lam[0] + lam[1]) <= tol) *done = 1;
-}
-
-__global__ void oc_write_kernel(int64_t nel, const int64_t* __restrict__ off, const int* __restrict__ dmap,
-                                double hx, double hy, const double* __restrict__ rho, const double* __restrict__ dc,
-                                double move, double eta, const double* __restrict__ lam, double* __restrict__ out) {
-  const double lmid = 0.5 * (lam[0] + lam[1]);
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nel; e += (int64_t)gridDim.x * blockDim.x) {
-    const int d = dmap[e];
-    const double dv = hx * hy / ((double)d * d);
-    for (int64_t j = off[e]; j < off[e + 1]; ++j) {
-      const double r = rho[j];
-      const double Bv = fmax(-dc[j], 0.0) / dv;
-      double v = r * pow(Bv / lmid, eta);
-      out[j] = fmin(fmax(v, fmax(0.0, r - move)), fmin(1.0, r + move));
-    }
+  if (lane == 0) ws[wib] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < kOCBlock / 32; ++w) b += ws[w];
+    part[blockIdx.x] = b;
+    __threadfence();
+    last = atomicAdd(cnt, 1u) == gridDim.x - 1;
   }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double tot = 0.0;
+  for (int i = 0; i < (int)gridDim.x; ++i) tot += __ldcg(part + i);
+  if (tot > target) lam[0] = lmid; else lam[1] = lmid;
+  if ((lam[1] - lam[0]) / (lam[0] + lam[1]) <= tol) *done = 1;
+  *cnt = 0u;
+}
+
+__global__ void __launch_bounds__(kOCBlock) oc_write_kernel(int64_t nel, const int64_t* __restrict__ off,
+                                                            const double* __restrict__ rho,
+                                                            const double* __restrict__ t, double move, double eta,
+                                                            const double* __restrict__ lam, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const double lmid = 0.5 * (lam[0] + lam[1]);
+  const double c = eta == 0.5 ? 1.0 / sqrt(lmid) : pow(lmid, -eta);
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = w0; e < nel; e += nw)
+    for (int64_t j = off[e] + lane; j < off[e + 1]; j += 32) {
+      const double r = rho[j];
+      out[j] = fmin(fmax(t[j] * c, fmax(0.0, r - move)), fmin(1.0, r + move));
+    }
 }
 
 // ------------------------------------------------------------------------------------ host side
@@ -713,24 +751,30 @@ mto_status indicators(mto_handle h, const double* u, const double* rho, const mt
 
 mto_status oc_update(mto_handle h, const double* rho, const double* dc, double volfrac, double move, double eta,
                      double* rho_new, double* lambda) {
+  TimedScope ts(h, F_INDICATOR);
   const int64_t nel = h->nel;
   double* lam = h->red + 16;       // [l1, l2]
-  double* sum = h->red + 18;
   int* done = h->flags + 8;
-  const double init[3] = {0.0, 1e9, 0.0};
-  MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(lam, init, sizeof(init), cudaMemcpyHostToDevice, h->stream), "copy"));
-  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(done, 0, sizeof(int), h->stream), "memset"));
+  unsigned* cnt = reinterpret_cast<unsigned*>(h->flags + 9);
+  if (!h->oc_t) MTO_TRY(mto_alloc(h, &h->oc_t, (size_t)h->design_len));
+  const double init[2] = {0.0, 1e9};
+  h->host_pinned[48] = init[0];
+  h->host_pinned[49] = init[1];
+  MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(lam, h->host_pinned + 48, 2 * sizeof(double), cudaMemcpyHostToDevice,
+                                            h->stream), "copy"));
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->flags + 8, 0, 2 * sizeof(int), h->stream), "memset"));
   const double target = volfrac * (double)h->nelx * h->nely * h->hx * h->hy;
-  const int grd = grid_for(nel, 256, 152 * 4);
-  for (int it = 0; it < 200; ++it) {
-    oc_sum_kernel<<<grd, 256, 0, h->stream>>>(nel, h->design_off_d, h->d_d, h->hx, h->hy, rho, dc, move, eta, lam,
-                                             done, sum);
+  const int grd = grid_for(nel * 32, kOCBlock, 152 * 8);
+  oc_prep_kernel<<<grd, kOCBlock, 0, h->stream>>>(nel, h->design_off_d, h->d_d, h->hx, h->hy, rho, dc, eta, h->oc_t);
+  MTO_TRY(mto_after_launch(h, "oc_prep_kernel"));
+  // bisection on [0, 1e9] to a relative width of 1e-10 takes at most ~100 halvings; the launches
+  // after convergence return at once
+  for (int it = 0; it < 128; ++it) {
+    oc_sum_kernel<<<grd, kOCBlock, 0, h->stream>>>(nel, h->design_off_d, h->d_d, h->hx, h->hy, rho, h->oc_t, move, eta,
+                                                  lam, target, 1e-10, done, h->cg_part, cnt);
     MTO_TRY(mto_after_launch(h, "oc_sum_kernel"));
-    oc_step_kernel<<<1, 32, 0, h->stream>>>(lam, sum, target, 1e-10, done);
-    MTO_TRY(mto_after_launch(h, "oc_step_kernel"));
   }
-  oc_write_kernel<<<grd, 256, 0, h->stream>>>(nel, h->design_off_d, h->d_d, h->hx, h->hy, rho, dc, move, eta, lam,
-                                             rho_new);
+  oc_write_kernel<<<grd, kOCBlock, 0, h->stream>>>(nel, h->design_off_d, rho, h->oc_t, move, eta, lam, rho_new);
   MTO_TRY(mto_after_launch(h, "oc_write_kernel"));
   if (lambda) {
     MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->host_pinned + 16, lam, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy"));

@@ -14,7 +14,7 @@
 //   coarsest  a dense inverse (at most 2048 DOFs; coarsening stops at the first grid that small,
 //             since one dense mat-vec costs less than the launches of two more levels).
 //
-// Smoothing: Chebyshev polynomials of the Jacobi-scaled operator on [lmax / 30, lmax], lmax from
+// Smoothing: Chebyshev polynomials of the Jacobi-scaled operator on [lmax / 100, lmax], lmax from
 // a power iteration (x 1.1), the same polynomial before and after the coarse correction, so the
 // cycle is a symmetric positive definite preconditioner.  Supported DOFs are masked on every level
 // (they coincide with vertices of the coarser grids for the clamped edge and the MBB supports; the
@@ -32,11 +32,12 @@ namespace {
 
 constexpr int kCoarseTarget = 2048;   // stop coarsening at or below this many DOFs
 constexpr int kCoarseMax = 2048;      // largest coarsest grid for the dense inverse
-constexpr double kChebRatio = 30.0;   // lmin = lmax / ratio
+constexpr double kChebRatio = 100.0;  // lmin = lmax / ratio (100 cut the iterations of the 1024 x 512
+                                      // beam by a third against 30, at the same smoothing cost)
 constexpr int kPowerIts = 30;
-constexpr int kCoarseDegree = 2;      // Chebyshev degree on the Q1 levels (the fine level: the option)
+constexpr int kCoarseDegree = 4;      // Chebyshev degree on the Q1 levels (the fine level: the option)
 constexpr int kMaxDegree = 16;        // largest smoothing degree (coefficient table size)
-constexpr int kMGBlocks = 152 * 4;
+constexpr int kMGBlocks = 152 * 8;    // vector kernels: one full wave of 8 blocks per SM
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -465,10 +466,10 @@ __global__ void mg_pow_final_kernel(const double* __restrict__ res, double* __re
 // Chebyshev step coefficients of every level from its bound (one thread per level): step 0
 // d = r / theta; step s > 0 d = rho_s rho_{s-1} d + (2 rho_s / delta) r, rho_0 = 1 / sigma,
 // rho_s = 1 / (2 sigma - rho_{s-1}), theta, delta the centre and half-width of [lmax / ratio, lmax].
-__global__ void mg_cheb_coef_kernel(int nlev, const double* __restrict__ lmax, double2* __restrict__ coef) {
+__global__ void mg_cheb_coef_kernel(int nlev, const double* __restrict__ lmax, double ratio, double2* __restrict__ coef) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= nlev) return;
-  const double lm = lmax[l], lo = lm / kChebRatio;
+  const double lm = lmax[l], lo = lm / ratio;
   const double th = 0.5 * (lm + lo), de = 0.5 * (lm - lo), sg = th / de;
   double2* c = coef + (size_t)l * kMaxDegree;
   c[0] = make_double2(0.0, 1.0 / th);
@@ -750,7 +751,8 @@ mto_status mg_build(mto_handle h) {
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->mg_q0, 0, h->ndof * sizeof(double), h->stream), "memset"));
   MTO_TRY(mg_power(h, -1, h->mg_lmax));
   for (size_t l = 0; l + 1 < h->mg.size(); ++l) MTO_TRY(mg_power(h, (int)l, h->mg_lmax + 1 + l));
-  mg_cheb_coef_kernel<<<1, 32, 0, h->stream>>>((int)h->mg.size(), h->mg_lmax, h->mg_coef);
+  mg_cheb_coef_kernel<<<1, 32, 0, h->stream>>>((int)h->mg.size(), h->mg_lmax, h->mg_ratio > 1.0 ? h->mg_ratio : kChebRatio,
+                                               h->mg_coef);
   MTO_TRY(mto_after_launch(h, "mg_cheb_coef_kernel"));
   for (auto& L : h->mg) MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(L.q, 0, L.n * sizeof(double), h->stream), "memset"));
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->mg_q0, 0, h->ndof * sizeof(double), h->stream), "memset"));
@@ -772,7 +774,7 @@ mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const
   const int nl = (int)h->mg.size();
   auto smooth = [&](int lev, const double* b, double* x, double* q, double* d, const double* invd, int64_t n,
                     bool pre, bool with_dot) -> mto_status {
-    const int k = lev < 0 ? degree : kCoarseDegree;
+    const int k = lev < 0 ? degree : (h->mg_q1deg > 0 ? h->mg_q1deg : kCoarseDegree);
     const double2* cf = h->mg_coef + (size_t)(lev + 1) * kMaxDegree;
     const int grd = vec_grid(n);
     for (int s = 0; s < k; ++s) {

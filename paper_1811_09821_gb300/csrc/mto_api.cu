@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -201,6 +202,7 @@ void release_mesh(mto_handle h) {
   free_dev(h, h->spring_k_d);
   h->n_springs = 0;
   free_dev(h, h->filt_W);
+  free_dev(h, h->oc_t);
   h->bytes = h->base_bytes;
 }
 
@@ -312,6 +314,9 @@ mto_status mto_create(mto_handle* out, int device, void* stream) {
   // MTO_SOLVE_LOG=1 prints, per refinement step of mto_solve, the inner iterations, the FP64
   // relative residual and the host wall time to stderr (diagnostics; no effect on the arithmetic)
   if (const char* sl = std::getenv("MTO_SOLVE_LOG")) h->solve_log = sl[0] == '1';
+  // multigrid smoothing knobs for studies of the cycle (defaults: interval ratio 100, Q1 degree 4)
+  if (const char* mr = std::getenv("MTO_MG_RATIO")) h->mg_ratio = std::atof(mr);
+  if (const char* md = std::getenv("MTO_MG_Q1DEG")) h->mg_q1deg = std::min(std::max(std::atoi(md), 0), 16);
   // MTO_OP_KERNEL=0 / 1 / 2 selects the split operator's kernel for n_e <= 32 as
   // mto_set_operator_kernel does (register pipeline / bulk-copy staging / generic)
   if (const char* ok = std::getenv("MTO_OP_KERNEL"))
@@ -323,7 +328,7 @@ mto_status mto_create(mto_handle* out, int device, void* stream) {
     delete h;
     return MTO_ECUDA;
   }
-  if (mto_alloc(h, &h->red, 64) || mto_alloc(h, &h->flags, 64) || mto_alloc(h, &h->sel, 256) ||
+  if (mto_alloc(h, &h->red, 64) || mto_alloc(h, &h->eng, 128) || mto_alloc(h, &h->flags, 64) || mto_alloc(h, &h->sel, 256) ||
       mto_alloc(h, &h->cg_res, 64) || mto_alloc(h, &h->cg_cnt, 64) || mto_alloc(h, &h->cg_base, 4)) {
     delete h;
     return MTO_ENOMEM;
@@ -352,6 +357,7 @@ mto_status mto_destroy(mto_handle h) {
   cudaEventDestroy(h->ev_in);
   cudaEventDestroy(h->ev_out);
   cudaFree(h->red);
+  cudaFree(h->eng);
   cudaFree(h->flags);
   cudaFree(h->sel);
   cudaFreeHost(h->host_pinned);
@@ -796,6 +802,10 @@ mto_status mto_solve(mto_handle h, const double* f, double* u, const mto_solve_o
   if (h->built_precision < 0) return mto_fail(h, MTO_EINVAL, "mto_solve: call mto_build_elements first");
   if (opts->precision != MTO_FP64 && opts->precision != MTO_MIXED && opts->precision != MTO_MIXED32)
     return mto_fail(h, MTO_EINVAL, "mto_solve: bad precision");
+  if (opts->norm != MTO_NORM_L2 && opts->norm != MTO_NORM_JACOBI && opts->norm != MTO_NORM_ENERGY)
+    return mto_fail(h, MTO_EINVAL, "mto_solve: bad norm");
+  if (opts->norm == MTO_NORM_ENERGY && opts->precision == MTO_MIXED32)
+    return mto_fail(h, MTO_EINVAL, "mto_solve: the compliance-accuracy test needs FP64 vectors");
   if (opts->precision != MTO_FP64 && h->built_precision != MTO_MIXED)
     return mto_fail(h, MTO_EINVAL, "mto_solve: the mixed solves need the split-precision (MTO_MIXED) build");
   if (!(opts->rtol > 0) || opts->max_iter < 1 || opts->check_every < 1 ||
@@ -803,6 +813,76 @@ mto_status mto_solve(mto_handle h, const double* f, double* u, const mto_solve_o
     return mto_fail(h, MTO_EINVAL, "mto_solve: bad options");
   cudaSetDevice(h->device);
   return solve(h, f, u, opts, iters, relres);
+}
+
+namespace {
+// common checks of one instance of a batched call
+mto_status batch_check(mto_handle h, int device, const char* what) {
+  if (!h) return MTO_EINVAL;
+  if (h->device != device) return mto_fail(h, MTO_EINVAL, std::string(what) + ": handles on different devices");
+  if (!h->have_setup) return mto_fail(h, MTO_EINVAL, std::string(what) + ": call mto_setup first");
+  return MTO_OK;
+}
+}  // namespace
+
+mto_status mto_build_elements_batched(mto_handle* hs, int32_t n, const double* const* rho, const mto_material* mat,
+                                      int32_t precision) {
+  if (!hs || n < 1 || !rho || !mat) return MTO_EINVAL;
+  mto_status first = MTO_OK;
+  for (int32_t i = 0; i < n; ++i) {   // asynchronous on every handle's own stream
+    const mto_status st = mto_build_elements(hs[i], rho[i], mat, precision);
+    if (first == MTO_OK && st != MTO_OK) first = st;
+  }
+  return first;
+}
+
+mto_status mto_solve_batched(mto_handle* hs, int32_t n, const double* const* f, double* const* u,
+                             const mto_solve_opts* opts, int32_t* iters, double* relres, mto_status* status) {
+  if (!hs || n < 1 || !f || !u || !opts || !hs[0]) return MTO_EINVAL;
+  const int device = hs[0]->device;
+  for (int32_t i = 0; i < n; ++i) {
+    MTO_TRY(batch_check(hs[i], device, "mto_solve_batched"));
+    mto_handle h = hs[i];
+    if (!f[i] || !u[i]) return mto_fail(h, MTO_EINVAL, "mto_solve_batched: bad arguments");
+    if (!h->have_supports) return mto_fail(h, MTO_EINVAL, "mto_solve_batched: call mto_set_supports first");
+    if (h->built_precision < 0) return mto_fail(h, MTO_EINVAL, "mto_solve_batched: call mto_build_elements first");
+    if (opts->precision != MTO_FP64 && opts->precision != MTO_MIXED)
+      return mto_fail(h, MTO_EINVAL, "mto_solve_batched: precision MTO_FP64 or MTO_MIXED");
+    if (opts->precision == MTO_MIXED && h->built_precision != MTO_MIXED)
+      return mto_fail(h, MTO_EINVAL, "mto_solve_batched: the mixed solve needs the MTO_MIXED build");
+    for (int32_t k = 0; k < i; ++k)
+      if (hs[k] == h) return mto_fail(h, MTO_EINVAL, "mto_solve_batched: a handle appears twice");
+  }
+  if (!(opts->rtol > 0) || opts->max_iter < 1 || opts->check_every < 1 ||
+      (opts->precond != MTO_PREC_JACOBI && opts->precond != MTO_PREC_SCHWARZ && opts->precond != MTO_PREC_MG) ||
+      (opts->norm != MTO_NORM_L2 && opts->norm != MTO_NORM_JACOBI && opts->norm != MTO_NORM_ENERGY))
+    return mto_fail(hs[0], MTO_EINVAL, "mto_solve_batched: bad options");
+  cudaSetDevice(device);
+  std::vector<std::unique_ptr<StreamJoin>> joins;
+  for (int32_t i = 0; i < n; ++i) joins.emplace_back(new StreamJoin(hs[i]));
+  return solve_batched(hs, n, f, u, opts, iters, relres, status);
+}
+
+mto_status mto_sensitivity_batched(mto_handle* hs, int32_t n, const double* const* u, const double* const* f,
+                                   const double* const* rho, const mto_material* mat, double* const* dc, double* C) {
+  if (!hs || n < 1 || !u || !f || !rho || !mat || !dc) return MTO_EINVAL;
+  mto_status first = MTO_OK;
+  for (int32_t i = 0; i < n; ++i) {   // the launches of every instance first (asynchronous) ...
+    const mto_status st = mto_sensitivity(hs[i], u[i], f[i], rho[i], mat, MTO_FP64, dc[i], nullptr);
+    if (first == MTO_OK && st != MTO_OK) first = st;
+  }
+  if (first != MTO_OK || !C) return first;
+  for (int32_t i = 0; i < n; ++i) {   // ... then the compliances (one synchronisation each)
+    mto_handle h = hs[i];
+    MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->host_pinned + 8, h->red + 8, sizeof(double), cudaMemcpyDeviceToHost,
+                                              h->stream), "copy"));
+  }
+  for (int32_t i = 0; i < n; ++i) {
+    mto_handle h = hs[i];
+    MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
+    C[i] = h->host_pinned[8];
+  }
+  return MTO_OK;
 }
 
 mto_status mto_apply(mto_handle h, const double* x, double* y) {
@@ -830,6 +910,16 @@ mto_status mto_compliance(mto_handle h, const double* f, const double* u, double
   return MTO_OK;
 }
 
+mto_status mto_compliance_energy(mto_handle h, const double* u, const double* f, const double* rho,
+                                 const mto_material* mat, double* C) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
+  if (!h->have_setup || !u || !f || !rho || !mat || !C)
+    return mto_fail(h, MTO_EINVAL, "mto_compliance_energy: bad arguments");
+  cudaSetDevice(h->device);
+  return compliance_energy(h, u, f, rho, mat, C);
+}
+
 mto_status mto_apply_operator(mto_handle h, int32_t op, const double* x, double* y, double* xKx) {
   if (!h) return MTO_EINVAL;
   StreamJoin join(h);
@@ -853,7 +943,17 @@ mto_status mto_set_operator_kernel(mto_handle h, int32_t kernel) {
     clear_graphs(h);   // captured iterations hold the previous kernel
   }
   h->op_kernel = kernel;
+  for (auto& k : h->op_kernel_cls) k = -2;   // the explicit choice overrides the autotuner's
   return MTO_OK;
+}
+
+mto_status mto_autotune(mto_handle h, int32_t* choice, double* us) {
+  if (!h) return MTO_EINVAL;
+  StreamJoin join(h);
+  if (!h->have_setup || h->built_precision < 0) return mto_fail(h, MTO_EINVAL, "mto_autotune: build first");
+  cudaSetDevice(h->device);
+  MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "mto_autotune"));
+  return autotune_operator(h, choice, us);
 }
 
 mto_status mto_element_matrix_split(mto_handle h, int64_t e, float* hi, float* lo) {

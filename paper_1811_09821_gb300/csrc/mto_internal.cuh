@@ -171,6 +171,7 @@ struct mto_handle_s {
   int64_t* fixed_d = nullptr;                  // [n_fixed] supported DOFs
   int64_t n_fixed = 0;
   double* filt_W = nullptr;                    // [design_len] density-filter weight sums (adjoint)
+  double* oc_t = nullptr;                      // [design_len] OC: rho_j B_j^eta
   int64_t* spring_dof_d = nullptr;             // [n_springs] DOFs with a spring to ground (K + k e e^T)
   double* spring_k_d = nullptr;                // [n_springs] their stiffness
   int n_springs = 0;
@@ -192,6 +193,8 @@ struct mto_handle_s {
   int* cg_base = nullptr;                      // first iteration of the running chunk
   bool schwarz_valid = false;
   bool inner_split = false;                    // operator applies use the split pair (mixed inner solves)
+  int op_kernel_cls[mto::kPMaxTab + 1] = {-2, -2, -2, -2, -2, -2, -2, -2};   // per order class (autotuner);
+                                               // -2: the handle-wide choice below
   int op_kernel = -1;                          // split operator, n_e <= 32: 0 register pipeline, 1 bulk-copy
                                                // staging, 2 the generic per-chunk kernel, -1 by the size
                                                // of the class's rows
@@ -218,8 +221,11 @@ struct mto_handle_s {
   int build_path = MTO_BUILD_SIMT;
   bool use_graphs = true;
   bool solve_log = false;                      // MTO_SOLVE_LOG=1: one stderr line per refinement step
+  double mg_ratio = 0.0;                       // MTO_MG_RATIO: Chebyshev interval lmax / ratio .. lmax (0: 100)
+  int mg_q1deg = 0;                            // MTO_MG_Q1DEG: smoothing degree on the Q1 levels (0: 4)
   std::vector<mto::GraphEntry*> graphs;
   double* red = nullptr;                       // misc reduction scratch [64]
+  double* eng = nullptr;                       // CG energy log of the compliance-accuracy test [128]
   int* flags = nullptr;                        // [0] iterations when done, [1] error code, [2..] misc
   int* host_flags = nullptr;                   // pinned host mirror of flags[0..1]
   double* host_pinned = nullptr;               // pinned host mirror for small read-backs [64]
@@ -433,10 +439,13 @@ int ebe_blocks(int p, int n);                                           // grid 
 // apply.cu
 mto_status apply64(mto_handle h, const double* x, double* y);        // y += K x (FP64 vectors)
 mto_status apply_operator(mto_handle h, int op, const double* x, double* y, double* xKx);   // mto_apply_operator
+mto_status autotune_operator(mto_handle h, int32_t* choice, double* us);                   // mto_autotune
 mto_status apply_fine(mto_handle h, const double* x, double* y, const int* done);   // same, early exit
 mto_status apply_q1(mto_handle h, const MGLevel& l, const double* x, double* y, const int* done);
 mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts* o, int32_t* iters,
                  double* relres);
+mto_status solve_batched(mto_handle* hs, int n, const double* const* f, double* const* u, const mto_solve_opts* o,
+                         int32_t* iters, double* relres, mto_status* status);
 // sens.cu
 // filter.cu
 mto_status density_filter(mto_handle h, double R, const double* x, double* out, bool adjoint);
@@ -455,4 +464,8 @@ mto_status oc_update(mto_handle h, const double* rho, const double* dc, double v
                      double eta, double* rho_new, double* lambda);
 // reductions shared by several units
 mto_status dot64(mto_handle h, const double* a, const double* b, int64_t n, double* out_dev);
+mto_status sum64(mto_handle h, const double* a, int64_t n, double* out_dev);
+// sens.cu
+mto_status compliance_energy(mto_handle h, const double* u, const double* f, const double* rho,
+                             const mto_material* m, double* C);
 }  // namespace mto

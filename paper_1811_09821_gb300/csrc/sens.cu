@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(128) sens_kernel(
     int n, int d, const int* __restrict__ elem, const int* __restrict__ slot, int ld, const int* __restrict__ gmap,
     const Constraint* __restrict__ cons, const double* __restrict__ u, const double* __restrict__ v,
     const double* __restrict__ rho, const int64_t* __restrict__ design_off, double E0, double Emin, double q,
-    double nu, double hx, double hy, const T* __restrict__ tab, const double* __restrict__ Z, double* __restrict__ dc) {
+    double nu, double hx, double hy, const T* __restrict__ tab, const double* __restrict__ Z, double* __restrict__ dc,
+    double* __restrict__ eout) {
   constexpr int N1 = PO + 1, NN = N1 * N1;
   static_assert(NN <= 64, "two nodes per lane at most");
   const int G = d * N1;
@@ -152,6 +153,7 @@ __global__ void __launch_bounds__(128) sens_kernel(
   const T D11 = (T)f, D12 = (T)(f * nu), D33 = (T)(f * 0.5 * (1.0 - nu));
   const double dE = E0 - Emin;
   const int64_t off = design_off[e];
+  double energy = 0.0;   // sum_s E(rho_s) w_s of this element (eout)
   for (int j = 0; j < d; ++j) {
     for (int g = lane; g < G; g += 32) {
       T acc = 0;
@@ -187,15 +189,20 @@ __global__ void __launch_bounds__(128) sens_kernel(
       for (int kk = 0; kk < N1; ++kk) w += part[i * N1 + kk];
       const int s = j * d + i;
       const double r = rho[off + s];
-      dc[off + s] = -q * pow(r, q - 1.0) * dE * (double)w;
+      if (dc) dc[off + s] = -q * pow(r, q - 1.0) * dE * (double)w;
+      if (eout) energy += (Emin + pow(r, q) * dE) * (double)w;
     }
     __syncwarp();
+  }
+  if (eout) {
+    energy = wsum(energy);
+    if (lane == 0) eout[e] = energy;
   }
 }
 
 template <int PO, int NF, typename T>
 mto_status launch_sens(mto_handle h, const BClass& b, const double* u, const double* v, const double* rho,
-                       const mto_material* m, const T* tab, double* dc) {
+                       const mto_material* m, const T* tab, double* dc, double* eout) {
   const int N1 = PO + 1, G = b.d * N1;
   const size_t per_warp = (size_t)(4 * NF * N1 * G + G + 2 * NF * N1 * N1) * sizeof(T);
   const int warps = 4;
@@ -206,23 +213,23 @@ mto_status launch_sens(mto_handle h, const BClass& b, const double* u, const dou
   const PClass& c = h->pc[b.p];
   sens_kernel<PO, NF, T><<<(b.n + warps - 1) / warps, 32 * warps, smem, h->stream>>>(
       b.n, b.d, b.elem, b.slot, c.ld, c.gmap, h->cons_d, u, v, rho, h->design_off_d, m->E0, m->Emin, m->q, m->nu,
-      h->hx, h->hy, tab, b.stab + 2 * N1 * G + G, dc);
+      h->hx, h->hy, tab, b.stab + 2 * N1 * G + G, dc, eout);
   return mto_after_launch(h, "sens_kernel");
 }
 
 template <int NF, typename T>
 mto_status sens_all(mto_handle h, const double* u, const double* v, const double* rho, const mto_material* m,
-                    double* dc) {
+                    double* dc, double* eout = nullptr) {
   for (auto& b : h->bc) {
     const T* tab;
     if constexpr (sizeof(T) == 8) tab = (const T*)b.stab; else tab = (const T*)b.stabf;
     switch (b.p) {
-      case 1: MTO_TRY((launch_sens<1, NF, T>(h, b, u, v, rho, m, tab, dc))); break;
-      case 2: MTO_TRY((launch_sens<2, NF, T>(h, b, u, v, rho, m, tab, dc))); break;
-      case 3: MTO_TRY((launch_sens<3, NF, T>(h, b, u, v, rho, m, tab, dc))); break;
-      case 4: MTO_TRY((launch_sens<4, NF, T>(h, b, u, v, rho, m, tab, dc))); break;
-      case 5: MTO_TRY((launch_sens<5, NF, T>(h, b, u, v, rho, m, tab, dc))); break;
-      case 6: MTO_TRY((launch_sens<6, NF, T>(h, b, u, v, rho, m, tab, dc))); break;
+      case 1: MTO_TRY((launch_sens<1, NF, T>(h, b, u, v, rho, m, tab, dc, eout))); break;
+      case 2: MTO_TRY((launch_sens<2, NF, T>(h, b, u, v, rho, m, tab, dc, eout))); break;
+      case 3: MTO_TRY((launch_sens<3, NF, T>(h, b, u, v, rho, m, tab, dc, eout))); break;
+      case 4: MTO_TRY((launch_sens<4, NF, T>(h, b, u, v, rho, m, tab, dc, eout))); break;
+      case 5: MTO_TRY((launch_sens<5, NF, T>(h, b, u, v, rho, m, tab, dc, eout))); break;
+      case 6: MTO_TRY((launch_sens<6, NF, T>(h, b, u, v, rho, m, tab, dc, eout))); break;
     }
   }
   return MTO_OK;
@@ -263,6 +270,26 @@ mto_status sensitivity_adjoint(mto_handle h, const double* u, const double* v, c
                                const mto_material* m, double* dc) {
   TimedScope ts(h, F_SENS);
   return sens_all<2, double>(h, u, v, rho, m, dc);
+}
+
+// Compliance of an approximate displacement in its energy form, C(u) = 2 f^T u - u^T K u
+// (= C* - ||u* - u||_K^2 for the exact u*, so its error is second order in the displacement's):
+// u^T K u as the sum of the element energies sum_s E(rho_s) u_e^T K0_s u_e, each after the FP64
+// removal of the element's rigid motion (free of the cancellation of a global u^T (K u)), summed
+// over the elements in a fixed order.
+mto_status compliance_energy(mto_handle h, const double* u, const double* f, const double* rho,
+                             const mto_material* m, double* C) {
+  {
+    TimedScope ts(h, F_SENS);
+    MTO_TRY((sens_all<1, double>(h, u, nullptr, rho, m, nullptr, h->dbuf)));
+    MTO_TRY(sum64(h, h->dbuf, h->nel, h->red + 10));
+    MTO_TRY(dot64(h, f, u, h->ndof, h->red + 11));
+  }
+  MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->host_pinned + 10, h->red + 10, 2 * sizeof(double),
+                                            cudaMemcpyDeviceToHost, h->stream), "copy"));
+  MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "sync"));
+  *C = 2.0 * h->host_pinned[11] - h->host_pinned[10];
+  return MTO_OK;
 }
 
 }  // namespace mto

@@ -67,15 +67,19 @@ def test_adaptive_cycles_against_oracle(mto):
         stops = [oad.cycle_converged(J[t - 1], J[t], rc.cycle) for t in range(1, len(J))]
         assert not any(stops[:-1])
         assert stops[-1] or rc.iterations == 25
-        # the final state against the oracle: u solves K(rho~) u = f, C = f^T u
+        # the final state against the oracle: the solves stop at a relative compliance accuracy of
+        # 1e-9, so J (the energy form) is within 1e-8 of the exact compliance and u within
+        # ||u - u*||_K^2 <= 1e-8 C of the exact displacement
         m = om.DPMesh(nelx, nely, rc.p, rc.d)
         fixed, f = om.cantilever_bc(m)
         rf = rc.state["rho_f"].cpu().numpy()
         K = osv.assemble(m, osv.element_matrices(m, rf, 1.0, 1e-9, 0.3, 3.0))
         u_o = osv.solve_direct(K, f, fixed)
+        C_o = ose.compliance(f, u_o)
         u = rc.state["u"].cpu().numpy()
-        assert np.linalg.norm(u - u_o) <= 1e-6 * np.linalg.norm(u_o)
-        assert abs(J[-1] - ose.compliance(f, u_o)) <= 1e-7 * abs(J[-1])
+        e = u - u_o
+        assert e @ (K @ e) <= 1e-8 * C_o
+        assert abs(J[-1] - C_o) <= 1e-8 * C_o
         # indicators and maps of the update, on the GPU's own state
         ga = oi.kelly(m, u)
         gd = oi.gamma_d(m, rf, cycle=rc.cycle)
@@ -83,12 +87,12 @@ def test_adaptive_cycles_against_oracle(mto):
         ind = rc.state["indicators"]
         np.testing.assert_allclose(ind["gamma_a"].cpu().numpy(), ga, rtol=1e-9, atol=1e-12 * np.abs(ga).max())
         np.testing.assert_allclose(ind["gamma_d"].cpu().numpy(), gd, rtol=0, atol=1e-15)
-        np.testing.assert_allclose(ind["eps_qr"].cpu().numpy(), eq, rtol=0, atol=1e-7)
+        np.testing.assert_allclose(ind["eps_qr"].cpu().numpy(), eq, rtol=0, atol=1e-6)
         srt = np.sort(ga, kind="stable")
         nc, nr = int(np.floor(0.05 * nel)), int(np.floor(0.10 * nel))
         ties = sum(int(srt[k] - srt[k - 1] <= 1e-12 * abs(srt[k])) for k in (nc, nel - nr))
         ties += int(((gd != 0) & (np.abs(gd) <= 1e-12 * np.abs(gd).max())).sum())
-        ties += int((np.abs(eq - 0.9) <= 1e-12).sum())
+        ties += int((np.abs(eq - 0.9) <= 1e-6).sum())
         pn, dn, th = oi.map_update(nelx, nely, rc.p, ga, gd, eq)
         np.testing.assert_array_equal(rc.p_new, pn)
         np.testing.assert_array_equal(rc.d_new, dn)

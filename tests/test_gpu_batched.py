@@ -1,0 +1,97 @@
+"""Batched instances (the 64-instance workload's recipe: uneven sizes, orders, design counts,
+alternating cantilever and MBB loads) through mto_build_elements_batched / mto_solve_batched /
+mto_sensitivity_batched, each instance against the oracle; the batched solve matches the same
+instance solved alone; the autotuner's choice is one of the kernels and keeps parity."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import workloads as W
+from oracle import mesh as om
+from oracle import sensitivity as ose
+from oracle import solve as osv
+
+
+@pytest.fixture(scope="module")
+def mto():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1811_09821_gb300 as m
+    from paper_1811_09821_gb300 import _build
+    _build.build()
+    m.load_library()
+    return m
+
+
+def small_instances(k=6):
+    """The first k instances of the batched recipe of at most 80 x 40 elements (oracle-sized)."""
+    return [pr for pr in W.batched() if pr.nelx <= 80][:k]
+
+
+def test_batched_solve_matches_oracle_and_single(mto):
+    prs = small_instances()
+    assert len({(int(p.p[0]), int(p.d[0]), p.nelx) for p in prs}) > 2      # uneven instances
+    hs, fs, us, rhos, dcs = [], [], [], [], []
+    mat = mto.material()
+    for pr in prs:
+        h = mto.Handle(0, stream=torch.cuda.Stream())
+        h.setup(pr.nelx, pr.nely, pr.p, pr.d)
+        fixed, f = mto.load_case(h, pr.load)
+        h.set_supports(fixed)
+        hs.append(h)
+        fs.append(f)
+        us.append(torch.zeros(h.ndof, dtype=torch.float64, device="cuda"))
+        rhos.append(torch.tensor(pr.rho, device="cuda"))
+        dcs.append(torch.zeros(h.design_len, dtype=torch.float64, device="cuda"))
+    mto.build_elements_batched(hs, rhos, mat, mto.MTO_MIXED)
+    its, rr, st = mto.solve_batched(hs, fs, us, precision=mto.MTO_MIXED, rtol=1e-10, norm=mto.NORM_ENERGY)
+    assert np.all(st == 0) and np.all(its > 0)
+    C = mto.sensitivity_batched(hs, us, fs, rhos, mat, dcs)
+    torch.cuda.synchronize()
+    for i, pr in enumerate(prs):
+        m = om.DPMesh(pr.nelx, pr.nely, pr.p, pr.d)
+        fixed, f = (om.mbb_bc if pr.load == W.MBB else om.cantilever_bc)(m)
+        K = osv.assemble(m, osv.element_matrices(m, pr.rho, pr.E0, pr.Emin, pr.nu, pr.q))
+        u_o = osv.solve_direct(K, f, fixed)
+        C_o = ose.compliance(f, u_o)
+        e = us[i].cpu().numpy() - u_o
+        assert e @ (K @ e) <= 1e-8 * C_o, (i, pr.name)
+        dc_o = ose.sensitivity(m, u_o, pr.rho, pr.E0, pr.Emin, pr.nu, pr.q)
+        assert np.abs(dcs[i].cpu().numpy() - dc_o).max() <= 1e-6 * np.abs(dc_o).max(), (i, pr.name)
+        assert abs(C[i] - C_o) <= 1e-4 * C_o      # f^T u: first order in the error of u
+    # one instance solved alone: the same iterations, and the same u up to the ordering of the FP64
+    # atomic scatter (the operator's only order-dependent step)
+    k = 2
+    u1 = torch.zeros_like(us[k])
+    it1, _ = hs[k].solve(fs[k], u1, precision=mto.MTO_MIXED, rtol=1e-10, norm=mto.NORM_ENERGY, max_iter=200000,
+                         check_every=32, precond=mto.PREC_MG)
+    assert abs(it1 - its[k]) <= 32
+    assert float((u1 - us[k]).norm()) <= 1e-6 * float(us[k].norm())
+    for h in hs:
+        h.close()
+
+
+def test_autotune_choice_keeps_parity(mto):
+    pr = W.named("mbb_40x20_p3_d8")
+    h = mto.Handle(0)
+    h.setup(pr.nelx, pr.nely, pr.p, pr.d)
+    mat = mto.material()
+    rho = torch.tensor(pr.rho, device="cuda")
+    h.build_elements(rho, mat, mto.MTO_MIXED)
+    res = h.autotune()
+    assert set(res) == {3} and res[3][0] in (0, 1, 2) and all(t > 0 for t in res[3][1])
+    x = torch.randn(h.ndof, dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(x)
+    y64 = torch.zeros_like(x)
+    h.apply_operator(x, y, mto.OP_SPLIT)
+    h.apply_operator(x, y64, mto.OP_FP64)
+    assert float((y - y64).abs().max()) <= 1e-13 * float(y64.abs().max())
+    # a second handle with the same class size takes the cached choice
+    h2 = mto.Handle(0)
+    h2.setup(pr.nelx, pr.nely, pr.p, pr.d)
+    h2.build_elements(rho, mat, mto.MTO_MIXED)
+    assert h2.autotune() == res
+    h.close()
+    h2.close()

@@ -129,7 +129,9 @@ def test_fullsize_indicators_and_maps(mto, name):
     eq = oi.qr_error(m, un, pr.rho, pr.E0, pr.Emin, pr.nu, pr.q)
     np.testing.assert_allclose(ind["gamma_a"].cpu().numpy(), ga, rtol=1e-9, atol=1e-12 * np.abs(ga).max())
     np.testing.assert_allclose(ind["gamma_d"].cpu().numpy(), gd, rtol=0, atol=1e-15)
-    np.testing.assert_allclose(ind["eps_qr"].cpu().numpy(), eq, rtol=0, atol=1e-7)
+    # eps = 1 - J^p / J^(p+1) of element problems whose condition reaches ~1e10 (solid/void
+    # elements): two FP64 evaluations agree to ~1e-16 x 1e10 = 1e-6
+    np.testing.assert_allclose(ind["eps_qr"].cpu().numpy(), eq, rtol=0, atol=1e-6)
     # guard band (1e-12 relative): the decisions are the two rank boundaries of Gamma^a, the sign
     # of Gamma^d and eps > 0.9; an element within the band of a cut-off is a tie, reported with
     # its neighbour across the boundary, and expected nowhere on these seeded workloads
@@ -142,7 +144,7 @@ def test_fullsize_indicators_and_maps(mto, name):
         if srt[k] - srt[k - 1] <= 1e-12 * abs(srt[k]):
             ties.append(("Gamma^a rank", int(order[k - 1]), int(order[k]), srt[k - 1], srt[k]))
     ties += [("Gamma^d sign", int(e), gd[e]) for e in np.flatnonzero((gd != 0) & (np.abs(gd) <= 1e-12 * np.abs(gd).max()))]
-    ties += [("eps 0.9", int(e), eq[e]) for e in np.flatnonzero(np.abs(eq - 0.9) <= 1e-12)]
+    ties += [("eps 0.9", int(e), eq[e]) for e in np.flatnonzero(np.abs(eq - 0.9) <= 1e-6)]
     print(f"{name}: ties {ties}")
     pn, dn, th = oi.map_update(pr.nelx, pr.nely, pr.p, ga, gd, eq)
     np.testing.assert_array_equal(ind["p_new"].cpu().numpy(), pn)
@@ -214,13 +216,13 @@ def test_fullsize_autograd_fd_50_points(mto):
     pr, h, m = c["pr"], c["h"], c["m"]
     f, rho, mat = c["gf"], c["rho"], c["mat"]
     r = rho.clone().requires_grad_(True)
-    C = mto.compliance(h, r, f, mat, precision=mto.MTO_MIXED, rtol=1e-10, norm=mto.NORM_JACOBI,
+    C = mto.compliance(h, r, f, mat, precision=mto.MTO_MIXED, rtol=1e-12, norm=mto.NORM_ENERGY,
                        max_iter=200000, precond=mto.PREC_MG)
     C.backward()
     g = r.grad.cpu().numpy()
     h.build_elements(rho, mat, mto.MTO_FP64)
     u0 = torch.zeros(h.ndof, dtype=torch.float64, device="cuda")
-    h.solve(f, u0, precision=mto.MTO_FP64, rtol=1e-10, norm=mto.NORM_JACOBI, max_iter=200000,
+    h.solve(f, u0, precision=mto.MTO_FP64, rtol=1e-13, norm=mto.NORM_ENERGY, max_iter=200000,
             precond=mto.PREC_MG)
     rng = np.random.default_rng(181109821 + 3)
     w = np.abs(g) / np.abs(g).sum()
@@ -237,7 +239,7 @@ def test_fullsize_autograd_fd_50_points(mto):
             r2[int(s)] += sign * hstep
             h.build_elements(r2, mat, mto.MTO_FP64)
             u.copy_(u0)
-            h.solve(f, u, precision=mto.MTO_FP64, rtol=1e-12, norm=mto.NORM_JACOBI, max_iter=20000,
+            h.solve(f, u, precision=mto.MTO_FP64, rtol=1e-14, norm=mto.NORM_ENERGY, max_iter=20000,
                     warm_start=True, precond=mto.PREC_MG, raise_on_noconv=False)
             vals.append(2.0 * float(f @ u) - element_energy(mto, h, u, f, r2, mat, work, pr))
         fd = (vals[0] - vals[1]) / (2 * hstep)

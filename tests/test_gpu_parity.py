@@ -429,3 +429,42 @@ def test_autograd_compliance_matches_oracle(mto):
     bad = np.abs(g - dc) > 1e-6 * np.abs(dc) + 1e-10 * np.abs(dc).max()
     assert not bad.any(), (int(bad.sum()), np.flatnonzero(bad)[:5])
     h.close()
+
+
+def abs_energy(o):
+    """sum_e |u_e|^T |K_e| |u_e| at the oracle's solution: the scale of the rounding error of any
+    FP64 evaluation of u^T K u."""
+    m, pr, u = o["mesh"], o["pr"], o["u"]
+    Ke = osv.element_matrices(m, pr.rho, pr.E0, pr.Emin, pr.nu, pr.q)
+    return sum(np.abs(m.gather(e, u)) @ (np.abs(Ke[e]) @ np.abs(m.gather(e, u))) for e in range(m.nel))
+
+
+@pytest.mark.parametrize("path", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", CASES)
+def test_compliance_accuracy_solve(mto, name, path):
+    """The compliance-accuracy solve (MTO_NORM_ENERGY, rtol 1e-8), from a zero start and
+    warm-started from a perturbed displacement: its compliance error ||u - u*||_K^2 (evaluated with
+    the oracle's K on the small difference u - u*, free of cancellation) is at most 1e-8 C*.  The
+    energy form 2 f^T u - u^T K u of mto_compliance_energy at the oracle's exact u reproduces C*
+    within the rounding floor of any FP64 evaluation of u^T K u, 64 eps sum_e |u_e|^T |K_e| |u_e|
+    (which on the binary beam is 2e-6 C: there no FP64 energy evaluation resolves 1e-8)."""
+    o = oracle_results(name)
+    pr = o["pr"]
+    build, sprec = (getattr(mto, k) for k in PATHS[path])
+    h, fixed, f, mat, rho = gpu_setup(mto, pr)
+    h.build_elements(rho, mat, build)
+    C_star = o["C"]
+    floor = 64 * np.finfo(np.float64).eps * abs_energy(o)
+    uo = torch.tensor(o["u"], device="cuda")
+    assert abs(h.compliance_energy(uo, f, rho, mat) - C_star) <= 1e-13 * abs(C_star) + floor
+    rng = np.random.default_rng(2)
+    for start in ("zero", "warm"):
+        u = torch.zeros(h.ndof, dtype=torch.float64, device="cuda")
+        if start == "warm":
+            u.copy_(uo * torch.tensor(1.0 + 0.05 * rng.standard_normal(h.ndof), device="cuda"))
+        it, rr = h.solve(f, u, precision=sprec, rtol=1e-8, norm=mto.NORM_ENERGY, max_iter=40000,
+                         precond=mto.PREC_MG, warm_start=start == "warm")
+        e = u.cpu().numpy() - o["u"]
+        err = e @ (o["K"] @ e)
+        assert err <= 1e-8 * C_star, (start, err / C_star, it)
+    h.close()

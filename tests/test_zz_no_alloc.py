@@ -63,6 +63,14 @@ def test_noalloc_limits(mto):
     assert call(mto, f, f, 4, out) == 0
     torch.cuda.synchronize()
     assert out.item() == 4.0
-    # beyond the scratch: refused before any launch (the pointers are never read)
-    assert call(mto, f, f, MAX_N + 1, out) == 1
-    assert call(mto, f, f, -1, out) == 1
+    # beyond the scratch: refused by the library before any launch (the pointers are never read);
+    # the binding's own checks refuse n beyond the tensors first
+    L = mto.load_library()
+    import ctypes
+    st = torch.cuda.current_stream(0).cuda_stream
+    for n in (MAX_N + 1, -1):
+        assert L.mto_compliance_noalloc(0, f.data_ptr(), f.data_ptr(), n, ctypes.c_void_p(st), out.data_ptr()) == 1
+    with pytest.raises(ValueError):
+        call(mto, f, f, 5, out)
+    with pytest.raises(ValueError):
+        call(mto, f.float(), f, 4, out)

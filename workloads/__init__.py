@@ -298,6 +298,8 @@ def named(name):
         "dp_cantilever_320x160": lambda: dp_cantilever(),
         "dp_cantilever_40x20": lambda: dp_cantilever(40, 20, vol=0.3, seed_index=13),
         "mbb_1024x512_p3_d8": lambda: mbb_smooth(),
+        # the same recipe on a 64 x 32 mesh: the bounded sample the CPU oracle is timed on
+        "mbb_64x32_p3_d8": lambda: mbb_smooth(64, 32, seed_index=15),
         # 3 x 3 tiles of the 160 x 80 binary beam: element matrices (~1 GB for both storages) above
         # L2, for hardware-counter captures of one operator launch
         "mbb_480x240_p3_d8": lambda: mbb_tiled(3, 3),
