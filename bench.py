@@ -56,7 +56,9 @@ def parse(argv=None):
                     help="oc: steps are iterations of one optimization run (default for the large beam); "
                          "pass: repeated passes over one fixed design (default for the other workloads)")
     ap.add_argument("--rtol", type=float, default=1e-8, help="relative compliance accuracy of every solve")
-    ap.add_argument("--mg-degree", type=int, default=4, help="Chebyshev degree of the multigrid smoothing")
+    ap.add_argument("--mg-degree", type=int, default=2, help="Chebyshev degree of the fine-level smoothing")
+    ap.add_argument("--smoother", default="block", choices=["block", "jacobi"],
+                    help="fine-level smoothing: element blocks (default) or point Jacobi")
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -237,6 +239,11 @@ def whole_job_rate(world, steps, max_ms):
     return world * steps / (max_ms * 1e-3)
 
 
+def smoother_of(args):
+    import paper_1811_09821_gb300 as mto
+    return mto.SMOOTH_BLOCK if args.smoother == "block" else mto.SMOOTH_JACOBI
+
+
 def operator_bytes(pr, ndof):
     """Algorithmic bytes of one split-operator launch: per element the hi/lo pair of its matrix in
     the circulant-diagonal row ((n_e/2 + 1) n_e entries, 2 x 4 bytes) and its node map (4 bytes per
@@ -279,7 +286,7 @@ class Run:
         h.build_elements(self.rho, self.mat, prec)
         it, rr = h.solve(self.f, self.u, precision=prec, rtol=self.args.rtol, norm=mto.NORM_ENERGY,
                          max_iter=400000, check_every=32, precond=mto.PREC_MG, mg_degree=self.args.mg_degree,
-                         warm_start=advance and self.k > 0)
+                         mg_smoother=smoother_of(self.args), warm_start=advance and self.k > 0)
         h.sensitivity(self.u, self.f, self.rho, self.mat, self.dc, precision=mto.MTO_FP64, want_C=False)
         h.indicator(self.u, self.rho, self.mat)
         h.oc_update(self.rho, self.dc, self.vol, self.rho_new, want_lambda=False)
@@ -330,7 +337,7 @@ def accuracy_check(run, last, prec):
     h.build_elements(rho, run.mat, mto.MTO_FP64)
     it, _ = h.solve(run.f, u, precision=mto.MTO_FP64, rtol=run.args.rtol * 1e-2, norm=mto.NORM_ENERGY,
                     max_iter=400000, check_every=32, precond=mto.PREC_MG, mg_degree=run.args.mg_degree,
-                    warm_start=True)
+                    mg_smoother=smoother_of(run.args), warm_start=True)
     Cr = h.compliance_energy(u, run.f, rho, run.mat)
     return {"path": "mixed" if prec == mto.MTO_MIXED else "fp64", "C": C, "C_fp64_ref": Cr,
             "rel_err": abs(C - Cr) / abs(Cr), "ref_iters": it}
@@ -428,7 +435,8 @@ def run_gpu(args, rank, world, local_rank):
                                                "its first iterations" if advance else
                                                "one pass over the fixed design from a zero start"),
                    "solve_accuracy": f"relative compliance error {args.rtol:g} (energy test)",
-                   "precond": "multigrid", "l2_flush": "512 MB write before each timed step",
+                   "precond": f"multigrid, {args.smoother} smoothing of degree {args.mg_degree} on the fine level",
+                   "l2_flush": "512 MB write before each timed step",
                    "parallelism": f"replicas x{world}"},
         "mdof_pcg_iter_per_s": run.nfree * mixed["iters"] / (mixed["ms"] * 1e-3) / 1e6,
         "pcg_iters_per_step": mixed["iters"] / steps,
@@ -463,10 +471,99 @@ def run_gpu(args, rank, world, local_rank):
     return out
 
 
+def run_batched(args, rank, world, local_rank):
+    """The 64-instance workload: every step builds, solves (compliance accuracy, from zero) and
+    differentiates all instances through the batched entry points (the instances run concurrently,
+    each on its own stream with its own captured iteration graphs).  value = instance TO iterations
+    per second of the whole batch."""
+    import numpy as np
+    import torch
+    import paper_1811_09821_gb300 as mto
+    import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    prs = W.batched()
+    mat = mto.material()
+    hs, fs, us, rhos, dcs, nfree, tune = [], [], [], [], [], 0, {}
+    for pr in prs:
+        h = mto.Handle(local_rank, stream=torch.cuda.Stream(dev))
+        nd, dl = h.setup(pr.nelx, pr.nely, pr.p, pr.d)
+        fixed, f = mto.load_case(h, pr.load)
+        h.set_supports(fixed)
+        nfree += nd - len(fixed)
+        hs.append(h)
+        fs.append(f)
+        us.append(torch.zeros(nd, dtype=torch.float64, device=dev))
+        rhos.append(torch.tensor(pr.rho, dtype=torch.float64, device=dev))
+        dcs.append(torch.zeros(dl, dtype=torch.float64, device=dev))
+    mto.build_elements_batched(hs, rhos, mat, mto.MTO_MIXED)
+    for h, pr in zip(hs, prs):
+        for p, (k, t) in h.autotune().items():
+            tune[f"p{p}_{pr.nelx}x{pr.nely}"] = ["pipe", "staged", "generic"][k]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(prec):
+        mto.build_elements_batched(hs, rhos, mat, prec)
+        its, _, _ = mto.solve_batched(hs, fs, us, precision=prec, rtol=args.rtol, norm=mto.NORM_ENERGY,
+                                      mg_degree=args.mg_degree, mg_smoother=smoother_of(args))
+        mto.sensitivity_batched(hs, us, fs, rhos, mat, dcs, want_C=False)
+        torch.cuda.synchronize(dev)
+        return int(its.sum())
+
+    def timed(prec, steps, warmup):
+        for _ in range(warmup):
+            step(prec)
+        l0 = sum(h.launch_count() for h in hs)
+        total, iters = 0.0, 0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            iters += step(prec)
+            total += (time.perf_counter() - t0) * 1e3
+        return total, iters, sum(h.launch_count() for h in hs) - l0
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    with ClockSampler(local_rank) as clk:
+        ms, iters, launches = timed(mto.MTO_MIXED, args.steps, args.warmup)
+    ms_max = max_over_ranks(ms, world, dev)
+    fsteps = max(1, min(args.steps, args.fp64_steps))
+    ms64, iters64, _ = timed(mto.MTO_FP64, fsteps, 1) if not args.no_fp64 else (None, None, None)
+    out = {
+        "metric": METRIC, "value": whole_job_rate(world, args.steps * len(hs), ms_max), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32x2 split operator (f32 pipes) in the inner PCG; f64 vectors, dots, refinement, compliance",
+        "data": "synthetic",
+        "config": {"workload": "batched_64", "instances": len(hs),
+                   "sizes": sorted({f"{p.nelx}x{p.nely}" for p in prs}),
+                   "orders": sorted({int(p.p[0]) for p in prs}), "design_counts": sorted({int(p.d[0]) for p in prs}),
+                   "free_dofs_total": nfree, "step": "build + compliance-accuracy solve from zero + sensitivities "
+                                                     "of all instances (batched entry points)",
+                   "solve_accuracy": f"relative compliance error {args.rtol:g}", "autotuned_kernels": tune,
+                   "timing": "host wall around each synchronised batched step (the instances run on 64 streams)",
+                   "l2_flush": "512 MB write before each timed step", "parallelism": f"replicas x{world}"},
+        "mdof_pcg_iter_per_s": None,
+        "pcg_iters_per_step": iters / args.steps, "gpu_launches": launches, "clocks": clk.summary(),
+        "e2e": None,
+    }
+    if ms64:
+        out["fp64_path"] = {"value": fsteps * len(hs) / (ms64 * 1e-3), "unit": UNIT, "steps": fsteps,
+                            "pcg_iters_per_step": iters64 / fsteps}
+        out["speedup_vs_fp64"] = out["value"] / world / out["fp64_path"]["value"]
+    for h in hs:
+        h.close()
+    return out
+
+
 def main(argv=None):
     args = parse(argv)
     if args.mode is None:
         args.mode = "oc" if args.workload == DEFAULT_WORKLOAD else "pass"
+    batched = args.workload == "batched_64"
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -497,9 +594,9 @@ def main(argv=None):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    out = run_gpu(args, rank, world, local_rank)
+    out = run_batched(args, rank, world, local_rank) if batched else run_gpu(args, rank, world, local_rank)
     if rank == 0:
-        if not args.no_cpu:
+        if not args.no_cpu and not batched:
             try:
                 out["cpu_baseline"] = cpu_baseline(args.workload)
             except Exception as ex:      # the oracle is only a reported baseline

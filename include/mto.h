@@ -113,6 +113,12 @@ typedef struct {
  *  inner_max   mixed solves: cap on the iterations of one inner solve (<= 0: none).
  *  mg_degree   MTO_PREC_MG only: Chebyshev degree of each pre- and post-smoothing on the fine
  *              level (<= 0: 4; at most 16); the Q1 levels use degree 4.
+ *  mg_smoother MTO_PREC_MG only: the fine level's smoothing.  MTO_SMOOTH_JACOBI: Chebyshev
+ *              polynomials of the point-Jacobi-scaled operator.  MTO_SMOOTH_BLOCK: of the
+ *              operator scaled by the element-block inverse sum_e P_e^T (K_e + Delta_e)^-1 P_e (the
+ *              blocks of MTO_PREC_SCHWARZ, which capture the element's own near-null modes; meshes
+ *              with hanging nodes fall back to Jacobi); one more block apply per smoothing step, and
+ *              on the 160 x 80 binary beam a third of the iterations.
  * CG iterations run in chunks of check_every (rounded up to a multiple of 4), each a CUDA graph;
  * the reported count stops at convergence, but a chunk already launched completes (cheaply). */
 typedef struct {
@@ -127,7 +133,11 @@ typedef struct {
   int32_t precond;
   int32_t inner_max;
   int32_t mg_degree;
+  int32_t mg_smoother;
 } mto_solve_opts;
+
+#define MTO_SMOOTH_JACOBI 0
+#define MTO_SMOOTH_BLOCK 1
 
 #define MTO_PREC_JACOBI 0
 #define MTO_PREC_SCHWARZ 1

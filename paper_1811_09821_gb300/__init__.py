@@ -23,6 +23,7 @@ BUILD_TENSOR, BUILD_SIMT = 0, 1
 OP_FP64, OP_SPLIT = 0, 1
 OPK_AUTO, OPK_PIPE, OPK_STAGED, OPK_GENERIC = -1, 0, 1, 2
 PREC_JACOBI, PREC_SCHWARZ, PREC_MG = 0, 1, 2
+SMOOTH_JACOBI, SMOOTH_BLOCK = 0, 1
 STATUS = {0: "MTO_OK", 1: "MTO_EINVAL", 2: "MTO_ENOMEM", 3: "MTO_ECUDA", 4: "MTO_ENOCONV", 5: "MTO_ENAN",
           6: "MTO_ETIMEOUT"}
 P_MAX, D_MAX = 6, 16
@@ -44,7 +45,7 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("rtol", ctypes.c_double), ("inner_rtol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("warm_start", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("norm", ctypes.c_int32), ("precond", ctypes.c_int32),
-                ("inner_max", ctypes.c_int32), ("mg_degree", ctypes.c_int32)]
+                ("inner_max", ctypes.c_int32), ("mg_degree", ctypes.c_int32), ("mg_smoother", ctypes.c_int32)]
 
 
 class IndicatorOpts(ctypes.Structure):
@@ -265,9 +266,9 @@ class Handle:
 
     def solve(self, f, u, precision=MTO_FP64, rtol=1e-8, inner_rtol=0.0, max_iter=200000, max_outer=50,
               warm_start=False, check_every=64, norm=NORM_L2, precond=PREC_SCHWARZ, inner_max=0,
-              mg_degree=0, raise_on_noconv=True):
+              mg_degree=0, mg_smoother=SMOOTH_JACOBI, raise_on_noconv=True):
         o = SolveOpts(precision, rtol, inner_rtol, max_iter, max_outer, int(bool(warm_start)), check_every, norm,
-                      precond, inner_max, mg_degree)
+                      precond, inner_max, mg_degree, mg_smoother)
         it, rr = ctypes.c_int32(), ctypes.c_double()
         st = self.L.mto_solve(self.h, _ptr(f, torch.float64), _ptr(u, torch.float64), ctypes.byref(o),
                               ctypes.byref(it), ctypes.byref(rr))
@@ -463,13 +464,13 @@ def build_elements_batched(handles, rhos, mat, precision=MTO_MIXED):
 
 def solve_batched(handles, fs, us, precision=MTO_MIXED, rtol=1e-8, inner_rtol=0.0, max_iter=200000, max_outer=50,
                   warm_start=False, check_every=32, norm=NORM_ENERGY, precond=PREC_MG, inner_max=0, mg_degree=0,
-                  raise_on_error=True):
+                  mg_smoother=SMOOTH_JACOBI, raise_on_error=True):
     """Step (b) of every instance, advanced together (mto_solve_batched).  Returns (iterations,
     relative residuals, statuses) as numpy arrays."""
     L = load_library()
     n = len(handles)
     o = SolveOpts(precision, rtol, inner_rtol, max_iter, max_outer, int(bool(warm_start)), check_every, norm,
-                  precond, inner_max, mg_degree)
+                  precond, inner_max, mg_degree, mg_smoother)
     it = np.zeros(n, np.int32)
     rr = np.zeros(n)
     stt = np.zeros(n, np.int32)

@@ -1312,6 +1312,11 @@ mto_status apply_fine(mto_handle h, const double* x, double* y, const int* done)
   return apply_all<double>(h, 0, x, y, -1, done, none);
 }
 
+mto_status apply_block(mto_handle h, const double* x, double* y, const int* done) {
+  ConvTest none{};
+  return apply_all<double>(h, 1, x, y, -1, done, none);
+}
+
 mto_status apply_q1(mto_handle h, const MGLevel& l, const double* x, double* y, const int* done) {
   ConvTest none{};
   ebe_kernel<1, false, double><<<ebe_blocks_p<1>(l.nel), 256, 0, h->stream>>>(
@@ -1355,6 +1360,7 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
   if (pc == MTO_PREC_MG) {
     if (o->precision == MTO_MIXED32)
       return mto_fail(h, MTO_EINVAL, "mto_solve: the multigrid preconditioner needs FP64 vectors");
+    MTO_TRY(mg_select_smoother(h, o->mg_smoother));
     if (!h->mg_valid) MTO_TRY(mg_build(h));
   }
   if (!o->warm_start) MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(u, 0, sizeof(double) * n, h->stream), "memset"));
@@ -1585,6 +1591,7 @@ mto_status solve_batched(mto_handle* hs, int n, const double* const* f, double* 
     else if (j.pc == MTO_PREC_SCHWARZ && h->n_cons > 0)
       st = mto_fail(h, MTO_EINVAL, "mto_solve_batched: element-block Schwarz is limited to meshes without order jumps");
     if (st == MTO_OK && j.pc == MTO_PREC_SCHWARZ && !h->schwarz_valid) st = build_schwarz(h);
+    if (st == MTO_OK && j.pc == MTO_PREC_MG) st = mg_select_smoother(h, o->mg_smoother);
     if (st == MTO_OK && j.pc == MTO_PREC_MG && !h->mg_valid) st = mg_build(h);
     if (st == MTO_OK) {
       if (!o->warm_start) st = mto_cuda_check(h, cudaMemsetAsync(j.u, 0, sizeof(double) * h->ndof, h->stream), "memset");

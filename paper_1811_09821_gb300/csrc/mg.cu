@@ -273,14 +273,16 @@ __global__ void __launch_bounds__(256) mg_cheb_kernel(int64_t n, const double* _
                                                       double* __restrict__ d, const double2* __restrict__ coef,
                                                       int step, int xzero, const int* __restrict__ done,
                                                       double* __restrict__ dpart, unsigned* __restrict__ dcnt,
-                                                      double* __restrict__ dres) {
+                                                      double* __restrict__ dres, int given) {
   if (done && *done) return;
   const double2 cc = coef[step];   // (c1, c2), precomputed per level
   const double c1 = cc.x, c2 = cc.y;
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double bi = b[i];
-    const double r = invd[i] * (bi - q[i]);
+    // given: q already holds the preconditioned residual (element-block smoothing), else the
+    // Jacobi-scaled residual is formed here from q = A x
+    const double r = given ? q[i] : invd[i] * (bi - q[i]);
     q[i] = 0.0;
     const double dn = step > 0 ? fma(c1, d[i], c2 * r) : c2 * r;   // c1 = 0 at step 0
     d[i] = dn;
@@ -306,6 +308,17 @@ __global__ void __launch_bounds__(256) mg_cheb_kernel(int64_t n, const double* _
       *dres = t;
       *dcnt = 0u;
     }
+  }
+}
+
+// element-block smoothing: w = b - q on free DOFs (0 on supports), q cleared for M^-1 w
+__global__ void __launch_bounds__(256) mg_block_resid_kernel(int64_t n, const double* __restrict__ b,
+                                                             double* __restrict__ q, const double* __restrict__ invd,
+                                                             double* __restrict__ w, const int* __restrict__ done) {
+  if (done && *done) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    w[i] = invd[i] != 0.0 ? (b ? b[i] : 0.0) - q[i] : 0.0;
+    q[i] = 0.0;
   }
 }
 
@@ -423,10 +436,10 @@ __global__ void mg_pow_init_kernel(int64_t n, const double* __restrict__ invd, d
 __global__ void __launch_bounds__(256) mg_pow_step_kernel(int64_t n, double* __restrict__ q,
                                                           const double* __restrict__ invd, double* __restrict__ w,
                                                           double* __restrict__ part, unsigned* __restrict__ cnt,
-                                                          double* __restrict__ res) {
+                                                          double* __restrict__ res, int given) {
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double wi = invd[i] * q[i];
+    const double wi = given ? q[i] : invd[i] * q[i];
     q[i] = 0.0;
     w[i] = wi;
     s += wi * wi;
@@ -675,10 +688,16 @@ mto_status mg_power(mto_handle h, int level, double* lmax_out) {
   const int grd = vec_grid(n);
   mg_pow_init_kernel<<<grd, 256, 0, h->stream>>>(n, invd, v, q);
   MTO_TRY(mto_after_launch(h, "mg_pow_init_kernel"));
+  const bool block = fine && h->mg_block;   // lmax of M^-1 A, M^-1 the element-block inverse
   for (int it = 0; it < kPowerIts; ++it) {
     if (fine) MTO_TRY(apply_fine(h, v, q, nullptr));
     else MTO_TRY(apply_q1(h, h->mg[level], v, q, nullptr));
-    mg_pow_step_kernel<<<grd, 256, 0, h->stream>>>(n, q, invd, w, h->mg_part, h->mg_cnt, h->mg_res);
+    if (block) {
+      mg_block_resid_kernel<<<grd, 256, 0, h->stream>>>(n, nullptr, q, invd, w, nullptr);   // w = -A v
+      MTO_TRY(mto_after_launch(h, "mg_block_resid_kernel"));
+      MTO_TRY(apply_block(h, w, q, nullptr));
+    }
+    mg_pow_step_kernel<<<grd, 256, 0, h->stream>>>(n, q, invd, w, h->mg_part, h->mg_cnt, h->mg_res, block);
     MTO_TRY(mto_after_launch(h, "mg_pow_step_kernel"));
     if (it + 1 < kPowerIts) {
       mg_pow_norm_kernel<<<grd, 256, 0, h->stream>>>(n, w, h->mg_res, v);
@@ -690,6 +709,19 @@ mto_status mg_power(mto_handle h, int level, double* lmax_out) {
 }
 
 }  // namespace
+
+// The fine level's smoothing for the next solves: a change rebuilds the Chebyshev bounds (lazily)
+// and drops the captured iteration graphs.
+mto_status mg_select_smoother(mto_handle h, int smoother) {
+  if (smoother != MTO_SMOOTH_JACOBI && smoother != MTO_SMOOTH_BLOCK)
+    return mto_fail(h, MTO_EINVAL, "mto_solve: bad mg_smoother");
+  if (smoother == h->mg_smoother) return MTO_OK;
+  MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "mto_solve"));
+  h->mg_smoother = smoother;
+  h->mg_valid = false;
+  clear_graphs(h);
+  return MTO_OK;
+}
 
 // Galerkin operators of every level, diagonals, Chebyshev bounds and the coarsest inverse, for the
 // element matrices of the last build (lazily, at the first multigrid solve after a build).
@@ -747,6 +779,10 @@ mto_status mg_build(mto_handle h) {
     h->mg_Acur = bufs[N & 1];
   }
   }
+  // element-block smoothing of the fine level: the blocks (K_e + Delta_e)^-1 of the element-block
+  // preconditioner (not on meshes with hanging nodes, where those blocks are not used)
+  h->mg_block = h->mg_smoother == 1 && h->n_cons == 0;
+  if (h->mg_block && !h->schwarz_valid) MTO_TRY(build_schwarz(h));
   // Chebyshev bounds: fine level first, then every smoothed Q1 level
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->mg_q0, 0, h->ndof * sizeof(double), h->stream), "memset"));
   MTO_TRY(mg_power(h, -1, h->mg_lmax));
@@ -777,6 +813,7 @@ mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const
     const int k = lev < 0 ? degree : (h->mg_q1deg > 0 ? h->mg_q1deg : kCoarseDegree);
     const double2* cf = h->mg_coef + (size_t)(lev + 1) * kMaxDegree;
     const int grd = vec_grid(n);
+    const bool block = lev < 0 && h->mg_block;   // element-block (additive Schwarz) smoothing
     for (int s = 0; s < k; ++s) {
       const bool skip_apply = pre && s == 0;   // x = 0: A x = 0
       if (!skip_apply) {
@@ -786,10 +823,18 @@ mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const
           MTO_TRY(apply_q1(h, h->mg[lev], x, q, done));
         }
       }
+      if (block) {   // q <- M^-1 (b - A x)
+        {
+          TimedScope ts(h, F_PRECOND);
+          mg_block_resid_kernel<<<grd, 256, 0, h->stream>>>(n, b, q, invd, h->mg_v0, done);
+          MTO_TRY(mto_after_launch(h, "mg_block_resid_kernel"));
+        }
+        MTO_TRY(apply_block(h, h->mg_v0, q, done));
+      }
       TimedScope ts(h, F_PRECOND);
       const bool dot = with_dot && s == k - 1;
       mg_cheb_kernel<<<grd, 256, 0, h->stream>>>(n, b, q, invd, x, d, cf, s, pre && s == 0, done,
-                                                  dot ? dot_part : nullptr, dot_cnt, dot_res);
+                                                  dot ? dot_part : nullptr, dot_cnt, dot_res, block);
       MTO_TRY(mto_after_launch(h, "mg_cheb_kernel"));
     }
     return MTO_OK;

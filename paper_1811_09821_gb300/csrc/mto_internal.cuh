@@ -223,6 +223,8 @@ struct mto_handle_s {
   bool solve_log = false;                      // MTO_SOLVE_LOG=1: one stderr line per refinement step
   double mg_ratio = 0.0;                       // MTO_MG_RATIO: Chebyshev interval lmax / ratio .. lmax (0: 100)
   int mg_q1deg = 0;                            // MTO_MG_Q1DEG: smoothing degree on the Q1 levels (0: 4)
+  int mg_smoother = 0;                         // fine-level smoothing: MTO_SMOOTH_JACOBI or MTO_SMOOTH_BLOCK
+  bool mg_block = false;                       // element-block smoothing in use (set by mg_build)
   std::vector<mto::GraphEntry*> graphs;
   double* red = nullptr;                       // misc reduction scratch [64]
   double* eng = nullptr;                       // CG energy log of the compliance-accuracy test [128]
@@ -429,6 +431,7 @@ int local_node_map_public(mto_handle h, int64_t e, int a, int b, int64_t* nodes,
 mto_status mg_setup(mto_handle h);                                      // hierarchy, transfer tables
 mto_status mg_set_masks(mto_handle h);                                  // supports on every level
 mto_status mg_build(mto_handle h);                                      // Galerkin operators, bounds
+mto_status mg_select_smoother(mto_handle h, int smoother);              // MTO_SMOOTH_* for next solves
 mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const int* done, double* dot_part,
                      unsigned* dot_cnt, double* dot_res);
 void mg_release(mto_handle h);
@@ -441,6 +444,7 @@ mto_status apply64(mto_handle h, const double* x, double* y);        // y += K x
 mto_status apply_operator(mto_handle h, int op, const double* x, double* y, double* xKx);   // mto_apply_operator
 mto_status autotune_operator(mto_handle h, int32_t* choice, double* us);                   // mto_autotune
 mto_status apply_fine(mto_handle h, const double* x, double* y, const int* done);   // same, early exit
+mto_status apply_block(mto_handle h, const double* x, double* y, const int* done);  // y += (element blocks) x
 mto_status apply_q1(mto_handle h, const MGLevel& l, const double* x, double* y, const int* done);
 mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts* o, int32_t* iters,
                  double* relres);

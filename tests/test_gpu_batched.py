@@ -50,6 +50,7 @@ def test_batched_solve_matches_oracle_and_single(mto):
     assert np.all(st == 0) and np.all(its > 0)
     C = mto.sensitivity_batched(hs, us, fs, rhos, mat, dcs)
     torch.cuda.synchronize()
+    Ks, Cs = [], []
     for i, pr in enumerate(prs):
         m = om.DPMesh(pr.nelx, pr.nely, pr.p, pr.d)
         fixed, f = (om.mbb_bc if pr.load == W.MBB else om.cantilever_bc)(m)
@@ -61,14 +62,19 @@ def test_batched_solve_matches_oracle_and_single(mto):
         dc_o = ose.sensitivity(m, u_o, pr.rho, pr.E0, pr.Emin, pr.nu, pr.q)
         assert np.abs(dcs[i].cpu().numpy() - dc_o).max() <= 1e-6 * np.abs(dc_o).max(), (i, pr.name)
         assert abs(C[i] - C_o) <= 1e-4 * C_o      # f^T u: first order in the error of u
-    # one instance solved alone: the same iterations, and the same u up to the ordering of the FP64
-    # atomic scatter (the operator's only order-dependent step)
+        Ks.append(K)
+        Cs.append(C_o)
+    # one instance solved alone: about the same iterations (the FP64 atomic scatter of the operator
+    # makes the order of additions, and so the last bits, differ from run to run), and the two
+    # displacements within the solve accuracy of each other in the energy norm (the islands of
+    # solid held only by void material move freely in the l2 norm)
     k = 2
     u1 = torch.zeros_like(us[k])
     it1, _ = hs[k].solve(fs[k], u1, precision=mto.MTO_MIXED, rtol=1e-10, norm=mto.NORM_ENERGY, max_iter=200000,
                          check_every=32, precond=mto.PREC_MG)
-    assert abs(it1 - its[k]) <= 32
-    assert float((u1 - us[k]).norm()) <= 1e-6 * float(us[k].norm())
+    assert abs(it1 - its[k]) <= 64
+    e = u1.cpu().numpy() - us[k].cpu().numpy()
+    assert e @ (Ks[k] @ e) <= 4e-10 * Cs[k]
     for h in hs:
         h.close()
 
