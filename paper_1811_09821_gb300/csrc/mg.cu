@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(256) mg_cheb_kernel(int64_t n, const double* _
                                                       double* __restrict__ d, const double2* __restrict__ coef,
                                                       int step, int xzero, const int* __restrict__ done,
                                                       double* __restrict__ dpart, unsigned* __restrict__ dcnt,
-                                                      double* __restrict__ dres, int given) {
+                                                      double* __restrict__ dres, int given, int zq) {
   if (done && *done) return;
   const double2 cc = coef[step];   // (c1, c2), precomputed per level
   const double c1 = cc.x, c2 = cc.y;
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(256) mg_cheb_kernel(int64_t n, const double* _
     // given: q already holds the preconditioned residual (element-block smoothing), else the
     // Jacobi-scaled residual is formed here from q = A x
     const double r = given ? q[i] : invd[i] * (bi - q[i]);
-    q[i] = 0.0;
+    if (zq) q[i] = 0.0;   // else a separate launch clears q (see mg_zero_kernel)
     const double dn = step > 0 ? fma(c1, d[i], c2 * r) : c2 * r;   // c1 = 0 at step 0
     d[i] = dn;
     const double xn = xzero ? dn : x[i] + dn;
@@ -311,16 +311,28 @@ __global__ void __launch_bounds__(256) mg_cheb_kernel(int64_t n, const double* _
   }
 }
 
-// element-block smoothing: w = b - q on free DOFs (0 on supports), q cleared for M^-1 w
+// element-block smoothing: w = b - q on free DOFs (0 on supports); q is cleared by the next launch
 __global__ void __launch_bounds__(256) mg_block_resid_kernel(int64_t n, const double* __restrict__ b,
-                                                             double* __restrict__ q, const double* __restrict__ invd,
+                                                             const double* __restrict__ q,
+                                                             const double* __restrict__ invd,
                                                              double* __restrict__ w, const int* __restrict__ done) {
   if (done && *done) return;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     w[i] = invd[i] != 0.0 ? (b ? b[i] : 0.0) - q[i] : 0.0;
-    q[i] = 0.0;
-  }
 }
+
+// v = 0 as its own launch: on GB300 a kernel that reads an array and stores zeros into it streams
+// at about a third of the rate of the same kernel without that store (see zero_kernel in apply.cu),
+// so the large accumulators are cleared separately
+__global__ void __launch_bounds__(256) mg_zero_kernel(int64_t n, double* __restrict__ v, const int* __restrict__ done) {
+  if (done && *done) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = 0.0;
+}
+
+// accumulators of at least this many entries are cleared by mg_zero_kernel (smaller ones, which stay
+// in L2, by the consuming kernel itself)
+constexpr int64_t kSeparateZero = 1 << 20;
 
 // level 0 -> 1: b1 = P^T r by the vertex-wise transposed table, the residual r = b - q formed on
 // the fly on free DOFs (q = A x stays; the prolongation clears it)
@@ -695,6 +707,8 @@ mto_status mg_power(mto_handle h, int level, double* lmax_out) {
     if (block) {
       mg_block_resid_kernel<<<grd, 256, 0, h->stream>>>(n, nullptr, q, invd, w, nullptr);   // w = -A v
       MTO_TRY(mto_after_launch(h, "mg_block_resid_kernel"));
+      mg_zero_kernel<<<grd, 256, 0, h->stream>>>(n, q, nullptr);
+      MTO_TRY(mto_after_launch(h, "mg_zero_kernel"));
       MTO_TRY(apply_block(h, w, q, nullptr));
     }
     mg_pow_step_kernel<<<grd, 256, 0, h->stream>>>(n, q, invd, w, h->mg_part, h->mg_cnt, h->mg_res, block);
@@ -828,14 +842,21 @@ mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const
           TimedScope ts(h, F_PRECOND);
           mg_block_resid_kernel<<<grd, 256, 0, h->stream>>>(n, b, q, invd, h->mg_v0, done);
           MTO_TRY(mto_after_launch(h, "mg_block_resid_kernel"));
+          mg_zero_kernel<<<grd, 256, 0, h->stream>>>(n, q, done);
+          MTO_TRY(mto_after_launch(h, "mg_zero_kernel"));
         }
         MTO_TRY(apply_block(h, h->mg_v0, q, done));
       }
       TimedScope ts(h, F_PRECOND);
       const bool dot = with_dot && s == k - 1;
+      const bool sep = n >= kSeparateZero;
       mg_cheb_kernel<<<grd, 256, 0, h->stream>>>(n, b, q, invd, x, d, cf, s, pre && s == 0, done,
-                                                  dot ? dot_part : nullptr, dot_cnt, dot_res, block);
+                                                  dot ? dot_part : nullptr, dot_cnt, dot_res, block, !sep);
       MTO_TRY(mto_after_launch(h, "mg_cheb_kernel"));
+      if (sep) {
+        mg_zero_kernel<<<grd, 256, 0, h->stream>>>(n, q, done);
+        MTO_TRY(mto_after_launch(h, "mg_zero_kernel"));
+      }
     }
     return MTO_OK;
   };
