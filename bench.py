@@ -314,11 +314,13 @@ def timed_steps(run, prec, steps, warmup, advance, flush):
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed_step")     # for profiler filters (ncu --nvtx-include timed_step/)
         e0.record(run.stream)
         rho_in = run.rho
         it = run.step(prec, advance)
         e1.record(run.stream)
         e1.synchronize()
+        torch.cuda.nvtx.range_pop()
         total_ms += e0.elapsed_time(e1)
         iters += it
     launches = run.h.launch_count() - l0

@@ -116,9 +116,10 @@ typedef struct {
  *  mg_smoother MTO_PREC_MG only: the fine level's smoothing.  MTO_SMOOTH_JACOBI: Chebyshev
  *              polynomials of the point-Jacobi-scaled operator.  MTO_SMOOTH_BLOCK: of the
  *              operator scaled by the element-block inverse sum_e P_e^T (K_e + Delta_e)^-1 P_e (the
- *              blocks of MTO_PREC_SCHWARZ, which capture the element's own near-null modes; meshes
- *              with hanging nodes fall back to Jacobi); one more block apply per smoothing step, and
- *              on the 160 x 80 binary beam a third of the iterations.
+ *              blocks of MTO_PREC_SCHWARZ, which capture the element's own near-null modes); one
+ *              more block apply per smoothing step, and on the 160 x 80 binary beam a third of the
+ *              iterations.  The element blocks' output is masked to the free DOFs (a hanging DOF's
+ *              row scatters onto the nodes it interpolates, supported ones included).
  * CG iterations run in chunks of check_every (rounded up to a multiple of 4), each a CUDA graph;
  * the reported count stops at convergence, but a chunk already launched completes (cheaply). */
 typedef struct {

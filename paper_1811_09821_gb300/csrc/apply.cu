@@ -821,7 +821,9 @@ __global__ void __launch_bounds__(256) cg_direction_kernel(
   const double beta = s_beta;
   const T b = (T)beta;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-    const T zj = kJacobi ? invd[j] * r[j] : z[j];
+    // the element-block preconditioner scatters its hanging DOFs' rows onto the nodes they
+    // interpolate, supported ones included: z is masked to the free DOFs here
+    const T zj = kJacobi ? invd[j] * r[j] : (invd[j] != (T)0 ? z[j] : (T)0);
     p[j] = fma(b, p[j], zj);
   }
 }
@@ -857,10 +859,12 @@ __global__ void __launch_bounds__(256) zero_kernel(int64_t n, T* __restrict__ v,
     v[j] = (T)0;
 }
 
+// b = a on free DOFs (invd != 0), 0 on supported ones
 template <typename T>
-__global__ void __launch_bounds__(256) copy_kernel(int64_t n, const T* __restrict__ a, T* __restrict__ b) {
+__global__ void __launch_bounds__(256) masked_copy_kernel(int64_t n, const T* __restrict__ a, T* __restrict__ b,
+                                                          const T* __restrict__ invd) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-    b[j] = a[j];
+    b[j] = invd[j] != (T)0 ? a[j] : (T)0;
 }
 
 __global__ void add2_kernel(const double* a, const double* b, double* out) {
@@ -1106,8 +1110,8 @@ mto_status cg_prepare(mto_handle h, CGRun<T>& run, T* x, T* r, int pc, int deg, 
   if (schwarz) {
     MTO_TRY(precond_step<T>(h, v, pc, deg, kGam, nullptr));
     TimedScope ts(h, F_VECTOR);
-    copy_kernel<T><<<kVecBlocks, 256, 0, h->stream>>>(n, v.z, v.p);
-    MTO_TRY(mto_after_launch(h, "copy_kernel"));
+    masked_copy_kernel<T><<<kVecBlocks, 256, 0, h->stream>>>(n, v.z, v.p, v.invd);
+    MTO_TRY(mto_after_launch(h, "masked_copy_kernel"));
   }
   if (!h->use_graphs) return MTO_OK;
   GraphKey key{sizeof(T), (const void*)x, (const void*)r, pc, deg, nrm, ref, tol2, chunk,
@@ -1364,10 +1368,6 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
   const int pc = o->precond;
   const int deg = o->mg_degree > 0 ? o->mg_degree : 4;
   if (deg > 16) return mto_fail(h, MTO_EINVAL, "mto_solve: mg_degree above 16");
-  if (pc == MTO_PREC_SCHWARZ && h->n_cons > 0)
-    return mto_fail(h, MTO_EINVAL,
-                    "mto_solve: the element-block Schwarz preconditioner is limited to meshes without order "
-                    "jumps (hanging nodes); use MTO_PREC_MG or MTO_PREC_JACOBI");
   if (pc == MTO_PREC_SCHWARZ && !h->schwarz_valid) MTO_TRY(build_schwarz(h));
   if (pc == MTO_PREC_MG) {
     if (o->precision == MTO_MIXED32)
@@ -1600,8 +1600,6 @@ mto_status solve_batched(mto_handle* hs, int n, const double* const* f, double* 
     j.itol = o->inner_rtol > 0 ? o->inner_rtol : 1e-6;
     mto_status st = MTO_OK;
     if (j.deg > 16) st = mto_fail(h, MTO_EINVAL, "mto_solve_batched: mg_degree above 16");
-    else if (j.pc == MTO_PREC_SCHWARZ && h->n_cons > 0)
-      st = mto_fail(h, MTO_EINVAL, "mto_solve_batched: element-block Schwarz is limited to meshes without order jumps");
     if (st == MTO_OK && j.pc == MTO_PREC_SCHWARZ && !h->schwarz_valid) st = build_schwarz(h);
     if (st == MTO_OK && j.pc == MTO_PREC_MG) st = mg_select_smoother(h, o->mg_smoother);
     if (st == MTO_OK && j.pc == MTO_PREC_MG && !h->mg_valid) st = mg_build(h);

@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(256) mg_cheb_kernel(int64_t n, const double* _
     const double bi = b[i];
     // given: q already holds the preconditioned residual (element-block smoothing), else the
     // Jacobi-scaled residual is formed here from q = A x
-    const double r = given ? q[i] : invd[i] * (bi - q[i]);
+    const double r = given ? (invd[i] != 0.0 ? q[i] : 0.0) : invd[i] * (bi - q[i]);
     if (zq) q[i] = 0.0;   // else a separate launch clears q (see mg_zero_kernel)
     const double dn = step > 0 ? fma(c1, d[i], c2 * r) : c2 * r;   // c1 = 0 at step 0
     d[i] = dn;
@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(256) mg_pow_step_kernel(int64_t n, double* __r
                                                           double* __restrict__ res, int given) {
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double wi = given ? q[i] : invd[i] * q[i];
+    const double wi = given ? (invd[i] != 0.0 ? q[i] : 0.0) : invd[i] * q[i];
     q[i] = 0.0;
     w[i] = wi;
     s += wi * wi;
@@ -794,8 +794,8 @@ mto_status mg_build(mto_handle h) {
   }
   }
   // element-block smoothing of the fine level: the blocks (K_e + Delta_e)^-1 of the element-block
-  // preconditioner (not on meshes with hanging nodes, where those blocks are not used)
-  h->mg_block = h->mg_smoother == 1 && h->n_cons == 0;
+  // preconditioner
+  h->mg_block = h->mg_smoother == 1;
   if (h->mg_block && !h->schwarz_valid) MTO_TRY(build_schwarz(h));
   // Chebyshev bounds: fine level first, then every smoothed Q1 level
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->mg_q0, 0, h->ndof * sizeof(double), h->stream), "memset"));

@@ -218,12 +218,11 @@ PATHS = {"fp64": ("MTO_FP64", "MTO_FP64"), "mixed": ("MTO_MIXED", "MTO_MIXED"),
 @pytest.mark.parametrize("path", ["fp64", "mixed", "mixed32"])
 @pytest.mark.parametrize("name", CASES)
 def test_solve_and_sensitivity_parity(mto, name, path, precond):
-    """mgblock: multigrid with element-block smoothing of the fine level (on the order-jump dp mesh
-    the solver falls back to Jacobi smoothing)."""
+    """schwarz: the element-block preconditioner; mgblock: multigrid with element-block smoothing of
+    the fine level.  Both on the order-jump dp mesh too (hanging DOFs: the block output is masked to
+    the free DOFs)."""
     if path == "mixed32" and (name != "cantilever_20x10_p2_d4" or precond != "schwarz"):
         pytest.skip("FP32-vector inner solves are checked on the smooth-density case (Schwarz)")
-    if precond == "schwarz" and name.startswith("dp_"):
-        pytest.skip("the element-block Schwarz preconditioner is refused on meshes with order jumps")
     o = oracle_results(name)
     pr = o["pr"]
     build, sprec = (getattr(mto, k) for k in PATHS[path])
@@ -252,8 +251,8 @@ def test_solve_and_sensitivity_parity(mto, name, path, precond):
 def test_multigrid_iterations_and_limits(mto):
     """The multigrid cycle is a strong preconditioner (several times fewer iterations than point
     Jacobi on the dp case), works when the Q1 grid of the mesh is itself the coarsest, and is
-    refused (not faked) on meshes that do not halve to a small coarsest grid; the element-block
-    Schwarz preconditioner is refused on meshes with order jumps."""
+    refused (not faked) on meshes that do not halve to a small coarsest grid; the element blocks
+    (preconditioner and smoother) work on the mesh with order jumps."""
     pr = W.named("dp_cantilever_40x20")
     h, fixed, f, mat, rho = gpu_setup(mto, pr)
     h.build_elements(rho, mat, mto.MTO_FP64)
@@ -262,10 +261,11 @@ def test_multigrid_iterations_and_limits(mto):
         u = torch.zeros(h.ndof, dtype=torch.float64, device="cuda")
         its[pc], _ = h.solve(f, u, rtol=1e-8, max_iter=400000, precond=pc, check_every=8)
     assert its[mto.PREC_MG] * 4 < its[mto.PREC_JACOBI], its
-    u = torch.zeros(h.ndof, dtype=torch.float64, device="cuda")
-    with pytest.raises(mto.MTOError) as ei:
-        h.solve(f, u, precond=mto.PREC_SCHWARZ)
-    assert ei.value.status == 1 and "order" in str(ei.value)
+    # element blocks on this order-jump mesh: as a preconditioner, and as the multigrid smoother
+    for pc, sm in ((mto.PREC_SCHWARZ, mto.SMOOTH_JACOBI), (mto.PREC_MG, mto.SMOOTH_BLOCK)):
+        u = torch.zeros(h.ndof, dtype=torch.float64, device="cuda")
+        it, _ = h.solve(f, u, rtol=1e-8, max_iter=400000, precond=pc, mg_smoother=sm, check_every=8)
+        assert it < its[mto.PREC_JACOBI], (pc, sm, it)
     h.close()
     # 8 x 4 Q2: the Q1 grid (90 DOFs) is the coarsest level
     nel = 32
