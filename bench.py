@@ -62,6 +62,9 @@ def parse(argv=None):
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--only-timed", action="store_true",
+                    help="stop after the timed steps (no FP64 leg, end-to-end leg, accuracy check or CPU "
+                         "baseline; for profiler captures of the timed region)")
     return ap.parse_args(argv)
 
 
@@ -373,6 +376,11 @@ def run_gpu(args, rank, world, local_rank):
         dist.barrier()
     mixed_ms_max = max_over_ranks(mixed["ms"], world, dev)
     steps = args.steps
+    if args.only_timed:
+        run.h.close()
+        return {"metric": METRIC, "value": whole_job_rate(world, steps, mixed_ms_max), "unit": UNIT,
+                "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": mixed_ms_max / steps,
+                "higher_is_better": True, "config": {"workload": args.workload, "note": "timed steps only"}}
 
     # end to end through the public API with host buffers: design and load in, displacement and
     # sensitivities out, every step (the mixed path, continuing the same run)
@@ -598,7 +606,7 @@ def main(argv=None):
         dist.init_process_group("nccl")
     out = run_batched(args, rank, world, local_rank) if batched else run_gpu(args, rank, world, local_rank)
     if rank == 0:
-        if not args.no_cpu and not batched:
+        if not args.no_cpu and not batched and not args.only_timed:
             try:
                 out["cpu_baseline"] = cpu_baseline(args.workload)
             except Exception as ex:      # the oracle is only a reported baseline

@@ -191,6 +191,69 @@ __global__ void __launch_bounds__(128) mg_galerkin_h_kernel(int nxc, int nyc, in
     }
 }
 
+// The assembled operator of a Q1 level as a stencil per vertex, from the element matrices: vertex
+// v = (i, j) couples with the vertices (i + di, j + dj), di, dj in {-1, 0, 1} (offset o =
+// 3 (dj + 1) + di + 1), through a 2 x 2 block per offset.  One thread per vertex gathers the
+// contributions of its (up to four) elements in a fixed order, so no atomics; the stencil is
+// stored offset-major ([36][nv]) for coalesced reads in the apply.
+__global__ void __launch_bounds__(256) mg_stencil_kernel(int nx, int ny, const double* __restrict__ K,
+                                                         double* __restrict__ S) {
+  const int64_t nv = (int64_t)(nx + 1) * (ny + 1);
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(v % (nx + 1)), j = (int)(v / (nx + 1));
+    double acc[36];
+#pragma unroll
+    for (int k = 0; k < 36; ++k) acc[k] = 0.0;
+    for (int ey = j - 1; ey <= j; ++ey) {
+      if (ey < 0 || ey >= ny) continue;
+      for (int ex = i - 1; ex <= i; ++ex) {
+        if (ex < 0 || ex >= nx) continue;
+        const double* ke = K + (size_t)(ey * nx + ex) * 40;
+        const int a = (i - ex) + 2 * (j - ey);   // local vertex of v (x fastest)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int o = 3 * (ey + (b >> 1) - j + 1) + (ex + (b & 1) - i + 1);
+#pragma unroll
+          for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int c2 = 0; c2 < 2; ++c2) acc[o * 4 + 2 * c + c2] += ke[circ_pos(2 * a + c, 2 * b + c2, 8)];
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 36; ++k) S[(size_t)k * nv + v] = acc[k];
+  }
+}
+
+// y = A x on a Q1 level by its vertex stencil (gather only; every DOF, supported ones included)
+__global__ void __launch_bounds__(256) mg_stencil_apply_kernel(int nx, int ny, const double* __restrict__ S,
+                                                               const double* __restrict__ x, double* __restrict__ y,
+                                                               const int* __restrict__ done) {
+  if (done && *done) return;
+  const int64_t nv = (int64_t)(nx + 1) * (ny + 1);
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(v % (nx + 1)), j = (int)(v / (nx + 1));
+    double y0 = 0.0, y1 = 0.0;
+#pragma unroll
+    for (int dj = -1; dj <= 1; ++dj) {
+#pragma unroll
+      for (int di = -1; di <= 1; ++di) {
+        const int ii = i + di, jj = j + dj;
+        if (ii < 0 || ii > nx || jj < 0 || jj > ny) continue;
+        const int o = 3 * (dj + 1) + di + 1;
+        const size_t w = 2 * ((size_t)jj * (nx + 1) + ii);
+        const double x0 = x[w], x1 = x[w + 1];
+        y0 = fma(S[(size_t)(o * 4 + 0) * nv + v], x0, y0);
+        y0 = fma(S[(size_t)(o * 4 + 1) * nv + v], x1, y0);
+        y1 = fma(S[(size_t)(o * 4 + 2) * nv + v], x0, y1);
+        y1 = fma(S[(size_t)(o * 4 + 3) * nv + v], x1, y1);
+      }
+    }
+    y[2 * v] = y0;
+    y[2 * v + 1] = y1;
+  }
+}
+
 // assembled diagonal of a Q1 level (atomics), then the masked inverse
 __global__ void mg_diag_kernel(int nel, const int* __restrict__ gmap, const double* __restrict__ K,
                                double* __restrict__ diag) {
@@ -513,8 +576,8 @@ int vec_grid(int64_t n) { return grid_for(n, 256, kMGBlocks); }
 // ---------------------------------------------------------------- host side
 void mg_release(mto_handle h) {
   for (auto& l : h->mg)
-    for (void* p : {(void*)l.gmap, (void*)l.K, (void*)l.mask, (void*)l.invd, (void*)l.x, (void*)l.b, (void*)l.q,
-                    (void*)l.d})
+    for (void* p : {(void*)l.gmap, (void*)l.K, (void*)l.S, (void*)l.mask, (void*)l.invd, (void*)l.x, (void*)l.b,
+                    (void*)l.q, (void*)l.d})
       cudaFree(p);
   h->mg.clear();
   for (void* p : {(void*)h->mg_pidx, (void*)h->mg_pw, (void*)h->mg_rptr, (void*)h->mg_rnode, (void*)h->mg_rw,
@@ -568,6 +631,7 @@ mto_status mg_setup(mto_handle h) {
     MTO_TRY(mto_alloc(h, &L.gmap, gm.size()));
     MTO_TRY(mto_cuda_check(h, cudaMemcpy(L.gmap, gm.data(), gm.size() * sizeof(int), cudaMemcpyHostToDevice), "upload"));
     MTO_TRY(mto_alloc(h, &L.K, (size_t)40 * L.nel));
+    if (l + 1 < dims.size()) MTO_TRY(mto_alloc(h, &L.S, (size_t)36 * L.nv));   // smoothed levels
     for (double** v : {&L.mask, &L.invd, &L.x, &L.b, &L.q, &L.d}) MTO_TRY(mto_alloc(h, v, L.n));
     MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(L.q, 0, L.n * sizeof(double), h->stream), "memset"));
   }
@@ -703,7 +767,7 @@ mto_status mg_power(mto_handle h, int level, double* lmax_out) {
   const bool block = fine && h->mg_block;   // lmax of M^-1 A, M^-1 the element-block inverse
   for (int it = 0; it < kPowerIts; ++it) {
     if (fine) MTO_TRY(apply_fine(h, v, q, nullptr));
-    else MTO_TRY(apply_q1(h, h->mg[level], v, q, nullptr));
+    else MTO_TRY(mg_apply_level(h, h->mg[level], v, q, nullptr));
     if (block) {
       mg_block_resid_kernel<<<grd, 256, 0, h->stream>>>(n, nullptr, q, invd, w, nullptr);   // w = -A v
       MTO_TRY(mto_after_launch(h, "mg_block_resid_kernel"));
@@ -767,6 +831,10 @@ mto_status mg_build(mto_handle h) {
     MTO_TRY(mto_after_launch(h, "mg_galerkin_h_kernel"));
   }
   for (auto& L : h->mg) {
+    if (L.S) {
+      mg_stencil_kernel<<<vec_grid(L.nv), 256, 0, h->stream>>>(L.nx, L.ny, L.K, L.S);
+      MTO_TRY(mto_after_launch(h, "mg_stencil_kernel"));
+    }
     MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(L.invd, 0, L.n * sizeof(double), h->stream), "memset"));
     mg_diag_kernel<<<(L.nel + 127) / 128, 128, 0, h->stream>>>(L.nel, L.gmap, L.K, L.invd);
     MTO_TRY(mto_after_launch(h, "mg_diag_kernel"));
@@ -834,7 +902,7 @@ mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const
         if (lev < 0) MTO_TRY(apply_fine(h, x, q, done));
         else {
           TimedScope ts(h, F_PRECOND);
-          MTO_TRY(apply_q1(h, h->mg[lev], x, q, done));
+          MTO_TRY(mg_apply_level(h, h->mg[lev], x, q, done));
         }
       }
       if (block) {   // q <- M^-1 (b - A x)
@@ -876,7 +944,7 @@ mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const
     MGLevel& C = h->mg[l + 1];
     MTO_TRY(smooth(l, L.b, L.x, L.q, L.d, L.invd, L.n, true, false));
     TimedScope ts(h, F_PRECOND);
-    MTO_TRY(apply_q1(h, L, L.x, L.q, done));
+    MTO_TRY(mg_apply_level(h, L, L.x, L.q, done));
     mg_restrict_h_kernel<<<vec_grid(C.nv), 256, 0, h->stream>>>(C.nx, C.ny, L.nx, L.ny, L.b, L.q, L.invd, C.mask,
                                                                 C.b, done);
     MTO_TRY(mto_after_launch(h, "mg_restrict_h_kernel"));
@@ -906,6 +974,14 @@ mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const
     MTO_TRY(mto_after_launch(h, "mg_prolong0_kernel"));
   }
   return smooth(-1, r, z, h->mg_q0, h->mg_d0, h->invd64, h->ndof, false, true);
+}
+
+// y = A x on Q1 level l (y is written, not accumulated): the vertex stencil where it exists (the
+// smoothed levels), else the element matrices
+mto_status mg_apply_level(mto_handle h, const MGLevel& l, const double* x, double* y, const int* done) {
+  if (!l.S) return apply_q1(h, l, x, y, done);
+  mg_stencil_apply_kernel<<<vec_grid(l.nv), 256, 0, h->stream>>>(l.nx, l.ny, l.S, x, y, done);
+  return mto_after_launch(h, "mg_stencil_apply_kernel");
 }
 
 }  // namespace mto

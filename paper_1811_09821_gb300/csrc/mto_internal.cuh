@@ -99,6 +99,8 @@ struct MGLevel {
   int64_t nv = 0, n = 0;           // vertices, DOFs
   int* gmap = nullptr;             // [nel][4] vertex ids (x fastest)
   double* K = nullptr;             // [nel][40]
+  double* S = nullptr;             // [36][nv] the assembled operator as a vertex stencil: entry
+                                   // (o * 4 + 2 c + c') of vertex v couples (v, c) with (v + offset o, c')
   double* mask = nullptr;          // [n] 0 on supported DOFs, else 1
   double* invd = nullptr;          // [n] inverse diagonal, 0 on supported DOFs
   double *x = nullptr, *b = nullptr, *q = nullptr, *d = nullptr;   // [n] cycle vectors
@@ -432,6 +434,7 @@ mto_status mg_setup(mto_handle h);                                      // hiera
 mto_status mg_set_masks(mto_handle h);                                  // supports on every level
 mto_status mg_build(mto_handle h);                                      // Galerkin operators, bounds
 mto_status mg_select_smoother(mto_handle h, int smoother);              // MTO_SMOOTH_* for next solves
+mto_status mg_apply_level(mto_handle h, const MGLevel& l, const double* x, double* y, const int* done);
 mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const int* done, double* dot_part,
                      unsigned* dot_cnt, double* dot_res);
 void mg_release(mto_handle h);
