@@ -59,9 +59,14 @@ def parse(argv=None):
     ap.add_argument("--mg-degree", type=int, default=2, help="Chebyshev degree of the fine-level smoothing")
     ap.add_argument("--smoother", default="block", choices=["block", "jacobi"],
                     help="fine-level smoothing: element blocks (default) or point Jacobi")
+    ap.add_argument("--build", default="tensor", choices=["tensor", "simt"],
+                    help="element build: tcgen05 sliced GEMM (default) or FP64 CUDA cores")
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--max-iters", type=int, default=400000,
+                    help="cap on the PCG iterations of a solve (profiler captures of a few iterations only; "
+                         "a capped solve is not a bench number)")
     ap.add_argument("--only-timed", action="store_true",
                     help="stop after the timed steps (no FP64 leg, end-to-end leg, accuracy check or CPU "
                          "baseline; for profiler captures of the timed region)")
@@ -242,6 +247,12 @@ def whole_job_rate(world, steps, max_ms):
     return world * steps / (max_ms * 1e-3)
 
 
+# DRAM bytes (read + write) of one launch of ebe_df_tma_kernel<3,double>, from an ncu capture of the
+# 480 x 240 beam's operator (115,200 Q3 elements; profiles/ebe_df_tma_kernel_mbb480x240.md), per
+# element; the kernel has not changed since.  Scaled to a launch by the elements it processes.
+TMA_TRAFFIC_PER_ELEMENT = (542046208 + 15458560) / 115200
+
+
 def smoother_of(args):
     import paper_1811_09821_gb300 as mto
     return mto.SMOOTH_BLOCK if args.smoother == "block" else mto.SMOOTH_JACOBI
@@ -265,6 +276,7 @@ class Run:
         self.pr, self.dev, self.stream = pr, dev, stream
         self.h = mto.Handle(local_rank, stream=stream)
         self.ndof, self.dlen = self.h.setup(pr.nelx, pr.nely, pr.p, pr.d)
+        self.h.set_build_path(mto.BUILD_TENSOR if args.build == "tensor" else mto.BUILD_SIMT)
         self.fixed, self.f = mto.load_case(self.h, pr.load)
         self.h.set_supports(self.fixed)
         self.nfree = self.ndof - len(self.fixed)
@@ -288,8 +300,9 @@ class Run:
         mto, h = self.mto, self.h
         h.build_elements(self.rho, self.mat, prec)
         it, rr = h.solve(self.f, self.u, precision=prec, rtol=self.args.rtol, norm=mto.NORM_ENERGY,
-                         max_iter=400000, check_every=32, precond=mto.PREC_MG, mg_degree=self.args.mg_degree,
-                         mg_smoother=smoother_of(self.args), warm_start=advance and self.k > 0)
+                         max_iter=self.args.max_iters, check_every=32, precond=mto.PREC_MG,
+                         mg_degree=self.args.mg_degree, mg_smoother=smoother_of(self.args),
+                         warm_start=advance and self.k > 0, raise_on_noconv=self.args.max_iters >= 400000)
         h.sensitivity(self.u, self.f, self.rho, self.mat, self.dc, precision=mto.MTO_FP64, want_C=False)
         h.indicator(self.u, self.rho, self.mat)
         h.oc_update(self.rho, self.dc, self.vol, self.rho_new, want_lambda=False)
@@ -382,6 +395,13 @@ def run_gpu(args, rank, world, local_rank):
                 "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": mixed_ms_max / steps,
                 "higher_is_better": True, "config": {"workload": args.workload, "note": "timed steps only"}}
 
+    # where one step's device time goes (one more step with every kernel family bracketed by events;
+    # outside the timed region, since the events add overhead)
+    run.h.timing_enable(True)
+    run.step(mto.MTO_MIXED, advance)
+    breakdown = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in run.h.timing_read().items() if v[0]}
+    run.h.timing_enable(False)
+
     # end to end through the public API with host buffers: design and load in, displacement and
     # sensitivities out, every step (the mixed path, continuing the same run)
     rho_h = run.rho.cpu().pin_memory()
@@ -446,6 +466,7 @@ def run_gpu(args, rank, world, local_rank):
                                                "one pass over the fixed design from a zero start"),
                    "solve_accuracy": f"relative compliance error {args.rtol:g} (energy test)",
                    "precond": f"multigrid, {args.smoother} smoothing of degree {args.mg_degree} on the fine level",
+                   "element_build": "tcgen05 sliced GEMM" if args.build == "tensor" else "FP64 CUDA cores",
                    "l2_flush": "512 MB write before each timed step",
                    "parallelism": f"replicas x{world}"},
         "mdof_pcg_iter_per_s": run.nfree * mixed["iters"] / (mixed["ms"] * 1e-3) / 1e6,
@@ -455,12 +476,15 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": mixed["launches"],
         "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if (achieved and hbm) else None,
-                     "traffic": None,
-                     "traffic_note": "DRAM bytes per launch are taken by ncu and summarised under profiles/ "
-                                     "(not measured inside this run)",
+                     "traffic": TMA_TRAFFIC_PER_ELEMENT * len(pr.p) if big else None,
+                     "traffic_note": ("stored ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of "
+                                      "ebe_df_tma_kernel<3,double> on the 480x240 beam, 115,200 elements), scaled "
+                                      "by elements to this launch; not measured in this run"
+                                      if big else "no stored capture for this kernel on this workload"),
                      "peak_note": "measured HBM copy of MEASURED_PEAKS.json" if hbm else "no measured peak file",
                      "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_ms * 1e3},
         "accuracy": checks,
+        "step_breakdown_ms": breakdown,
         "clocks": clk.summary(),
         "e2e": {"value": world * e2e_steps / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * (run.dlen + run.ndof),

@@ -433,7 +433,8 @@ mto_status mto_oc_update(mto_handle h, const double* rho, const double* dc, doub
 #define MTO_TIME_INDICATOR 4 /* step (d): indicators and map update */
 #define MTO_TIME_VECTOR 5    /* PCG vector updates, residuals, precision conversions */
 #define MTO_TIME_APPLYDF64 6 /* split-precision operator on FP64 vectors (refinement residuals) */
-#define MTO_TIME_PRECOND 7   /* element-block preconditioner applications and set-up */
+#define MTO_TIME_PRECOND 7   /* preconditioner: multigrid cycle, element blocks, their set-up */
+#define MTO_TIME_OC 8        /* optimality-criteria update */
 mto_status mto_timing_enable(mto_handle h, int32_t enable);
 mto_status mto_timing_read(mto_handle h, int32_t family, int64_t* launches, double* total_ms);
 

@@ -751,7 +751,7 @@ mto_status indicators(mto_handle h, const double* u, const double* rho, const mt
 
 mto_status oc_update(mto_handle h, const double* rho, const double* dc, double volfrac, double move, double eta,
                      double* rho_new, double* lambda) {
-  TimedScope ts(h, F_INDICATOR);
+  TimedScope ts(h, F_OC);
   const int64_t nel = h->nel;
   double* lam = h->red + 16;       // [l1, l2]
   int* done = h->flags + 8;

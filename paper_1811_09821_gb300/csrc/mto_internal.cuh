@@ -77,7 +77,7 @@ struct QRTab {
 
 // Kernel families timed with CUDA events when timing is enabled (see mto_timing_enable).
 enum Family { F_APPLY32 = 0, F_APPLY64 = 1, F_BUILD = 2, F_SENS = 3, F_INDICATOR = 4, F_VECTOR = 5,
-              F_APPLYDF64 = 6, F_PRECOND = 7, F_COUNT = 8 };
+              F_APPLYDF64 = 6, F_PRECOND = 7, F_OC = 8, F_COUNT = 9 };
 
 struct Timing {
   bool on = false;

@@ -3,24 +3,24 @@
 //   C[e][pos] = sum_s E[e][s] * K0[c(pos)][s],
 // M = elements, N = positions of the circulant-diagonal element row, K = subcells.
 //
-// The split-precision element matrices need ~48 significant bits, so the products cannot be
-// plain BF16 products.  The GEMM is made exact by slicing (an Ozaki-type error-free splitting):
-// each element's moduli row is scaled by a power of two sigma_e (max E <= sigma_e) and each K0
-// column by a power of two tau_pos, and both are cut into 7 slices of 7 bits, E/sigma =
-// sum_i a_i 2^-7i and K0/tau = sum_j b_j 2^-7j with integer a_i in [0, 127], b_j in [-127, 127]
-// (exact in BF16).  Every slice product a_i . b_j over K <= 64 subcells is an integer below 2^20,
-// and all pairs of one level g = i + j share the weight 2^-7g: each level accumulates its (at most
-// 7) slice GEMMs in one FP32 TMEM accumulator exactly (sums below 2^23).  Levels g = 2..9 are
-// kept (the dropped levels weigh below 2^-47 of the row/column scale); the epilogue adds the
-// levels from the smallest with FP32 TwoSum into a hi/lo pair (FP32 pipes), rescales by
-// sigma_e tau_pos (powers of two, exact) and stores hi + lo as the FP64 matrix and, for the
-// mixed build, the pair itself.
+// The element matrices need FP64 accuracy (on the binary designs a relative error of 1e-13 in K_e
+// moves the compliance by ~1e-6), so the products cannot be plain BF16 products.  The GEMM is made
+// exact by slicing (an Ozaki-type error-free splitting): each element's moduli row is scaled by a
+// power of two sigma_e (max E <= sigma_e) and each K0 column by a power of two tau_pos, and both
+// are cut into 8 slices of 7 bits (56 bits), E/sigma = sum_i a_i 2^-7i and K0/tau = sum_j b_j 2^-7j
+// with integer a_i in [0, 127], b_j in [-127, 127] (exact in BF16).  Every slice product a_i . b_j
+// over K <= 64 subcells is an integer below 2^20, and all pairs of one level g = i + j share the
+// weight 2^-7g: each level accumulates its (at most 8) slice GEMMs in one FP32 TMEM accumulator
+// exactly (sums below 2^23).  Levels g = 2..10 are kept (the dropped levels weigh below 2^-51 of
+// the row/column scale, the operands' truncation 2^-56); the epilogue adds the levels in FP64,
+// rescales by sigma_e tau_pos (powers of two, exact) and stores the FP64 matrix and, for the mixed
+// build, its split pair.
 //
-// One CTA (4 warps) per 128 elements: the A slices (7 x 128 x K) are formed in shared memory from
-// rho once; the CTA then walks the N tiles of 64 positions: B slices copied to shared memory, one
-// thread issues the 34 x (K/16) tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = 128, N = 64)
-// into 8 level accumulators (all 512 TMEM columns), commits to an mbarrier, and all threads read
-// their row back with tcgen05.ld and store 64 consecutive entries of their element's row.
+// One CTA (4 warps) per 128 elements: the A slices (8 x 128 x K) are formed in shared memory from
+// rho once; the CTA then walks the N tiles of 32 positions: B slices copied to shared memory, one
+// thread issues the 43 x (K/16) tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = 128, N = 32)
+// into 9 level accumulators (288 TMEM columns), commits to an mbarrier, and all threads read
+// their row back with tcgen05.ld and store 32 consecutive entries of their element's row.
 // Operands use the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix).
 // Every wait is bounded: on expiry the kernel records an error word and skips the tile.
 #include <cstdio>
@@ -32,11 +32,12 @@ namespace mto {
 namespace {
 
 constexpr int kTM = 128;        // elements per CTA (MMA M)
-constexpr int kTN = 64;         // positions per N tile (MMA N)
-constexpr int kSlices = 7;      // slices per operand
+constexpr int kTN = 32;         // positions per N tile (MMA N)
+constexpr int kSlices = 8;      // slices per operand (8 x 7 = 56 bits)
 constexpr int kSliceBits = 7;
-constexpr int kLevels = 8;      // levels g = i + j = 2..9
-constexpr int kTmemCols = 512;  // 8 x 64 = 512 used
+constexpr int kOpBits = kSlices * kSliceBits;
+constexpr int kLevels = 9;      // levels g = i + j = 2..10
+constexpr int kTmemCols = 512;  // 9 x 32 = 288 used (allocations are powers of two)
 constexpr unsigned kSpinLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -121,14 +122,6 @@ __host__ __device__ __forceinline__ uint32_t core_off(int row, int k, int kpad) 
   return (uint32_t)(((row >> 3) * (kpad >> 3) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
-__device__ __forceinline__ void two_sum(float& sh, float& sl, float t) {
-  const float s = sh + t;
-  const float bv = s - sh;
-  const float err = (sh - (s - bv)) + (t - bv);
-  sh = s;
-  sl += err;
-}
-
 // B operand tables of a class: per N tile, 7 slices of kTN x kpad BF16 in the core layout, and
 // the column scales tau (power of two) per position.  One thread per (position, subcell).
 __global__ void tc_btable_kernel(int S, int kpad, int L, int ntile, const double* __restrict__ K0T,
@@ -153,9 +146,9 @@ __global__ void tc_btable_kernel(int S, int kpad, int L, int ntile, const double
   for (int s = threadIdx.x; s < kpad; s += blockDim.x) {
     const double w = (c >= 0 && s < S) ? K0T[(size_t)c * S + s] * sc : 0.0;   // |w| < 1
     const double aw = fabs(w);
-    const unsigned long long W = (unsigned long long)(aw * 562949953421312.0);   // floor(|w| 2^49)
+    const unsigned long long W = (unsigned long long)ldexp(aw, kOpBits);   // floor(|w| 2^56)
     for (int j = 0; j < kSlices; ++j) {
-      const int bits = (int)((W >> (49 - kSliceBits * (j + 1))) & 127ull);
+      const int bits = (int)((W >> (kOpBits - kSliceBits * (j + 1))) & 127ull);
       const float v = (w < 0.0 ? -1.0f : 1.0f) * (float)bits;
       const unsigned short b = (unsigned short)(__float_as_uint(v) >> 16);   // exact: |v| <= 127
       unsigned char* base = reinterpret_cast<unsigned char*>(Bt) +
@@ -212,9 +205,9 @@ __global__ void __launch_bounds__(128, 1) tc_build_kernel(
     for (int s = 0; s < kpad; ++s) {
       double v = 0.0;
       if (act && s < S) v = modulus(rho[off + s]) * sc;   // [0, 1)
-      const unsigned long long V = (unsigned long long)(v * 562949953421312.0);
+      const unsigned long long V = (unsigned long long)ldexp(v, kOpBits);   // floor(v 2^56)
       for (int i = 0; i < kSlices; ++i) {
-        const float a = (float)((V >> (49 - kSliceBits * (i + 1))) & 127ull);
+        const float a = (float)((V >> (kOpBits - kSliceBits * (i + 1))) & 127ull);
         const unsigned short b = (unsigned short)(__float_as_uint(a) >> 16);
         *reinterpret_cast<unsigned short*>(As + (size_t)i * kTM * kpad * 2 + core_off(t, s, kpad)) = b;
       }
@@ -276,24 +269,23 @@ __global__ void __launch_bounds__(128, 1) tc_build_kernel(
       if (t == 0) atomicExch(err, 1);
       break;   // the accumulators are not trustworthy: stop this CTA (the caller reports the error)
     }
-    // epilogue: this thread's TMEM lane = its row; 4 chunks of 16 positions
+    // epilogue: this thread's TMEM lane = its row; chunks of 16 positions.  Every level sum is an
+    // integer below 2^23 (exact in FP32); the levels are added from the smallest in FP64 (9 terms
+    // per entry), then scaled by sigma_e tau_pos (a power of two: exact)
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
     for (int ch = 0; ch < kTN / 16; ++ch) {
-      float sh[16], slo[16];
+      double acc[16];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        sh[c] = 0.0f;
-        slo[c] = 0.0f;
-      }
+      for (int c = 0; c < 16; ++c) acc[c] = 0.0;
 #pragma unroll 1
       for (int g = kLevels - 1; g >= 0; --g) {
         uint32_t v[16];
         tmem_ld16(lane_addr + (uint32_t)(g * kTN + ch * 16), v);
         tmem_wait_ld();
-        const float wgt = ldexpf(1.0f, -kSliceBits * (g + 2));
+        const double wgt = ldexp(1.0, -kSliceBits * (g + 2));
 #pragma unroll
-        for (int c = 0; c < 16; ++c) two_sum(sh[c], slo[c], __uint_as_float(v[c]) * wgt);   // exact terms
+        for (int c = 0; c < 16; ++c) acc[c] = fma((double)__uint_as_float(v[c]), wgt, acc[c]);
       }
       if (act) {
         const int pos0 = tile * kTN + ch * 16;
@@ -301,14 +293,13 @@ __global__ void __launch_bounds__(128, 1) tc_build_kernel(
         for (int c = 0; c < 16; ++c) {
           const int pos = pos0 + c;
           if (pos >= L) break;
-          const float sc = sig * __ldg(tau + pos);
-          const float hi = sh[c] + slo[c];
-          const float lo = slo[c] - (hi - sh[c]);
+          const double kv = acc[c] * ((double)sig * (double)__ldg(tau + pos));
           const size_t o = (size_t)sl * L + pos;
-          K64[o] = (double)(hi * sc) + (double)(lo * sc);
+          K64[o] = kv;
           if (Kh) {
-            Kh[o] = hi * sc;
-            Kl[o] = lo * sc;
+            const float hi = (float)kv;
+            Kh[o] = hi;
+            Kl[o] = (float)(kv - (double)hi);
           }
         }
       }
