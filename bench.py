@@ -59,6 +59,9 @@ def parse(argv=None):
     ap.add_argument("--mg-degree", type=int, default=2, help="Chebyshev degree of the fine-level smoothing")
     ap.add_argument("--smoother", default="block", choices=["block", "jacobi"],
                     help="fine-level smoothing: element blocks (default) or point Jacobi")
+    ap.add_argument("--mg-operator", default="lead", choices=["lead", "split"],
+                    help="element matrices inside the multigrid cycle of the mixed path: the FP32 leading part "
+                         "of the split pair (default) or the pair itself")
     ap.add_argument("--build", default="tensor", choices=["tensor", "simt"],
                     help="element build: tcgen05 sliced GEMM (default) or FP64 CUDA cores")
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 leg")
@@ -258,6 +261,11 @@ def smoother_of(args):
     return mto.SMOOTH_BLOCK if args.smoother == "block" else mto.SMOOTH_JACOBI
 
 
+def mg_operator_of(args):
+    import paper_1811_09821_gb300 as mto
+    return mto.MG_OP_LEAD if args.mg_operator == "lead" else mto.MG_OP_SPLIT
+
+
 def operator_bytes(pr, ndof):
     """Algorithmic bytes of one split-operator launch: per element the hi/lo pair of its matrix in
     the circulant-diagonal row ((n_e/2 + 1) n_e entries, 2 x 4 bytes) and its node map (4 bytes per
@@ -302,7 +310,7 @@ class Run:
         it, rr = h.solve(self.f, self.u, precision=prec, rtol=self.args.rtol, norm=mto.NORM_ENERGY,
                          max_iter=self.args.max_iters, check_every=32, precond=mto.PREC_MG,
                          mg_degree=self.args.mg_degree, mg_smoother=smoother_of(self.args),
-                         warm_start=advance and self.k > 0, raise_on_noconv=self.args.max_iters >= 400000)
+                         mg_operator=mg_operator_of(self.args), warm_start=advance and self.k > 0, raise_on_noconv=self.args.max_iters >= 400000)
         h.sensitivity(self.u, self.f, self.rho, self.mat, self.dc, precision=mto.MTO_FP64, want_C=False)
         h.indicator(self.u, self.rho, self.mat)
         h.oc_update(self.rho, self.dc, self.vol, self.rho_new, want_lambda=False)
@@ -465,7 +473,9 @@ def run_gpu(args, rank, world, local_rank):
                                                "its first iterations" if advance else
                                                "one pass over the fixed design from a zero start"),
                    "solve_accuracy": f"relative compliance error {args.rtol:g} (energy test)",
-                   "precond": f"multigrid, {args.smoother} smoothing of degree {args.mg_degree} on the fine level",
+                   "precond": (f"multigrid, {args.smoother} smoothing of degree {args.mg_degree} on the fine level; "
+                               + ("cycle on the FP32 leading part of the split matrices" if args.mg_operator == "lead"
+                                  else "cycle on the split pair")),
                    "element_build": "tcgen05 sliced GEMM" if args.build == "tensor" else "FP64 CUDA cores",
                    "l2_flush": "512 MB write before each timed step",
                    "parallelism": f"replicas x{world}"},
@@ -540,7 +550,8 @@ def run_batched(args, rank, world, local_rank):
     def step(prec):
         mto.build_elements_batched(hs, rhos, mat, prec)
         its, _, _ = mto.solve_batched(hs, fs, us, precision=prec, rtol=args.rtol, norm=mto.NORM_ENERGY,
-                                      mg_degree=args.mg_degree, mg_smoother=smoother_of(args))
+                                      mg_degree=args.mg_degree, mg_smoother=smoother_of(args),
+                                      mg_operator=mg_operator_of(args))
         mto.sensitivity_batched(hs, us, fs, rhos, mat, dcs, want_C=False)
         torch.cuda.synchronize(dev)
         return int(its.sum())

@@ -120,6 +120,13 @@ typedef struct {
  *              more block apply per smoothing step, and on the 160 x 80 binary beam a third of the
  *              iterations.  The element blocks' output is masked to the free DOFs (a hanging DOF's
  *              row scatters onto the nodes it interpolates, supported ones included).
+ *  mg_operator MTO_PREC_MG with the MTO_MIXED build only: the copy of the matrices the cycle applies
+ *              (fine level: its smoothing steps, the restriction residual, the element blocks and the
+ *              power iteration of the Chebyshev bounds; Q1 levels: their vertex stencils).
+ *              MTO_MG_OP_AUTO (default) = MTO_MG_OP_LEAD: the FP32 leading part of the split pair and
+ *              the stencils rounded to FP32 (half the bytes; a preconditioner needs a fixed
+ *              operator, not the operator's accuracy: the outer PCG keeps the split pair and the
+ *              FP64 refinement).  MTO_MG_OP_SPLIT: the split pair and FP64 stencils.
  * CG iterations run in chunks of check_every (rounded up to a multiple of 4), each a CUDA graph;
  * the reported count stops at convergence, but a chunk already launched completes (cheaply). */
 typedef struct {
@@ -135,10 +142,14 @@ typedef struct {
   int32_t inner_max;
   int32_t mg_degree;
   int32_t mg_smoother;
+  int32_t mg_operator;
 } mto_solve_opts;
 
 #define MTO_SMOOTH_JACOBI 0
 #define MTO_SMOOTH_BLOCK 1
+#define MTO_MG_OP_AUTO 0
+#define MTO_MG_OP_SPLIT 1
+#define MTO_MG_OP_LEAD 2
 
 #define MTO_PREC_JACOBI 0
 #define MTO_PREC_SCHWARZ 1
@@ -258,10 +269,12 @@ mto_status mto_build_elements(mto_handle h, const double* rho, const mto_materia
 mto_status mto_element_matrix(mto_handle h, int64_t e, double* packed);
 
 /* Which kernel forms the element matrices in mto_build_elements:
- * MTO_BUILD_TENSOR: classes with d <= 8 run as one exact sliced GEMM per class on the tensor
- *   cores (tcgen05, BF16 slices, FP32 TMEM accumulators, ~48-bit result); larger d fall back to
- *   the FP64 CUDA-core kernel.
- * MTO_BUILD_SIMT (default): the FP64 CUDA-core kernel for every class. */
+ * MTO_BUILD_TENSOR (default): classes with d <= 8 run as one sliced GEMM per class on the tensor
+ *   cores (tcgen05: both operands cut into 8 BF16 slices of 7 bits with power-of-two scales, the
+ *   slice products summed exactly in FP32 TMEM columns by level, the levels combined in FP64:
+ *   agrees with the FP64 kernel to ~1e-15 of each element's largest entry); larger d use the FP64
+ *   CUDA-core kernel.
+ * MTO_BUILD_SIMT: the FP64 CUDA-core kernel for every class. */
 #define MTO_BUILD_TENSOR 0
 #define MTO_BUILD_SIMT 1
 mto_status mto_set_build_path(mto_handle h, int32_t path);
@@ -322,12 +335,17 @@ mto_status mto_apply(mto_handle h, const double* x, double* y);
 /* y = K x with a chosen operator (tests and tools), over all DOFs like mto_apply.  op:
  *   MTO_OP_FP64   the FP64 element matrices on the FP64 pipes (plain FP64 path, refinement residuals);
  *   MTO_OP_SPLIT  the split-precision pair on the FP32 pipes with FP64 vectors: exactly the kernels the
- *                 inner PCG of MTO_MIXED solves launches (needs the MTO_MIXED build).
+ *                 inner PCG of MTO_MIXED solves launches (needs the MTO_MIXED build);
+ *   MTO_OP_LEAD   the pair's FP32 leading part alone (the hi rows, x rounded to FP32, FP32 sums per
+ *                 element, FP64 assembly): the copy of the operator the multigrid cycle may apply
+ *                 where it only needs a fixed operator (see mg_lead of mto_solve_opts; MTO_MIXED
+ *                 build).  Entries differ from K by the FP32 rounding of the matrices.
  * x, y: device double[ndof].  *xKx (host, may be NULL: then asynchronous) receives x^T y as the
  * operator launches reduce it for CG (per order class, summed in class order).  Synchronises when
  * xKx is given. */
 #define MTO_OP_FP64 0
 #define MTO_OP_SPLIT 1
+#define MTO_OP_LEAD 2
 mto_status mto_apply_operator(mto_handle h, int32_t op, const double* x, double* y, double* xKx);
 
 /* Kernel of the split-precision operator for orders with n_e <= 32 (p <= 3); orders above always use

@@ -20,10 +20,11 @@ LIB_PATH = os.path.join(_HERE, "libmto.so")
 MTO_FP64, MTO_MIXED, MTO_MIXED32 = 0, 1, 2
 NORM_L2, NORM_JACOBI, NORM_ENERGY = 0, 1, 2
 BUILD_TENSOR, BUILD_SIMT = 0, 1
-OP_FP64, OP_SPLIT = 0, 1
+OP_FP64, OP_SPLIT, OP_LEAD = 0, 1, 2
 OPK_AUTO, OPK_PIPE, OPK_STAGED, OPK_GENERIC = -1, 0, 1, 2
 PREC_JACOBI, PREC_SCHWARZ, PREC_MG = 0, 1, 2
 SMOOTH_JACOBI, SMOOTH_BLOCK = 0, 1
+MG_OP_AUTO, MG_OP_SPLIT, MG_OP_LEAD = 0, 1, 2
 STATUS = {0: "MTO_OK", 1: "MTO_EINVAL", 2: "MTO_ENOMEM", 3: "MTO_ECUDA", 4: "MTO_ENOCONV", 5: "MTO_ENAN",
           6: "MTO_ETIMEOUT"}
 P_MAX, D_MAX = 6, 16
@@ -45,7 +46,8 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("rtol", ctypes.c_double), ("inner_rtol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("warm_start", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("norm", ctypes.c_int32), ("precond", ctypes.c_int32),
-                ("inner_max", ctypes.c_int32), ("mg_degree", ctypes.c_int32), ("mg_smoother", ctypes.c_int32)]
+                ("inner_max", ctypes.c_int32), ("mg_degree", ctypes.c_int32), ("mg_smoother", ctypes.c_int32),
+                ("mg_operator", ctypes.c_int32)]
 
 
 class IndicatorOpts(ctypes.Structure):
@@ -266,9 +268,9 @@ class Handle:
 
     def solve(self, f, u, precision=MTO_FP64, rtol=1e-8, inner_rtol=0.0, max_iter=200000, max_outer=50,
               warm_start=False, check_every=64, norm=NORM_L2, precond=PREC_SCHWARZ, inner_max=0,
-              mg_degree=0, mg_smoother=SMOOTH_JACOBI, raise_on_noconv=True):
+              mg_degree=0, mg_smoother=SMOOTH_JACOBI, mg_operator=MG_OP_AUTO, raise_on_noconv=True):
         o = SolveOpts(precision, rtol, inner_rtol, max_iter, max_outer, int(bool(warm_start)), check_every, norm,
-                      precond, inner_max, mg_degree, mg_smoother)
+                      precond, inner_max, mg_degree, mg_smoother, mg_operator)
         it, rr = ctypes.c_int32(), ctypes.c_double()
         st = self.L.mto_solve(self.h, _ptr(f, torch.float64), _ptr(u, torch.float64), ctypes.byref(o),
                               ctypes.byref(it), ctypes.byref(rr))
@@ -280,8 +282,9 @@ class Handle:
         self._check(self.L.mto_apply(self.h, _ptr(x, torch.float64), _ptr(y, torch.float64)))
 
     def apply_operator(self, x, y, op=OP_FP64, want_xKx=True):
-        """y = K x with the FP64 matrices (OP_FP64) or the split-precision pair (OP_SPLIT, the inner
-        PCG's kernels); returns x^T K x as the launches reduce it (or None)."""
+        """y = K x with the FP64 matrices (OP_FP64), the split-precision pair (OP_SPLIT, the inner
+        PCG's kernels) or the pair's FP32 leading part (OP_LEAD, the multigrid cycle's copy); returns
+        x^T K x as the launches reduce it (or None)."""
         v = ctypes.c_double()
         self._check(self.L.mto_apply_operator(self.h, op, _ptr(x, torch.float64), _ptr(y, torch.float64),
                                               ctypes.byref(v) if want_xKx else None))
@@ -464,13 +467,13 @@ def build_elements_batched(handles, rhos, mat, precision=MTO_MIXED):
 
 def solve_batched(handles, fs, us, precision=MTO_MIXED, rtol=1e-8, inner_rtol=0.0, max_iter=200000, max_outer=50,
                   warm_start=False, check_every=32, norm=NORM_ENERGY, precond=PREC_MG, inner_max=0, mg_degree=0,
-                  mg_smoother=SMOOTH_JACOBI, raise_on_error=True):
+                  mg_smoother=SMOOTH_JACOBI, mg_operator=MG_OP_AUTO, raise_on_error=True):
     """Step (b) of every instance, advanced together (mto_solve_batched).  Returns (iterations,
     relative residuals, statuses) as numpy arrays."""
     L = load_library()
     n = len(handles)
     o = SolveOpts(precision, rtol, inner_rtol, max_iter, max_outer, int(bool(warm_start)), check_every, norm,
-                  precond, inner_max, mg_degree, mg_smoother)
+                  precond, inner_max, mg_degree, mg_smoother, mg_operator)
     it = np.zeros(n, np.int32)
     rr = np.zeros(n)
     stt = np.zeros(n, np.int32)

@@ -79,13 +79,35 @@ __device__ __forceinline__ void df_acc(float& sh, float& sl, float pp, float pe)
   sl += err + pe;
 }
 
+// The leading (FP32) part alone, for preconditioners, which need a fixed operator but not the
+// operator's accuracy: row i of the lane sums K[i][i+k] x_{i+k} and receives K[i-k][i] x_{i-k} from
+// lane i-k, in plain FP32 (x rounded to FP32).  row(k) = D_k[i] of this lane (0 beyond n_e).
+template <int NE, int ND, typename RowFn>
+__device__ __forceinline__ float lead_rows(RowFn row, float x, int li, int gb) {
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < ND; ++k) {
+    const float a = row(k);
+    int j = li + k;
+    if (j >= NE) j -= NE;
+    s = fmaf(a, __shfl_sync(0xffffffffu, x, gb + j), s);
+    if (k > 0 && 2 * k != NE) {
+      int s2 = li - k;
+      if (s2 < 0) s2 += NE;
+      s += __shfl_sync(0xffffffffu, a * x, gb + s2);
+    }
+  }
+  return s;
+}
+
 // y += sum_e P_e^T K_e P_e x, one element per lane group (W lanes; G elements per warp).
 // Lane li owns rows i = li + 32 m.  Element matrices are rows of the circulant-diagonal layout:
 // at step k lane i reads D_k[i] = K[i][i+k], adds K[i][i+k] x_{i+k} to its row (x_{i+k} by
 // shuffle) and hands K[i][i+k] x_i to the lane owning row i+k (shuffle from the receiver's side),
 // so each stored entry serves both triangles.  kDF = false: FP64 matrices and arithmetic (plain
 // FP64 path).  kDF = true: the split-precision pair on the FP32 pipes with error-free products and
-// sums (~48-bit accurate), vectors TX = double (refinement residuals) or float (inner iterations).
+// sums (~48-bit accurate), vectors TX = double (refinement residuals) or float (inner iterations);
+// with Kl null, the leading part alone (the lo rows taken as zero).
 // A reduction output of one launch: every block stores its partial, the last block to finish
 // (counted with an atomic) sums the partials in index order (deterministic) into *res and
 // re-arms the counter.  Consumers read res[0 .. nres) (one scalar per launch).
@@ -235,7 +257,7 @@ __global__ void __launch_bounds__(256) ebe_kernel(const double* __restrict__ K64
           tdv[m] = a * xd[m];
         } else {
           const float ah = vi ? __ldg(Kh + rowb + k * NE + i) : 0.0f;
-          const float al = vi ? __ldg(Kl + rowb + k * NE + i) : 0.0f;
+          const float al = (vi && Kl) ? __ldg(Kl + rowb + k * NE + i) : 0.0f;
           const float xjh = shfl_sel<M>(xh, src, reg);
           const float xjl = kSplitX ? shfl_sel<M>(xl, src, reg) : 0.0f;
           float pp, pe;
@@ -284,7 +306,7 @@ __global__ void __launch_bounds__(256) ebe_kernel(const double* __restrict__ K64
 // grid walks its elements with a stride, and while a warp computes one element's rows it already
 // holds the next element's hi/lo rows (2 (n_e/2 + 1) registers each) and node map, so the
 // element stream from L2/HBM never waits on the arithmetic.  Same arithmetic as ebe_kernel.
-template <int PO, typename TX>
+template <int PO, bool kLo, typename TX>
 __global__ void __launch_bounds__(256, 2) ebe_df_pipe_kernel(const float* __restrict__ Kh,
                                                              const float* __restrict__ Kl, int L, int n,
                                                              const int* __restrict__ gmap,
@@ -309,7 +331,7 @@ __global__ void __launch_bounds__(256, 2) ebe_df_pipe_kernel(const float* __rest
 #pragma unroll
     for (int k = 0; k < ND; ++k) {
       h[k] = v ? __ldg(Kh + rowb + k * NE + li) : 0.0f;
-      l[k] = v ? __ldg(Kl + rowb + k * NE + li) : 0.0f;
+      l[k] = (kLo && v) ? __ldg(Kl + rowb + k * NE + li) : 0.0f;
     }
     g = v ? __ldg(gmap + (size_t)e * NN + (li >> 1)) : 0;
   };
@@ -334,28 +356,32 @@ __global__ void __launch_bounds__(256, 2) ebe_df_pipe_kernel(const float* __rest
     float bh[ND], bl[ND];
     int gnext = 0;
     fetch(base + stride + gid, bh, bl, gnext);
-    const float xh = (float)xd;
-    const float xl = kSplitX ? (float)(xd - (double)xh) : 0.0f;
     float sh = 0.0f, sl = 0.0f;
+    if constexpr (kLo) {
+      const float xh = (float)xd;
+      const float xl = kSplitX ? (float)(xd - (double)xh) : 0.0f;
 #pragma unroll
-    for (int k = 0; k < ND; ++k) {
-      int j = li + k;
-      if (j >= NE) j -= NE;
-      const int src = gb + j;
-      const float xjh = __shfl_sync(0xffffffffu, xh, src);
-      const float xjl = kSplitX ? __shfl_sync(0xffffffffu, xl, src) : 0.0f;
-      float pp, pe;
-      df_prod<kSplitX>(ah[k], al[k], xjh, xjl, pp, pe);
-      df_acc(sh, sl, pp, pe);
-      if (k > 0 && 2 * k != NE) {
-        float tp, te;
-        df_prod<kSplitX>(ah[k], al[k], xh, xl, tp, te);
-        int s = li - k;
-        if (s < 0) s += NE;
-        const float rp = __shfl_sync(0xffffffffu, tp, gb + s);
-        const float re = __shfl_sync(0xffffffffu, te, gb + s);
-        df_acc(sh, sl, rp, re);
+      for (int k = 0; k < ND; ++k) {
+        int j = li + k;
+        if (j >= NE) j -= NE;
+        const int src = gb + j;
+        const float xjh = __shfl_sync(0xffffffffu, xh, src);
+        const float xjl = kSplitX ? __shfl_sync(0xffffffffu, xl, src) : 0.0f;
+        float pp, pe;
+        df_prod<kSplitX>(ah[k], al[k], xjh, xjl, pp, pe);
+        df_acc(sh, sl, pp, pe);
+        if (k > 0 && 2 * k != NE) {
+          float tp, te;
+          df_prod<kSplitX>(ah[k], al[k], xh, xl, tp, te);
+          int s = li - k;
+          if (s < 0) s += NE;
+          const float rp = __shfl_sync(0xffffffffu, tp, gb + s);
+          const float re = __shfl_sync(0xffffffffu, te, gb + s);
+          df_acc(sh, sl, rp, re);
+        }
       }
+    } else {
+      sh = lead_rows<NE, ND>([&](int k) { return ah[k]; }, (float)xd, li, gb);
     }
     // scatter P_e^T y_e and the curvature term
     if (act) {
@@ -416,9 +442,10 @@ constexpr unsigned kWaitLimit = 1u << 24;
 // warp walks its own sequence of element groups (G elements of W lanes, G = 32 / W) and keeps
 // kStages groups' hi/lo rows in flight in its shared-memory ring, so the row stream no longer
 // depends on how many warps the registers allow.  Node maps and x values run one group ahead in
-// registers.  Same arithmetic and reduction as ebe_kernel.  Every wait is bounded: on expiry the
-// warp records MTO_ETIMEOUT, waits (bounded) for its copies still in flight, and stops.
-template <int PO, typename TX>
+// registers.  Same arithmetic and reduction as ebe_kernel (kLo = false: the hi rows alone, staged
+// and summed as in lead_rows).  Every wait is bounded: on expiry the warp records MTO_ETIMEOUT,
+// waits (bounded) for its copies still in flight, and stops.
+template <int PO, bool kLo, typename TX>
 __global__ void __launch_bounds__(kTmaWarps * 32) ebe_df_tma_kernel(const float* __restrict__ Kh,
                                                                     const float* __restrict__ Kl, int L, int n,
                                                                     const int* __restrict__ gmap,
@@ -430,6 +457,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32) ebe_df_tma_kernel(const float*
   constexpr int W = WarpShape<NE>::W, G = WarpShape<NE>::G;
   static_assert(WarpShape<NE>::M == 1, "one row per lane");
   constexpr bool kSplitX = sizeof(TX) == 8;
+  constexpr int NM = kLo ? 2 : 1;   // matrices staged per group (hi, lo)
   extern __shared__ __align__(128) unsigned char tma_smem[];
   if (done && *done) return;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -438,9 +466,9 @@ __global__ void __launch_bounds__(kTmaWarps * 32) ebe_df_tma_kernel(const float*
   const int nwarps = gridDim.x * kTmaWarps;
   const int stride = nwarps * G;
   const size_t stage_floats = (size_t)G * L;   // one group's rows (hi or lo)
-  float* ring = reinterpret_cast<float*>(tma_smem) + (size_t)wib * kStages * 2 * stage_floats;
+  float* ring = reinterpret_cast<float*>(tma_smem) + (size_t)wib * kStages * NM * stage_floats;
   uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<float*>(tma_smem) +
-                                               (size_t)kTmaWarps * kStages * 2 * stage_floats) +
+                                               (size_t)kTmaWarps * kStages * NM * stage_floats) +
                    wib * kStages;
   if (lane == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init1(bars + s);
@@ -454,11 +482,11 @@ __global__ void __launch_bounds__(kTmaWarps * 32) ebe_df_tma_kernel(const float*
     if (base >= n) return;
     const int cnt = n - base < G ? n - base : G;
     const uint32_t bytes = (uint32_t)(cnt * L * sizeof(float));
-    float* dst = ring + (size_t)(it % kStages) * 2 * stage_floats;
+    float* dst = ring + (size_t)(it % kStages) * NM * stage_floats;
     uint64_t* bar = bars + it % kStages;
-    mbar_expect_tx(bar, 2 * bytes);
+    mbar_expect_tx(bar, NM * bytes);
     bulk_g2s(dst, Kh + (size_t)base * L, bytes, bar);
-    bulk_g2s(dst + stage_floats, Kl + (size_t)base * L, bytes, bar);
+    if constexpr (kLo) bulk_g2s(dst + stage_floats, Kl + (size_t)base * L, bytes, bar);
   };
   if (lane == 0)
     for (int it = 0; it < kStages; ++it) issue(it);
@@ -495,33 +523,37 @@ __global__ void __launch_bounds__(kTmaWarps * 32) ebe_df_tma_kernel(const float*
       }
     }
     if (!__all_sync(0xffffffffu, ok)) break;
-    const float* rh = ring + (size_t)st * 2 * stage_floats + (size_t)gid * L;
+    const float* rh = ring + (size_t)st * NM * stage_floats + (size_t)gid * L;
     const float* rl = rh + stage_floats;
     const double xd = x_cur;
-    const float xh = (float)xd;
-    const float xl = kSplitX ? (float)(xd - (double)xh) : 0.0f;
     float sh = 0.0f, sl = 0.0f;
+    if constexpr (kLo) {
+      const float xh = (float)xd;
+      const float xl = kSplitX ? (float)(xd - (double)xh) : 0.0f;
 #pragma unroll
-    for (int k = 0; k < ND; ++k) {
-      const float ah = li < NE ? rh[k * NE + li] : 0.0f;
-      const float al = li < NE ? rl[k * NE + li] : 0.0f;
-      int j = li + k;
-      if (j >= NE) j -= NE;
-      const int src = gb + j;
-      const float xjh = __shfl_sync(0xffffffffu, xh, src);
-      const float xjl = kSplitX ? __shfl_sync(0xffffffffu, xl, src) : 0.0f;
-      float pp, pe;
-      df_prod<kSplitX>(ah, al, xjh, xjl, pp, pe);
-      df_acc(sh, sl, pp, pe);
-      if (k > 0 && 2 * k != NE) {
-        float tp, te;
-        df_prod<kSplitX>(ah, al, xh, xl, tp, te);
-        int s2 = li - k;
-        if (s2 < 0) s2 += NE;
-        const float rp = __shfl_sync(0xffffffffu, tp, gb + s2);
-        const float re = __shfl_sync(0xffffffffu, te, gb + s2);
-        df_acc(sh, sl, rp, re);
+      for (int k = 0; k < ND; ++k) {
+        const float ah = li < NE ? rh[k * NE + li] : 0.0f;
+        const float al = li < NE ? rl[k * NE + li] : 0.0f;
+        int j = li + k;
+        if (j >= NE) j -= NE;
+        const int src = gb + j;
+        const float xjh = __shfl_sync(0xffffffffu, xh, src);
+        const float xjl = kSplitX ? __shfl_sync(0xffffffffu, xl, src) : 0.0f;
+        float pp, pe;
+        df_prod<kSplitX>(ah, al, xjh, xjl, pp, pe);
+        df_acc(sh, sl, pp, pe);
+        if (k > 0 && 2 * k != NE) {
+          float tp, te;
+          df_prod<kSplitX>(ah, al, xh, xl, tp, te);
+          int s2 = li - k;
+          if (s2 < 0) s2 += NE;
+          const float rp = __shfl_sync(0xffffffffu, tp, gb + s2);
+          const float re = __shfl_sync(0xffffffffu, te, gb + s2);
+          df_acc(sh, sl, rp, re);
+        }
       }
+    } else {
+      sh = lead_rows<NE, ND>([&](int k) { return li < NE ? rh[k * NE + li] : 0.0f; }, (float)xd, li, gb);
     }
     // the stage is free again: refill it with the group kStages ahead
     __syncwarp();
@@ -560,8 +592,8 @@ __global__ void __launch_bounds__(kTmaWarps * 32) ebe_df_tma_kernel(const float*
   if (red.part) reduce_out(dot, red);
 }
 
-size_t tma_smem_bytes(int L, int G) {
-  return (size_t)kTmaWarps * kStages * 2 * G * L * sizeof(float) + (size_t)kTmaWarps * kStages * sizeof(uint64_t);
+size_t tma_smem_bytes(int L, int G, int nm) {
+  return (size_t)kTmaWarps * kStages * nm * G * L * sizeof(float) + (size_t)kTmaWarps * kStages * sizeof(uint64_t);
 }
 
 }  // namespace
@@ -599,28 +631,41 @@ void launch_ebe(mto_handle h, const PClass& c, const double* M64, const float* M
       // bulk-copy staging pays off when the rows stream from HBM (measured: 6.5 % faster on
       // 1 GB of rows, 6 % slower when they sit in L2), so by default it serves classes whose
       // split rows exceed 64 MB
-      const bool big = (size_t)c.n * c.L * 2 * sizeof(float) > ((size_t)64 << 20);
+      const bool lo = Ml != nullptr;   // null: the hi rows alone (a preconditioner's copy)
+      const bool big = (size_t)c.n * c.L * (lo ? 2 : 1) * sizeof(float) > ((size_t)64 << 20);
       if (opk == 1 || (opk < 0 && big)) {
         // bulk-copy staging: persistent, as many 8-warp blocks per SM as the shared memory holds
-        const size_t smem = tma_smem_bytes(c.L, WarpShape<NE>::G);
+        const size_t smem = tma_smem_bytes(c.L, WarpShape<NE>::G, lo ? 2 : 1);
         const int per_sm = smem > 0 ? (int)((227u * 1024u) / smem) : 1;
         int blocks = (warps + kTmaWarps - 1) / kTmaWarps;
         const int cap = 152 * (per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm));
         if (blocks > cap) blocks = cap;
-        static bool attr_set = false;   // once per process, before any stream capture uses it
-        if (!attr_set && smem > 48 * 1024) {
-          cudaFuncSetAttribute(ebe_df_tma_kernel<PO, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        static bool attr_set = false;   // once per process (both variants), before any stream capture
+        if (!attr_set) {
+          const int s2 = (int)tma_smem_bytes(c.L, WarpShape<NE>::G, 2), s1 = (int)tma_smem_bytes(c.L, WarpShape<NE>::G, 1);
+          if (s2 > 48 * 1024)
+            cudaFuncSetAttribute(ebe_df_tma_kernel<PO, true, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
+          if (s1 > 48 * 1024)
+            cudaFuncSetAttribute(ebe_df_tma_kernel<PO, false, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
           attr_set = true;
         }
-        ebe_df_tma_kernel<PO, TX><<<blocks, kTmaWarps * 32, smem, h->stream>>>(Mh, Ml, c.L, c.n, c.gmap, h->cons_d,
-                                                                               x, y, red, done, h->flags + 1);
+        if (lo)
+          ebe_df_tma_kernel<PO, true, TX><<<blocks, kTmaWarps * 32, smem, h->stream>>>(
+              Mh, Ml, c.L, c.n, c.gmap, h->cons_d, x, y, red, done, h->flags + 1);
+        else
+          ebe_df_tma_kernel<PO, false, TX><<<blocks, kTmaWarps * 32, smem, h->stream>>>(
+              Mh, Ml, c.L, c.n, c.gmap, h->cons_d, x, y, red, done, h->flags + 1);
         return;
       }
       // persistent: two blocks of 8 warps per SM (the register budget of the pipelined rows)
       int blocks = (warps + 7) / 8;
       if (blocks > 152 * 2) blocks = 152 * 2;
-      ebe_df_pipe_kernel<PO, TX><<<blocks, 256, 0, h->stream>>>(Mh, Ml, c.L, c.n, c.gmap, h->cons_d, x, y, red,
-                                                                  done);
+      if (lo)
+        ebe_df_pipe_kernel<PO, true, TX><<<blocks, 256, 0, h->stream>>>(Mh, Ml, c.L, c.n, c.gmap, h->cons_d, x, y,
+                                                                         red, done);
+      else
+        ebe_df_pipe_kernel<PO, false, TX><<<blocks, 256, 0, h->stream>>>(Mh, Ml, c.L, c.n, c.gmap, h->cons_d, x, y,
+                                                                          red, done);
       return;
     }
   }
@@ -654,14 +699,15 @@ Red red_slot(mto_handle h, int k, int j) {
 // y += sum_e P_e^T A_e P_e x over all order classes, where A_e is the element stiffness (which = 0)
 // or the element-block preconditioner (which = 1).  FP64 matrices on the FP64 pipes (plain FP64
 // path, refinement residuals) or the split-precision pair on the FP32 pipes (inner iterations of
-// the mixed solves) with FP64 or FP32 vectors.  x^T y goes to reduction slot `slot` (one result
-// per class launch; -1: not wanted); *nres receives the number of class launches.
+// the mixed solves) with FP64 or FP32 vectors; `lead`: of a split pair the FP32 leading part
+// alone (inside the preconditioner).  x^T y goes to reduction slot `slot` (one result per class
+// launch; -1: not wanted); *nres receives the number of class launches.
 template <typename T>
 mto_status apply_all(mto_handle h, int which, const T* x, T* y, int slot, const int* done, ConvTest cv,
-                     int* nres = nullptr) {
+                     int* nres = nullptr, bool lead = false) {
   const bool mixed_build = h->built_precision == MTO_MIXED;
-  const bool df = which == 1 ? mixed_build : (sizeof(T) == 4 || (mixed_build && h->inner_split));
-  const int fam = which == 1 ? F_PRECOND : (df ? (sizeof(T) == 8 ? F_APPLYDF64 : F_APPLY32) : F_APPLY64);
+  const bool df = which == 1 ? mixed_build : (sizeof(T) == 4 || (mixed_build && (h->inner_split || lead)));
+  const int fam = (which == 1 || lead) ? F_PRECOND : (df ? (sizeof(T) == 8 ? F_APPLYDF64 : F_APPLY32) : F_APPLY64);
   TimedScope ts(h, fam);
   int ci = 0;
   for (int p = 1; p <= MTO_P_MAX; ++p) {
@@ -669,10 +715,10 @@ mto_status apply_all(mto_handle h, int which, const T* x, T* y, int slot, const 
     if (c.n == 0) continue;
     const double* M64 = which ? c.B64 : c.K64;
     const float* Mh = which ? c.B32 : c.K32;
-    const float* Ml = which ? c.B32lo : c.K32lo;
+    const float* Ml = lead ? nullptr : (which ? c.B32lo : c.K32lo);
     const Red pp = red_slot(h, slot, ci);
     if (df) {
-      if (!Mh || !Ml) return mto_fail(h, MTO_EINVAL, "split-precision element matrices are not built");
+      if (!Mh || (!Ml && !lead)) return mto_fail(h, MTO_EINVAL, "split-precision element matrices are not built");
       switch (p) {
         case 1: launch_ebe<1, true, T>(h, c, M64, Mh, Ml, x, y, pp, done, cv); break;
         case 2: launch_ebe<2, true, T>(h, c, M64, Mh, Ml, x, y, pp, done, cv); break;
@@ -1232,8 +1278,8 @@ mto_status apply_operator(mto_handle h, int op, const double* x, double* y, doub
   int nres = 0;
   // a launch that ended a CG run early may have left a finished-block count behind
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->cg_cnt, 0, 64 * sizeof(unsigned), h->stream), "memset"));
-  h->inner_split = op == MTO_OP_SPLIT;
-  const mto_status st = apply_all<double>(h, 0, x, y, kGam, nullptr, none, &nres);
+  h->inner_split = op != MTO_OP_FP64;
+  const mto_status st = apply_all<double>(h, 0, x, y, kGam, nullptr, none, &nres, op == MTO_OP_LEAD);
   h->inner_split = false;
   MTO_TRY(st);
   if (!xKx) return MTO_OK;
@@ -1323,14 +1369,14 @@ mto_status autotune_operator(mto_handle h, int32_t* choice, double* us) {
   return st;
 }
 
-mto_status apply_fine(mto_handle h, const double* x, double* y, const int* done) {
+mto_status apply_fine(mto_handle h, const double* x, double* y, const int* done, bool lead) {
   ConvTest none{};
-  return apply_all<double>(h, 0, x, y, -1, done, none);
+  return apply_all<double>(h, 0, x, y, -1, done, none, nullptr, lead);
 }
 
-mto_status apply_block(mto_handle h, const double* x, double* y, const int* done) {
+mto_status apply_block(mto_handle h, const double* x, double* y, const int* done, bool lead) {
   ConvTest none{};
-  return apply_all<double>(h, 1, x, y, -1, done, none);
+  return apply_all<double>(h, 1, x, y, -1, done, none, nullptr, lead);
 }
 
 mto_status apply_q1(mto_handle h, const MGLevel& l, const double* x, double* y, const int* done) {
@@ -1373,6 +1419,7 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
     if (o->precision == MTO_MIXED32)
       return mto_fail(h, MTO_EINVAL, "mto_solve: the multigrid preconditioner needs FP64 vectors");
     MTO_TRY(mg_select_smoother(h, o->mg_smoother));
+    MTO_TRY(mg_select_operator(h, o->mg_operator));
     if (!h->mg_valid) MTO_TRY(mg_build(h));
   }
   if (!o->warm_start) MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(u, 0, sizeof(double) * n, h->stream), "memset"));
@@ -1602,6 +1649,7 @@ mto_status solve_batched(mto_handle* hs, int n, const double* const* f, double* 
     if (j.deg > 16) st = mto_fail(h, MTO_EINVAL, "mto_solve_batched: mg_degree above 16");
     if (st == MTO_OK && j.pc == MTO_PREC_SCHWARZ && !h->schwarz_valid) st = build_schwarz(h);
     if (st == MTO_OK && j.pc == MTO_PREC_MG) st = mg_select_smoother(h, o->mg_smoother);
+    if (st == MTO_OK && j.pc == MTO_PREC_MG) st = mg_select_operator(h, o->mg_operator);
     if (st == MTO_OK && j.pc == MTO_PREC_MG && !h->mg_valid) st = mg_build(h);
     if (st == MTO_OK) {
       if (!o->warm_start) st = mto_cuda_check(h, cudaMemsetAsync(j.u, 0, sizeof(double) * h->ndof, h->stream), "memset");

@@ -24,25 +24,35 @@ __global__ void basis_table_kernel(BasisTab* t) {
 }
 
 // Local displacement of element e (order p): 2 (p+1)^2 values, minimum-rule constraints applied.
+// both components of local node ln of the element in slot `slot` (through its constraint if hanging)
+__device__ __forceinline__ void gather_node(int nn, int slot, int ln, const int* __restrict__ gmap,
+                                            const Constraint* __restrict__ cons, const double* __restrict__ u,
+                                            double* ue) {
+  int g = gmap[(size_t)slot * nn + ln];
+  double a = 0.0, b = 0.0;
+  if (g >= 0) {
+    a = u[2 * (size_t)g];
+    b = u[2 * (size_t)g + 1];
+  } else {
+    const Constraint& c = cons[-g - 1];
+    for (int k = 0; k < c.cnt; ++k) {
+      a += c.w[k] * u[2 * (size_t)c.node[k]];
+      b += c.w[k] * u[2 * (size_t)c.node[k] + 1];
+    }
+  }
+  ue[2 * ln] = a;
+  ue[2 * ln + 1] = b;
+}
+
 __device__ void gather_element(int p, int slot, const int* __restrict__ gmap, const Constraint* __restrict__ cons,
                                const double* __restrict__ u, double* ue) {
   const int nn = (p + 1) * (p + 1);
-  for (int ln = 0; ln < nn; ++ln) {
-    int g = gmap[(size_t)slot * nn + ln];
-    double a = 0.0, b = 0.0;
-    if (g >= 0) {
-      a = u[2 * (size_t)g];
-      b = u[2 * (size_t)g + 1];
-    } else {
-      const Constraint& c = cons[-g - 1];
-      for (int k = 0; k < c.cnt; ++k) {
-        a += c.w[k] * u[2 * (size_t)c.node[k]];
-        b += c.w[k] * u[2 * (size_t)c.node[k] + 1];
-      }
-    }
-    ue[2 * ln] = a;
-    ue[2 * ln + 1] = b;
-  }
+  for (int ln = 0; ln < nn; ++ln) gather_node(nn, slot, ln, gmap, cons, u, ue);
+}
+
+__device__ __forceinline__ double warp_sum_all(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 struct ClassPtrs {
@@ -167,7 +177,8 @@ __global__ void gamma_d_kernel(int64_t nel, const int64_t* __restrict__ off, con
 // ------------------------------------------------------------------------------------ QR error
 // One warp per element of a (p, d) class (Eq. 14).  Shared layout (doubles): Kf[n1 * n1] (order p+1
 // matrix, full, factorised in place), Kp[P1] (an unmodified packed copy for J^(p+1)), f[n0],
-// f1[n1], u1[n1], E[S], ue[n0], with n0 = 2 (p+1)^2, n1 = 2 (p+2)^2, P1 = n1 (n1 + 1) / 2.
+// f1[n1], u1[n1], E[S], ue[n0], rd[n1] (reciprocal pivots), with n0 = 2 (p+1)^2, n1 = 2 (p+2)^2,
+// P1 = n1 (n1 + 1) / 2.
 // eps is invariant to rigid motions of u^(p), which are removed first (FP64) so that the element
 // energies carry no cancellation.
 __global__ void __launch_bounds__(32) qr_kernel(int p, int d, int n, const int* __restrict__ elem,
@@ -196,22 +207,24 @@ __global__ void __launch_bounds__(32) qr_kernel(int p, int d, int n, const int* 
   double* u1 = f1 + n1;
   double* E = u1 + n1;
   double* ue = E + S;
-  if (lane == 0) {
-    gather_element(p, sl, gmap, cons, u, ue);
-    // least-squares rigid motion about the element centre (translations and rotation)
+  // gather u_e (lanes over nodes), then remove its least-squares rigid motion about the element
+  // centre (translations and rotation; node sums over the warp)
+  for (int ln = lane; ln < na; ln += 32) gather_node(na, sl, ln, gmap, cons, u, ue);
+  __syncwarp();
+  {
     const double* z = B->gll[p];
     double tx = 0.0, ty = 0.0, num = 0.0, den = 0.0;
-    for (int ln = 0; ln < na; ++ln) {
+    for (int ln = lane; ln < na; ln += 32) {
       const double x = 0.5 * hx * z[ln % n1d], y = 0.5 * hy * z[ln / n1d];
       tx += ue[2 * ln];
       ty += ue[2 * ln + 1];
       num += x * ue[2 * ln + 1] - y * ue[2 * ln];
       den += x * x + y * y;
     }
-    tx /= na;
-    ty /= na;
-    const double om = num / den;
-    for (int ln = 0; ln < na; ++ln) {
+    tx = warp_sum_all(tx) / na;
+    ty = warp_sum_all(ty) / na;
+    const double om = warp_sum_all(num) / warp_sum_all(den);
+    for (int ln = lane; ln < na; ln += 32) {
       const double x = 0.5 * hx * z[ln % n1d], y = 0.5 * hy * z[ln / n1d];
       ue[2 * ln] = ue[2 * ln] - tx + om * y;
       ue[2 * ln + 1] = ue[2 * ln + 1] - ty - om * x;
@@ -277,33 +290,48 @@ __global__ void __launch_bounds__(32) qr_kernel(int p, int d, int n, const int* 
     }
   }
   __syncwarp();
-  // Cholesky (lower), right-looking, rows distributed over lanes
+  // Cholesky K = L L^T (lower, right-looking).  Column c is scaled by the reciprocal of its pivot,
+  // kept in rd[c] for the substitutions; the trailing update A_ij -= L_ic L_jc (c < j <= i) runs
+  // over the m (m + 1) / 2 pairs of the trailing block spread evenly over the lanes: pair
+  // t = s (s + 1) / 2 + r (0 <= r <= s < m) is row n1 - 1 - r, column n1 - 1 - s.
+  double* rd = ue + n0;   // [n1]
   for (int c = 0; c < n1; ++c) {
     const double dcc = sqrt(Kf[c * n1 + c]);
+    const double inv = 1.0 / dcc;
     __syncwarp();
-    for (int i = c + 1 + lane; i < n1; i += 32) Kf[i * n1 + c] /= dcc;
-    if (lane == 0) Kf[c * n1 + c] = dcc;
+    for (int i = c + 1 + lane; i < n1; i += 32) Kf[i * n1 + c] *= inv;
+    if (lane == 0) {
+      Kf[c * n1 + c] = dcc;
+      rd[c] = inv;
+    }
     __syncwarp();
-    for (int i = c + 1 + lane; i < n1; i += 32) {
-      const double lic = Kf[i * n1 + c];
-      for (int j = c + 1; j <= i; ++j) Kf[i * n1 + j] -= lic * Kf[j * n1 + c];
+    const int m = n1 - 1 - c;
+    const int T = m * (m + 1) / 2;
+    for (int t = lane; t < T; t += 32) {
+      int s = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+      while (s * (s + 1) / 2 > t) --s;
+      while ((s + 1) * (s + 2) / 2 <= t) ++s;
+      const int r = t - s * (s + 1) / 2;
+      const int i = n1 - 1 - r, j = n1 - 1 - s;
+      Kf[i * n1 + j] -= Kf[i * n1 + c] * Kf[j * n1 + c];
     }
     __syncwarp();
   }
-  // forward then backward substitution (lane 0; n1 <= 128)
-  if (lane == 0) {
-    for (int i = 0; i < n1; ++i) {
-      double s = u1[i];
-      for (int j = 0; j < i; ++j) s -= Kf[i * n1 + j] * u1[j];
-      u1[i] = s / Kf[i * n1 + i];
-    }
-    for (int i = n1 - 1; i >= 0; --i) {
-      double s = u1[i];
-      for (int j = i + 1; j < n1; ++j) s -= Kf[j * n1 + i] * u1[j];
-      u1[i] = s / Kf[i * n1 + i];
-    }
+  // L y = b, then L^T x = y, column by column (each solved entry updates the rest over the lanes)
+  for (int j = 0; j < n1; ++j) {
+    const double yj = u1[j] * rd[j];
+    __syncwarp();
+    for (int i = j + 1 + lane; i < n1; i += 32) u1[i] -= Kf[i * n1 + j] * yj;
+    if (lane == 0) u1[j] = yj;
+    __syncwarp();
   }
-  __syncwarp();
+  for (int j = n1 - 1; j >= 0; --j) {
+    const double xj = u1[j] * rd[j];
+    __syncwarp();
+    for (int i = lane; i < j; i += 32) u1[i] -= Kf[j * n1 + i] * xj;
+    if (lane == 0) u1[j] = xj;
+    __syncwarp();
+  }
   // J^(p+1) = u1^T K u1 / 2 from the unmodified packed copy
   double j1 = 0.0;
   for (int c = lane; c < P1; c += 32) {
@@ -503,33 +531,53 @@ __global__ void final_kernel(int64_t nel, const int* __restrict__ p_s, const int
 
 // ------------------------------------------------------------------------------------ OC
 // rho_new_j = clip(rho_j (B_j / lambda)^eta, max(0, rho_j - m), min(1, rho_j + m)), B_j = -dc_j / dv_j,
-// written as t_j lambda^-eta with t_j = rho_j B_j^eta formed once, so every bisection pass is one
-// multiply per value (sqrt for the usual eta = 1/2).  One warp per element (coalesced over its
-// subcells); the volume sum is reduced in a fixed order and its last block takes the bisection
-// step itself, so the whole bisection is a chain of identical launches with no host round trip.
+// written as t_j lambda^-eta with t_j = rho_j B_j^eta formed once.  The volume of a trial lambda is
+// sum_j dv_j clip(t_j c, lo_j, hi_j) = sum_j clip(T_j c, L_j, H_j) with T, L, H the values scaled by
+// their subcell's area (dv > 0 commutes with the clip), so a bisection pass is a flat stream of
+// three arrays with one multiply and one add per value on the FP64 pipes; the clip is taken on the
+// integer pipes (non-negative doubles order like their bit patterns).  The volume sum is reduced
+// in a fixed order and its last block takes the bisection step itself, so the whole bisection is a
+// chain of identical launches with no host round trip.
 constexpr int kOCBlock = 256;
 
 __device__ __forceinline__ double oc_pow(double x, double eta) { return eta == 0.5 ? sqrt(x) : pow(x, eta); }
 
+// clip(x, lo, hi) for non-negative lo <= hi (x >= 0 or -0) by signed 64-bit compares of the bits
+__device__ __forceinline__ double clip_nonneg(double x, double lo, double hi) {
+  long long xi = __double_as_longlong(x);
+  const long long li = __double_as_longlong(lo), hi_ = __double_as_longlong(hi);
+  xi = xi > li ? xi : li;
+  xi = xi < hi_ ? xi : hi_;
+  return __longlong_as_double(xi);
+}
+
+// t_j, and the area-scaled T_j = dv t_j, L_j = dv max(0, rho_j - m), H_j = dv min(1, rho_j + m)
 __global__ void __launch_bounds__(kOCBlock) oc_prep_kernel(int64_t nel, const int64_t* __restrict__ off,
                                                            const int* __restrict__ dmap, double hx, double hy,
                                                            const double* __restrict__ rho,
-                                                           const double* __restrict__ dc, double eta,
-                                                           double* __restrict__ t) {
+                                                           const double* __restrict__ dc, double move, double eta,
+                                                           double* __restrict__ t, double* __restrict__ T,
+                                                           double* __restrict__ Lo, double* __restrict__ Hi) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t e = w0; e < nel; e += nw) {
     const int d = dmap[e];
     const double dv = hx * hy / ((double)d * d);
-    for (int64_t j = off[e] + lane; j < off[e + 1]; j += 32) t[j] = rho[j] * oc_pow(fmax(-dc[j], 0.0) / dv, eta);
+    for (int64_t j = off[e] + lane; j < off[e + 1]; j += 32) {
+      const double r = rho[j];
+      const double tj = r * oc_pow(fmax(-dc[j], 0.0) / dv, eta);
+      t[j] = tj;
+      T[j] = dv * tj;
+      Lo[j] = dv * fmax(0.0, r - move);
+      Hi[j] = dv * fmin(1.0, r + move);
+    }
   }
 }
 
-__global__ void __launch_bounds__(kOCBlock) oc_sum_kernel(int64_t nel, const int64_t* __restrict__ off,
-                                                          const int* __restrict__ dmap, double hx, double hy,
-                                                          const double* __restrict__ rho,
-                                                          const double* __restrict__ t, double move, double eta,
+__global__ void __launch_bounds__(kOCBlock) oc_sum_kernel(int64_t n, const double* __restrict__ T,
+                                                          const double* __restrict__ Lo,
+                                                          const double* __restrict__ Hi, double eta,
                                                           double* __restrict__ lam, double target, double tol,
                                                           int* __restrict__ done, double* __restrict__ part,
                                                           unsigned* __restrict__ cnt) {
@@ -539,19 +587,9 @@ __global__ void __launch_bounds__(kOCBlock) oc_sum_kernel(int64_t nel, const int
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const double lmid = 0.5 * (lam[0] + lam[1]);
   const double c = eta == 0.5 ? 1.0 / sqrt(lmid) : pow(lmid, -eta);
-  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double s = 0.0;
-  for (int64_t e = w0; e < nel; e += nw) {
-    const int d = dmap[e];
-    const double dv = hx * hy / ((double)d * d);
-    double se = 0.0;
-    for (int64_t j = off[e] + lane; j < off[e + 1]; j += 32) {
-      const double r = rho[j];
-      se += fmin(fmax(t[j] * c, fmax(0.0, r - move)), fmin(1.0, r + move));
-    }
-    s += se * dv;
-  }
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    s += clip_nonneg(T[j] * c, Lo[j], Hi[j]);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) ws[wib] = s;
   __syncthreads();
@@ -572,20 +610,15 @@ __global__ void __launch_bounds__(kOCBlock) oc_sum_kernel(int64_t nel, const int
   *cnt = 0u;
 }
 
-__global__ void __launch_bounds__(kOCBlock) oc_write_kernel(int64_t nel, const int64_t* __restrict__ off,
-                                                            const double* __restrict__ rho,
+__global__ void __launch_bounds__(kOCBlock) oc_write_kernel(int64_t n, const double* __restrict__ rho,
                                                             const double* __restrict__ t, double move, double eta,
                                                             const double* __restrict__ lam, double* __restrict__ out) {
-  const int lane = threadIdx.x & 31;
   const double lmid = 0.5 * (lam[0] + lam[1]);
   const double c = eta == 0.5 ? 1.0 / sqrt(lmid) : pow(lmid, -eta);
-  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t e = w0; e < nel; e += nw)
-    for (int64_t j = off[e] + lane; j < off[e + 1]; j += 32) {
-      const double r = rho[j];
-      out[j] = fmin(fmax(t[j] * c, fmax(0.0, r - move)), fmin(1.0, r + move));
-    }
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double r = rho[j];
+    out[j] = fmin(fmax(t[j] * c, fmax(0.0, r - move)), fmin(1.0, r + move));
+  }
 }
 
 // ------------------------------------------------------------------------------------ host side
@@ -736,7 +769,7 @@ mto_status indicators(mto_handle h, const double* u, const double* rho, const mt
     const BClass& b1 = h->bc_qr[ci];
     const PClass& c = h->pc[b.p];
     const int n0 = 2 * (b.p + 1) * (b.p + 1), n1 = 2 * (b.p + 2) * (b.p + 2);
-    size_t smem = sizeof(double) * ((size_t)n1 * n1 + packed_size(n1) + n0 + n1 + n1 + b.S + n0);
+    size_t smem = sizeof(double) * ((size_t)n1 * n1 + packed_size(n1) + n0 + n1 + n1 + b.S + n0 + n1);
     if (smem > 48 * 1024) cudaFuncSetAttribute(qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     qr_kernel<<<b.n, 32, smem, h->stream>>>(b.p, b.d, b.n, b.elem, b.slot, c.L, c.dpos, c.gmap, h->cons_d,
                                             c.K64, c.K32, c.K32lo, b1.K0T,
@@ -756,7 +789,11 @@ mto_status oc_update(mto_handle h, const double* rho, const double* dc, double v
   double* lam = h->red + 16;       // [l1, l2]
   int* done = h->flags + 8;
   unsigned* cnt = reinterpret_cast<unsigned*>(h->flags + 9);
-  if (!h->oc_t) MTO_TRY(mto_alloc(h, &h->oc_t, (size_t)h->design_len));
+  if (!h->oc_t) MTO_TRY(mto_alloc(h, &h->oc_t, (size_t)4 * h->design_len));   // t, T, L, H
+  const int64_t n = h->design_len;
+  double* T = h->oc_t + n;
+  double* Lo = T + n;
+  double* Hi = Lo + n;
   const double init[2] = {0.0, 1e9};
   h->host_pinned[48] = init[0];
   h->host_pinned[49] = init[1];
@@ -765,16 +802,17 @@ mto_status oc_update(mto_handle h, const double* rho, const double* dc, double v
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->flags + 8, 0, 2 * sizeof(int), h->stream), "memset"));
   const double target = volfrac * (double)h->nelx * h->nely * h->hx * h->hy;
   const int grd = grid_for(nel * 32, kOCBlock, 152 * 8);
-  oc_prep_kernel<<<grd, kOCBlock, 0, h->stream>>>(nel, h->design_off_d, h->d_d, h->hx, h->hy, rho, dc, eta, h->oc_t);
+  const int gsum = grid_for(n, kOCBlock, 152 * 8);
+  oc_prep_kernel<<<grd, kOCBlock, 0, h->stream>>>(nel, h->design_off_d, h->d_d, h->hx, h->hy, rho, dc, move, eta,
+                                                  h->oc_t, T, Lo, Hi);
   MTO_TRY(mto_after_launch(h, "oc_prep_kernel"));
   // bisection on [0, 1e9] to a relative width of 1e-10 takes at most ~100 halvings; the launches
   // after convergence return at once
   for (int it = 0; it < 128; ++it) {
-    oc_sum_kernel<<<grd, kOCBlock, 0, h->stream>>>(nel, h->design_off_d, h->d_d, h->hx, h->hy, rho, h->oc_t, move, eta,
-                                                  lam, target, 1e-10, done, h->cg_part, cnt);
+    oc_sum_kernel<<<gsum, kOCBlock, 0, h->stream>>>(n, T, Lo, Hi, eta, lam, target, 1e-10, done, h->cg_part, cnt);
     MTO_TRY(mto_after_launch(h, "oc_sum_kernel"));
   }
-  oc_write_kernel<<<grd, kOCBlock, 0, h->stream>>>(nel, h->design_off_d, rho, h->oc_t, move, eta, lam, rho_new);
+  oc_write_kernel<<<gsum, kOCBlock, 0, h->stream>>>(n, rho, h->oc_t, move, eta, lam, rho_new);
   MTO_TRY(mto_after_launch(h, "oc_write_kernel"));
   if (lambda) {
     MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->host_pinned + 16, lam, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy"));

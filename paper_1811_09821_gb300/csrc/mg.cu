@@ -195,9 +195,9 @@ __global__ void __launch_bounds__(128) mg_galerkin_h_kernel(int nxc, int nyc, in
 // v = (i, j) couples with the vertices (i + di, j + dj), di, dj in {-1, 0, 1} (offset o =
 // 3 (dj + 1) + di + 1), through a 2 x 2 block per offset.  One thread per vertex gathers the
 // contributions of its (up to four) elements in a fixed order, so no atomics; the stencil is
-// stored offset-major ([36][nv]) for coalesced reads in the apply.
+// stored offset-major ([36][nv]) for coalesced reads in the apply, in FP64 and rounded to FP32.
 __global__ void __launch_bounds__(256) mg_stencil_kernel(int nx, int ny, const double* __restrict__ K,
-                                                         double* __restrict__ S) {
+                                                         double* __restrict__ S, float* __restrict__ S32) {
   const int64_t nv = (int64_t)(nx + 1) * (ny + 1);
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(v % (nx + 1)), j = (int)(v / (nx + 1));
@@ -221,19 +221,26 @@ __global__ void __launch_bounds__(256) mg_stencil_kernel(int nx, int ny, const d
       }
     }
 #pragma unroll
-    for (int k = 0; k < 36; ++k) S[(size_t)k * nv + v] = acc[k];
+    for (int k = 0; k < 36; ++k) {
+      S[(size_t)k * nv + v] = acc[k];
+      S32[(size_t)k * nv + v] = (float)acc[k];
+    }
   }
 }
 
-// y = A x on a Q1 level by its vertex stencil (gather only; every DOF, supported ones included)
-__global__ void __launch_bounds__(256) mg_stencil_apply_kernel(int nx, int ny, const double* __restrict__ S,
+// y = A x on a Q1 level by its vertex stencil (gather only; every DOF, supported ones included):
+// FP64 stencil and arithmetic, or (TS = float, the cycle's FP32 copy) the stencil rounded to FP32
+// with x rounded to FP32 and FP32 products and sums (36 FP64 FMAs per vertex would make the apply
+// bound by GB300's FP64 pipes rather than by memory)
+template <typename TS>
+__global__ void __launch_bounds__(256) mg_stencil_apply_kernel(int nx, int ny, const TS* __restrict__ S,
                                                                const double* __restrict__ x, double* __restrict__ y,
                                                                const int* __restrict__ done) {
   if (done && *done) return;
   const int64_t nv = (int64_t)(nx + 1) * (ny + 1);
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(v % (nx + 1)), j = (int)(v / (nx + 1));
-    double y0 = 0.0, y1 = 0.0;
+    TS y0 = 0, y1 = 0;
 #pragma unroll
     for (int dj = -1; dj <= 1; ++dj) {
 #pragma unroll
@@ -242,15 +249,15 @@ __global__ void __launch_bounds__(256) mg_stencil_apply_kernel(int nx, int ny, c
         if (ii < 0 || ii > nx || jj < 0 || jj > ny) continue;
         const int o = 3 * (dj + 1) + di + 1;
         const size_t w = 2 * ((size_t)jj * (nx + 1) + ii);
-        const double x0 = x[w], x1 = x[w + 1];
+        const TS x0 = (TS)x[w], x1 = (TS)x[w + 1];
         y0 = fma(S[(size_t)(o * 4 + 0) * nv + v], x0, y0);
         y0 = fma(S[(size_t)(o * 4 + 1) * nv + v], x1, y0);
         y1 = fma(S[(size_t)(o * 4 + 2) * nv + v], x0, y1);
         y1 = fma(S[(size_t)(o * 4 + 3) * nv + v], x1, y1);
       }
     }
-    y[2 * v] = y0;
-    y[2 * v + 1] = y1;
+    y[2 * v] = (double)y0;
+    y[2 * v + 1] = (double)y1;
   }
 }
 
@@ -576,7 +583,7 @@ int vec_grid(int64_t n) { return grid_for(n, 256, kMGBlocks); }
 // ---------------------------------------------------------------- host side
 void mg_release(mto_handle h) {
   for (auto& l : h->mg)
-    for (void* p : {(void*)l.gmap, (void*)l.K, (void*)l.S, (void*)l.mask, (void*)l.invd, (void*)l.x, (void*)l.b,
+    for (void* p : {(void*)l.gmap, (void*)l.K, (void*)l.S, (void*)l.S32, (void*)l.mask, (void*)l.invd, (void*)l.x, (void*)l.b,
                     (void*)l.q, (void*)l.d})
       cudaFree(p);
   h->mg.clear();
@@ -631,7 +638,10 @@ mto_status mg_setup(mto_handle h) {
     MTO_TRY(mto_alloc(h, &L.gmap, gm.size()));
     MTO_TRY(mto_cuda_check(h, cudaMemcpy(L.gmap, gm.data(), gm.size() * sizeof(int), cudaMemcpyHostToDevice), "upload"));
     MTO_TRY(mto_alloc(h, &L.K, (size_t)40 * L.nel));
-    if (l + 1 < dims.size()) MTO_TRY(mto_alloc(h, &L.S, (size_t)36 * L.nv));   // smoothed levels
+    if (l + 1 < dims.size()) {   // smoothed levels
+      MTO_TRY(mto_alloc(h, &L.S, (size_t)36 * L.nv));
+      MTO_TRY(mto_alloc(h, &L.S32, (size_t)36 * L.nv));
+    }
     for (double** v : {&L.mask, &L.invd, &L.x, &L.b, &L.q, &L.d}) MTO_TRY(mto_alloc(h, v, L.n));
     MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(L.q, 0, L.n * sizeof(double), h->stream), "memset"));
   }
@@ -766,14 +776,14 @@ mto_status mg_power(mto_handle h, int level, double* lmax_out) {
   MTO_TRY(mto_after_launch(h, "mg_pow_init_kernel"));
   const bool block = fine && h->mg_block;   // lmax of M^-1 A, M^-1 the element-block inverse
   for (int it = 0; it < kPowerIts; ++it) {
-    if (fine) MTO_TRY(apply_fine(h, v, q, nullptr));
+    if (fine) MTO_TRY(apply_fine(h, v, q, nullptr, h->mg_lead != 0));
     else MTO_TRY(mg_apply_level(h, h->mg[level], v, q, nullptr));
     if (block) {
       mg_block_resid_kernel<<<grd, 256, 0, h->stream>>>(n, nullptr, q, invd, w, nullptr);   // w = -A v
       MTO_TRY(mto_after_launch(h, "mg_block_resid_kernel"));
       mg_zero_kernel<<<grd, 256, 0, h->stream>>>(n, q, nullptr);
       MTO_TRY(mto_after_launch(h, "mg_zero_kernel"));
-      MTO_TRY(apply_block(h, w, q, nullptr));
+      MTO_TRY(apply_block(h, w, q, nullptr, h->mg_lead & 1));
     }
     mg_pow_step_kernel<<<grd, 256, 0, h->stream>>>(n, q, invd, w, h->mg_part, h->mg_cnt, h->mg_res, block);
     MTO_TRY(mto_after_launch(h, "mg_pow_step_kernel"));
@@ -796,6 +806,20 @@ mto_status mg_select_smoother(mto_handle h, int smoother) {
   if (smoother == h->mg_smoother) return MTO_OK;
   MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "mto_solve"));
   h->mg_smoother = smoother;
+  h->mg_valid = false;
+  clear_graphs(h);
+  return MTO_OK;
+}
+
+// The copy of the element matrices the cycle applies with the MTO_MIXED build (all its split-pair
+// applies on the FP32 leading part, or none); a change rebuilds the bounds and drops the graphs.
+mto_status mg_select_operator(mto_handle h, int op) {
+  if (op != MTO_MG_OP_AUTO && op != MTO_MG_OP_SPLIT && op != MTO_MG_OP_LEAD)
+    return mto_fail(h, MTO_EINVAL, "mto_solve: bad mg_operator");
+  const int lead = op == MTO_MG_OP_SPLIT ? 0 : 7;
+  if (lead == h->mg_lead) return MTO_OK;
+  MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "mto_solve"));
+  h->mg_lead = lead;
   h->mg_valid = false;
   clear_graphs(h);
   return MTO_OK;
@@ -832,7 +856,7 @@ mto_status mg_build(mto_handle h) {
   }
   for (auto& L : h->mg) {
     if (L.S) {
-      mg_stencil_kernel<<<vec_grid(L.nv), 256, 0, h->stream>>>(L.nx, L.ny, L.K, L.S);
+      mg_stencil_kernel<<<vec_grid(L.nv), 256, 0, h->stream>>>(L.nx, L.ny, L.K, L.S, L.S32);
       MTO_TRY(mto_after_launch(h, "mg_stencil_kernel"));
     }
     MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(L.invd, 0, L.n * sizeof(double), h->stream), "memset"));
@@ -899,7 +923,7 @@ mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const
     for (int s = 0; s < k; ++s) {
       const bool skip_apply = pre && s == 0;   // x = 0: A x = 0
       if (!skip_apply) {
-        if (lev < 0) MTO_TRY(apply_fine(h, x, q, done));
+        if (lev < 0) MTO_TRY(apply_fine(h, x, q, done, h->mg_lead & (pre ? 2 : 4)));
         else {
           TimedScope ts(h, F_PRECOND);
           MTO_TRY(mg_apply_level(h, h->mg[lev], x, q, done));
@@ -913,7 +937,7 @@ mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const
           mg_zero_kernel<<<grd, 256, 0, h->stream>>>(n, q, done);
           MTO_TRY(mto_after_launch(h, "mg_zero_kernel"));
         }
-        MTO_TRY(apply_block(h, h->mg_v0, q, done));
+        MTO_TRY(apply_block(h, h->mg_v0, q, done, h->mg_lead & 1));
       }
       TimedScope ts(h, F_PRECOND);
       const bool dot = with_dot && s == k - 1;
@@ -930,7 +954,7 @@ mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const
   };
   // level 0 pre-smoothing and residual
   MTO_TRY(smooth(-1, r, z, h->mg_q0, h->mg_d0, h->invd64, h->ndof, true, false));
-  MTO_TRY(apply_fine(h, z, h->mg_q0, done));
+  MTO_TRY(apply_fine(h, z, h->mg_q0, done, h->mg_lead & 2));
   {
     TimedScope ts(h, F_PRECOND);
     MGLevel& L1 = h->mg[0];
@@ -977,10 +1001,14 @@ mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const
 }
 
 // y = A x on Q1 level l (y is written, not accumulated): the vertex stencil where it exists (the
-// smoothed levels), else the element matrices
+// smoothed levels; rounded to FP32 when the cycle runs on the leading parts of a mixed build), else
+// the element matrices
 mto_status mg_apply_level(mto_handle h, const MGLevel& l, const double* x, double* y, const int* done) {
   if (!l.S) return apply_q1(h, l, x, y, done);
-  mg_stencil_apply_kernel<<<vec_grid(l.nv), 256, 0, h->stream>>>(l.nx, l.ny, l.S, x, y, done);
+  if (h->mg_lead && h->built_precision == MTO_MIXED)
+    mg_stencil_apply_kernel<float><<<vec_grid(l.nv), 256, 0, h->stream>>>(l.nx, l.ny, l.S32, x, y, done);
+  else
+    mg_stencil_apply_kernel<double><<<vec_grid(l.nv), 256, 0, h->stream>>>(l.nx, l.ny, l.S, x, y, done);
   return mto_after_launch(h, "mg_stencil_apply_kernel");
 }
 

@@ -924,9 +924,10 @@ mto_status mto_apply_operator(mto_handle h, int32_t op, const double* x, double*
   if (!h) return MTO_EINVAL;
   StreamJoin join(h);
   if (!h->have_setup || !x || !y) return mto_fail(h, MTO_EINVAL, "mto_apply_operator: bad arguments");
-  if (op != MTO_OP_FP64 && op != MTO_OP_SPLIT) return mto_fail(h, MTO_EINVAL, "mto_apply_operator: bad operator");
+  if (op != MTO_OP_FP64 && op != MTO_OP_SPLIT && op != MTO_OP_LEAD)
+    return mto_fail(h, MTO_EINVAL, "mto_apply_operator: bad operator");
   if (h->built_precision < 0) return mto_fail(h, MTO_EINVAL, "mto_apply_operator: call mto_build_elements first");
-  if (op == MTO_OP_SPLIT && h->built_precision != MTO_MIXED)
+  if (op != MTO_OP_FP64 && h->built_precision != MTO_MIXED)
     return mto_fail(h, MTO_EINVAL, "mto_apply_operator: the split operator needs the MTO_MIXED build");
   cudaSetDevice(h->device);
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(y, 0, h->ndof * sizeof(double), h->stream), "mto_apply_operator"));

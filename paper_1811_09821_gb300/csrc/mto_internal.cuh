@@ -101,6 +101,7 @@ struct MGLevel {
   double* K = nullptr;             // [nel][40]
   double* S = nullptr;             // [36][nv] the assembled operator as a vertex stencil: entry
                                    // (o * 4 + 2 c + c') of vertex v couples (v, c) with (v + offset o, c')
+  float* S32 = nullptr;            // [36][nv] the same rounded to FP32 (the cycle's copy with mg_operator LEAD)
   double* mask = nullptr;          // [n] 0 on supported DOFs, else 1
   double* invd = nullptr;          // [n] inverse diagonal, 0 on supported DOFs
   double *x = nullptr, *b = nullptr, *q = nullptr, *d = nullptr;   // [n] cycle vectors
@@ -173,7 +174,7 @@ struct mto_handle_s {
   int64_t* fixed_d = nullptr;                  // [n_fixed] supported DOFs
   int64_t n_fixed = 0;
   double* filt_W = nullptr;                    // [design_len] density-filter weight sums (adjoint)
-  double* oc_t = nullptr;                      // [design_len] OC: rho_j B_j^eta
+  double* oc_t = nullptr;                      // [4][design_len] OC: rho_j B_j^eta and the area-scaled T, L, H
   int64_t* spring_dof_d = nullptr;             // [n_springs] DOFs with a spring to ground (K + k e e^T)
   double* spring_k_d = nullptr;                // [n_springs] their stiffness
   int n_springs = 0;
@@ -220,11 +221,13 @@ struct mto_handle_s {
   double* mg_part = nullptr;                   // reduction partials
   unsigned* mg_cnt = nullptr;
   double* mg_res = nullptr;
-  int build_path = MTO_BUILD_SIMT;
+  int build_path = MTO_BUILD_TENSOR;
   bool use_graphs = true;
   bool solve_log = false;                      // MTO_SOLVE_LOG=1: one stderr line per refinement step
   double mg_ratio = 0.0;                       // MTO_MG_RATIO: Chebyshev interval lmax / ratio .. lmax (0: 100)
   int mg_q1deg = 0;                            // MTO_MG_Q1DEG: smoothing degree on the Q1 levels (0: 4)
+  int mg_lead = 7;   // split-pair applies of the cycle taken on the FP32 leading part (mg_operator):
+                     // bit 0 element blocks, bit 1 pre-smoothing and restriction residual, bit 2 post-smoothing
   int mg_smoother = 0;                         // fine-level smoothing: MTO_SMOOTH_JACOBI or MTO_SMOOTH_BLOCK
   bool mg_block = false;                       // element-block smoothing in use (set by mg_build)
   std::vector<mto::GraphEntry*> graphs;
@@ -446,8 +449,10 @@ int ebe_blocks(int p, int n);                                           // grid 
 mto_status apply64(mto_handle h, const double* x, double* y);        // y += K x (FP64 vectors)
 mto_status apply_operator(mto_handle h, int op, const double* x, double* y, double* xKx);   // mto_apply_operator
 mto_status autotune_operator(mto_handle h, int32_t* choice, double* us);                   // mto_autotune
-mto_status apply_fine(mto_handle h, const double* x, double* y, const int* done);   // same, early exit
-mto_status apply_block(mto_handle h, const double* x, double* y, const int* done);  // y += (element blocks) x
+// same, early exit; lead: of the split pair the FP32 leading part alone (MTO_MIXED builds)
+mto_status apply_fine(mto_handle h, const double* x, double* y, const int* done, bool lead = false);
+mto_status mg_select_operator(mto_handle h, int op);   // mg_operator of mto_solve_opts
+mto_status apply_block(mto_handle h, const double* x, double* y, const int* done, bool lead = false);  // element blocks
 mto_status apply_q1(mto_handle h, const MGLevel& l, const double* x, double* y, const int* done);
 mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts* o, int32_t* iters,
                  double* relres);

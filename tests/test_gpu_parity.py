@@ -93,7 +93,11 @@ def test_numbering_bit_exact(mto, name):
 # ----------------------------------------------------------------------------- step (a) via the operator
 # (operator, kernel): the FP64 operator; the split-precision operator through each kernel the inner
 # PCG of the mixed solves can launch (register pipeline, bulk-copy staging, generic)
-OPERATORS = [("fp64", "auto"), ("split", "pipe"), ("split", "staged"), ("split", "generic")]
+OPERATORS = [("fp64", "auto"), ("split", "pipe"), ("split", "staged"), ("split", "generic"),
+             ("lead", "pipe"), ("lead", "staged"), ("lead", "generic")]
+# the leading part alone: entries and x rounded to FP32 (2^-24 each) and FP32 sums of the n_e <= 32
+# products of a row plus the n_e received ones, so within (2 + 2 n_e) 2^-24 of |K||x| per element row
+LEAD_TOL = 72 * 2.0 ** -24
 
 
 @pytest.mark.parametrize("op,kernel", OPERATORS)
@@ -104,7 +108,9 @@ def test_operator_matches_assembled_oracle(mto, name, op, kernel):
     FP64 vectors) in each kernel the mixed inner PCG launches, against the oracle's assembled FP64
     K x element by element: within 1e-13 of max|K x| (the pair carries ~48 bits of each entry, and
     every product and sum keeps its rounding error), and x^T K x as the launches reduce it for CG
-    within 1e-13 of x^T |K| |x|."""
+    within 1e-13 of x^T |K| |x|.  The pair's leading part alone (the multigrid cycle's copy): within
+    LEAD_TOL of max(|K||x|) and of x^T |K| |x|, and not within 1e-9 (the lo rows are really left
+    out)."""
     o = oracle_results(name)
     pr = o["pr"]
     h, fixed, f, mat, rho = gpu_setup(mto, pr)
@@ -116,11 +122,18 @@ def test_operator_matches_assembled_oracle(mto, name, op, kernel):
     for _ in range(2):
         x = rng.standard_normal(h.ndof)
         y = torch.zeros(h.ndof, dtype=torch.float64, device="cuda")
-        xKx = h.apply_operator(torch.tensor(x, device="cuda"), y, mto.OP_FP64 if op == "fp64" else mto.OP_SPLIT)
+        xKx = h.apply_operator(torch.tensor(x, device="cuda"), y,
+                               {"fp64": mto.OP_FP64, "split": mto.OP_SPLIT, "lead": mto.OP_LEAD}[op])
         want = o["K"] @ x
+        scale = absK @ np.abs(x)
+        if op == "lead":
+            err = np.abs(y.cpu().numpy() - want).max() / scale.max()
+            assert 1e-9 < err < LEAD_TOL, err
+            assert abs(xKx - x @ want) <= LEAD_TOL * (np.abs(x) @ scale), (xKx, x @ want)
+            continue
         err = np.abs(y.cpu().numpy() - want).max() / np.abs(want).max()
         assert err < 1e-13, err
-        assert abs(xKx - x @ want) <= 1e-13 * (np.abs(x) @ (absK @ np.abs(x))), (xKx, x @ want)
+        assert abs(xKx - x @ want) <= 1e-13 * (np.abs(x) @ scale), (xKx, x @ want)
     h.close()
 
 
@@ -128,7 +141,8 @@ def test_split_operator_on_large_class(mto):
     """The same comparison on a class whose split rows exceed 64 MB (the 160 x 80 binary beam's
     design tiled 2 x 2: 51,200 Q3 elements, 223 MB of hi/lo rows), where the automatic choice is the
     bulk-copy staged kernel, and through the register-pipelined and generic kernels: y = K x
-    against the oracle's assembled FP64 K x within 1e-13 of max|K x|."""
+    against the oracle's assembled FP64 K x within 1e-13 of max|K x|; the leading part alone within
+    LEAD_TOL of max(|K||x|)."""
     base = W.named("mbb_160x80_p3_d8")
     d = int(base.d[0])
     fine = W.unpack_uniform(base.rho, base.nelx, base.nely, d)
@@ -143,6 +157,7 @@ def test_split_operator_on_large_class(mto):
     rng = np.random.default_rng(11)
     xn = rng.standard_normal(h.ndof)
     want = K @ xn
+    scale = abs(K) @ np.abs(xn)
     x = torch.tensor(xn, device="cuda")
     for kernel in (mto.OPK_AUTO, mto.OPK_PIPE, mto.OPK_STAGED, mto.OPK_GENERIC):
         h.set_operator_kernel(kernel)
@@ -150,6 +165,10 @@ def test_split_operator_on_large_class(mto):
         h.apply_operator(x, y, mto.OP_SPLIT)
         err = np.abs(y.cpu().numpy() - want).max() / np.abs(want).max()
         assert err < 1e-13, (kernel, err)
+        y.zero_()
+        h.apply_operator(x, y, mto.OP_LEAD)
+        err = np.abs(y.cpu().numpy() - want).max() / scale.max()
+        assert 1e-9 < err < LEAD_TOL, (kernel, err)
     h.close()
 
 
@@ -176,9 +195,11 @@ def test_split_pair_matches_oracle_element_matrices(mto, name):
     h.close()
 
 
+@pytest.mark.parametrize("path", ["tensor", "simt"])
 @pytest.mark.parametrize("name", CASES)
-def test_tensor_core_build_matches_oracle(mto, name):
-    """The sliced tcgen05 build (8 slices of 7 bits per operand, 9 levels, FP64 level sums) against
+def test_build_paths_match_oracle(mto, name, path):
+    """The sliced tcgen05 build (8 slices of 7 bits per operand, 9 levels, FP64 level sums; the
+    default) and the FP64 CUDA-core build, each against
     the oracle's K_e element by element within 1e-14 of each element's largest entry (FP64-level:
     the slicing keeps 56 bits of each operand and drops terms below 2^-51 of the scales), its split
     pair within 2^-47 of each entry, and the compliance of a solve on it within 1e-8 of the oracle's
@@ -186,7 +207,7 @@ def test_tensor_core_build_matches_oracle(mto, name):
     o = oracle_results(name)
     pr, m = o["pr"], o["mesh"]
     h, fixed, f, mat, rho = gpu_setup(mto, pr)
-    h.set_build_path(mto.BUILD_TENSOR)
+    h.set_build_path(mto.BUILD_TENSOR if path == "tensor" else mto.BUILD_SIMT)
     for build in (mto.MTO_FP64, mto.MTO_MIXED):
         h.build_elements(rho, mat, build)
         for e in range(m.nel):
@@ -205,7 +226,6 @@ def test_tensor_core_build_matches_oracle(mto, name):
                 raise_on_noconv=False)
         C = float(f @ u)
         assert abs(C - o["C"]) <= 1e-8 * abs(o["C"]), (build, C, o["C"])
-    h.set_build_path(mto.BUILD_SIMT)
     h.close()
 
 
@@ -445,7 +465,7 @@ def abs_energy(o):
     return sum(np.abs(m.gather(e, u)) @ (np.abs(Ke[e]) @ np.abs(m.gather(e, u))) for e in range(m.nel))
 
 
-@pytest.mark.parametrize("path", ["fp64", "mixed"])
+@pytest.mark.parametrize("path", ["fp64", "mixed", "mixed_split_cycle"])
 @pytest.mark.parametrize("name", CASES)
 def test_compliance_accuracy_solve(mto, name, path):
     """The compliance-accuracy solve (MTO_NORM_ENERGY, rtol 1e-8), from a zero start and
@@ -453,10 +473,13 @@ def test_compliance_accuracy_solve(mto, name, path):
     the oracle's K on the small difference u - u*, free of cancellation) is at most 1e-8 C*.  The
     energy form 2 f^T u - u^T K u of mto_compliance_energy at the oracle's exact u reproduces C*
     within the rounding floor of any FP64 evaluation of u^T K u, 64 eps sum_e |u_e|^T |K_e| |u_e|
-    (which on the binary beam is 2e-6 C: there no FP64 energy evaluation resolves 1e-8)."""
+    (which on the binary beam is 2e-6 C: there no FP64 energy evaluation resolves 1e-8).  The mixed
+    path runs its multigrid cycle on the FP32 leading part of the split matrices (the default) and,
+    as mixed_split_cycle, on the split pair."""
     o = oracle_results(name)
     pr = o["pr"]
-    build, sprec = (getattr(mto, k) for k in PATHS[path])
+    build, sprec = (getattr(mto, k) for k in PATHS[path.replace("_split_cycle", "")])
+    mg_op = mto.MG_OP_SPLIT if path.endswith("split_cycle") else mto.MG_OP_AUTO
     h, fixed, f, mat, rho = gpu_setup(mto, pr)
     h.build_elements(rho, mat, build)
     C_star = o["C"]
@@ -469,7 +492,7 @@ def test_compliance_accuracy_solve(mto, name, path):
         if start == "warm":
             u.copy_(uo * torch.tensor(1.0 + 0.05 * rng.standard_normal(h.ndof), device="cuda"))
         it, rr = h.solve(f, u, precision=sprec, rtol=1e-8, norm=mto.NORM_ENERGY, max_iter=40000,
-                         precond=mto.PREC_MG, warm_start=start == "warm")
+                         precond=mto.PREC_MG, mg_operator=mg_op, warm_start=start == "warm")
         e = u.cpu().numpy() - o["u"]
         err = e @ (o["K"] @ e)
         assert err <= 1e-8 * C_star, (start, err / C_star, it)
