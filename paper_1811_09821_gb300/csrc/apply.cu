@@ -1379,6 +1379,16 @@ mto_status apply_block(mto_handle h, const double* x, double* y, const int* done
   return apply_all<double>(h, 1, x, y, -1, done, none, nullptr, lead);
 }
 
+mto_status apply_fine32(mto_handle h, const float* x, float* y, const int* done) {
+  ConvTest none{};
+  return apply_all<float>(h, 0, x, y, -1, done, none, nullptr, true);
+}
+
+mto_status apply_block32(mto_handle h, const float* x, float* y, const int* done) {
+  ConvTest none{};
+  return apply_all<float>(h, 1, x, y, -1, done, none, nullptr, true);
+}
+
 mto_status apply_q1(mto_handle h, const MGLevel& l, const double* x, double* y, const int* done) {
   ConvTest none{};
   ebe_kernel<1, false, double><<<ebe_blocks_p<1>(l.nel), 256, 0, h->stream>>>(

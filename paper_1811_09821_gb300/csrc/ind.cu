@@ -175,10 +175,12 @@ __global__ void gamma_d_kernel(int64_t nel, const int64_t* __restrict__ off, con
 }
 
 // ------------------------------------------------------------------------------------ QR error
-// One warp per element of a (p, d) class (Eq. 14).  Shared layout (doubles): Kf[n1 * n1] (order p+1
-// matrix, full, factorised in place), Kp[P1] (an unmodified packed copy for J^(p+1)), f[n0],
-// f1[n1], u1[n1], E[S], ue[n0], rd[n1] (reciprocal pivots), with n0 = 2 (p+1)^2, n1 = 2 (p+2)^2,
-// P1 = n1 (n1 + 1) / 2.
+// One warp per element of a (p, d) class (Eq. 14).  Shared layout (doubles): A[P1] (the order p+1
+// matrix, lower triangle packed by rows, A_ij at i (i + 1) / 2 + j, factorised in place as
+// L D L^T), f[n0], f1[n1], u1[n1], E[S], ue[n0], rd[n1] (reciprocal pivots), cl[n1] (the pivot
+// column before scaling), pr[3 n1] (the pinned rows of the unmodified matrix), with
+// n0 = 2 (p+1)^2, n1 = 2 (p+2)^2, P1 = n1 (n1 + 1) / 2.  The footprint sets how many elements an
+// SM works on at once, and the kernel is bound by GB300's FP64 pipes, so it keeps one triangle.
 // eps is invariant to rigid motions of u^(p), which are removed first (FP64) so that the element
 // energies carry no cancellation.
 __global__ void __launch_bounds__(32) qr_kernel(int p, int d, int n, const int* __restrict__ elem,
@@ -200,13 +202,15 @@ __global__ void __launch_bounds__(32) qr_kernel(int p, int d, int n, const int* 
   const int na = (p + 1) * (p + 1), nb = (p + 2) * (p + 2);
   const int n0 = 2 * na, n1 = 2 * nb, S = d * d;
   const int P1 = packed_size(n1);
-  double* Kf = sh;
-  double* Kp = Kf + n1 * n1;
-  double* f = Kp + P1;
+  double* A = sh;
+  double* f = A + P1;
   double* f1 = f + n0;
   double* u1 = f1 + n1;
   double* E = u1 + n1;
   double* ue = E + S;
+  double* rd = ue + n0;
+  double* cl = rd + n1;
+  double* pr = cl + n1;
   // gather u_e (lanes over nodes), then remove its least-squares rigid motion about the element
   // centre (translations and rotation; node sums over the warp)
   for (int ln = lane; ln < na; ln += 32) gather_node(na, sl, ln, gmap, cons, u, ue);
@@ -256,54 +260,56 @@ __global__ void __launch_bounds__(32) qr_kernel(int p, int d, int n, const int* 
     for (int kk = 0; kk < na; ++kk) s += R[jn * na + kk] * f[2 * kk + c];
     f1[i] = s;
   }
-  // K^(p+1) = sum_s E_s K0_s^(p+1): packed copy and full symmetric storage
+  // K^(p+1) = sum_s E_s K0_s^(p+1) (table rows by upper packed index (i <= j)) into the lower triangle
   for (int c = lane; c < P1; c += 32) {
     double s = 0.0;
     const double* kc = K0T1 + (size_t)c * S;
     for (int t = 0; t < S; ++t) s = fma(E[t], kc[t], s);
     int i = 0, rem = c;
     while (rem >= n1 - i) { rem -= n1 - i; ++i; }
-    int j = i + rem;
-    Kp[c] = s;
-    Kf[i * n1 + j] = s;
-    Kf[j * n1 + i] = s;
+    const int j = i + rem;
+    A[j * (j + 1) / 2 + i] = s;
   }
   __syncwarp();
   // pinned DOFs of the (p+1) element: u_x, u_y at the bottom-left vertex, u_y at the bottom-right
   // vertex; their values are those of u^(p) at the same vertices
-  const int fx0 = 0, fx1 = 1, fx2 = 2 * (p + 1) + 1;
-  const double v0 = ue[0], v1 = ue[1], v2 = ue[2 * p + 1];
-  // right-hand side on free DOFs; identity rows / columns on pinned DOFs
+  const int fx[3] = {0, 1, 2 * (p + 1) + 1};
+  const double v[3] = {ue[0], ue[1], ue[2 * p + 1]};
+  auto at = [&](int a, int b) -> double { return a >= b ? A[a * (a + 1) / 2 + b] : A[b * (b + 1) / 2 + a]; };
+  // the pinned rows before the modification (for J^(p+1)), and the right-hand side on free DOFs
   for (int i = lane; i < n1; i += 32) {
-    double r = f1[i] - Kf[i * n1 + fx0] * v0 - Kf[i * n1 + fx1] * v1 - Kf[i * n1 + fx2] * v2;
-    if (i == fx0) r = v0;
-    if (i == fx1) r = v1;
-    if (i == fx2) r = v2;
+    const double k0 = at(i, fx[0]), k1 = at(i, fx[1]), k2 = at(i, fx[2]);
+    pr[i] = k0;
+    pr[n1 + i] = k1;
+    pr[2 * n1 + i] = k2;
+    double r = f1[i] - k0 * v[0] - k1 * v[1] - k2 * v[2];
+    for (int k = 0; k < 3; ++k)
+      if (i == fx[k]) r = v[k];
     u1[i] = r;
   }
   __syncwarp();
-  for (int i = lane; i < n1; i += 32) {
-    bool pi = (i == fx0 || i == fx1 || i == fx2);
-    for (int j = 0; j < n1; ++j) {
-      bool pj = (j == fx0 || j == fx1 || j == fx2);
-      if (pi || pj) Kf[i * n1 + j] = (i == j) ? 1.0 : 0.0;
-    }
+  // identity rows and columns on the pinned DOFs
+  for (int c = lane; c < P1; c += 32) {
+    int i = (int)((sqrtf(8.0f * (float)c + 1.0f) - 1.0f) * 0.5f);
+    while (i * (i + 1) / 2 > c) --i;
+    while ((i + 1) * (i + 2) / 2 <= c) ++i;
+    const int j = c - i * (i + 1) / 2;
+    const bool pin = i == fx[0] || i == fx[1] || i == fx[2] || j == fx[0] || j == fx[1] || j == fx[2];
+    if (pin) A[c] = (i == j) ? 1.0 : 0.0;
   }
   __syncwarp();
-  // Cholesky K = L L^T (lower, right-looking).  Column c is scaled by the reciprocal of its pivot,
-  // kept in rd[c] for the substitutions; the trailing update A_ij -= L_ic L_jc (c < j <= i) runs
-  // over the m (m + 1) / 2 pairs of the trailing block spread evenly over the lanes: pair
+  // A = L D L^T (right-looking).  Column c: the pivot's reciprocal into rd[c], the column kept
+  // unscaled in cl and scaled into L; the trailing update A_ij -= L_ic cl_j (c < j <= i) runs over
+  // the m (m + 1) / 2 pairs of the trailing block spread evenly over the lanes: pair
   // t = s (s + 1) / 2 + r (0 <= r <= s < m) is row n1 - 1 - r, column n1 - 1 - s.
-  double* rd = ue + n0;   // [n1]
   for (int c = 0; c < n1; ++c) {
-    const double dcc = sqrt(Kf[c * n1 + c]);
-    const double inv = 1.0 / dcc;
-    __syncwarp();
-    for (int i = c + 1 + lane; i < n1; i += 32) Kf[i * n1 + c] *= inv;
-    if (lane == 0) {
-      Kf[c * n1 + c] = dcc;
-      rd[c] = inv;
+    const double inv = 1.0 / A[c * (c + 1) / 2 + c];
+    for (int i = c + 1 + lane; i < n1; i += 32) {
+      const double a = A[i * (i + 1) / 2 + c];
+      cl[i] = a;
+      A[i * (i + 1) / 2 + c] = a * inv;
     }
+    if (lane == 0) rd[c] = inv;
     __syncwarp();
     const int m = n1 - 1 - c;
     const int T = m * (m + 1) / 2;
@@ -313,32 +319,31 @@ __global__ void __launch_bounds__(32) qr_kernel(int p, int d, int n, const int* 
       while ((s + 1) * (s + 2) / 2 <= t) ++s;
       const int r = t - s * (s + 1) / 2;
       const int i = n1 - 1 - r, j = n1 - 1 - s;
-      Kf[i * n1 + j] -= Kf[i * n1 + c] * Kf[j * n1 + c];
+      A[i * (i + 1) / 2 + j] -= A[i * (i + 1) / 2 + c] * cl[j];
     }
     __syncwarp();
   }
-  // L y = b, then L^T x = y, column by column (each solved entry updates the rest over the lanes)
+  // L y = b, y <- D^-1 y, L^T x = y, column by column (each solved entry updates the rest over the
+  // lanes)
   for (int j = 0; j < n1; ++j) {
-    const double yj = u1[j] * rd[j];
-    __syncwarp();
-    for (int i = j + 1 + lane; i < n1; i += 32) u1[i] -= Kf[i * n1 + j] * yj;
-    if (lane == 0) u1[j] = yj;
+    const double yj = u1[j];
+    for (int i = j + 1 + lane; i < n1; i += 32) u1[i] -= A[i * (i + 1) / 2 + j] * yj;
     __syncwarp();
   }
+  for (int i = lane; i < n1; i += 32) u1[i] *= rd[i];
+  __syncwarp();
   for (int j = n1 - 1; j >= 0; --j) {
-    const double xj = u1[j] * rd[j];
-    __syncwarp();
-    for (int i = lane; i < j; i += 32) u1[i] -= Kf[j * n1 + i] * xj;
-    if (lane == 0) u1[j] = xj;
+    const double xj = u1[j];
+    for (int i = lane; i < j; i += 32) u1[i] -= A[j * (j + 1) / 2 + i] * xj;
     __syncwarp();
   }
-  // J^(p+1) = u1^T K u1 / 2 from the unmodified packed copy
+  // J^(p+1) = u1^T K u1 / 2 = (u1_f^T f1_f + v^T (K u1)_pinned) / 2: on the free rows K u1 is the
+  // right-hand side f1, on the pinned rows the saved rows of the unmodified matrix give it
   double j1 = 0.0;
-  for (int c = lane; c < P1; c += 32) {
-    int i = 0, rem = c;
-    while (rem >= n1 - i) { rem -= n1 - i; ++i; }
-    int j = i + rem;
-    j1 += (i == j ? 1.0 : 2.0) * Kp[c] * u1[i] * u1[j];
+  for (int i = lane; i < n1; i += 32) {
+    const bool pin = i == fx[0] || i == fx[1] || i == fx[2];
+    if (!pin) j1 += u1[i] * f1[i];
+    j1 += u1[i] * (v[0] * pr[i] + v[1] * pr[n1 + i] + v[2] * pr[2 * n1 + i]);
   }
   for (int o = 16; o > 0; o >>= 1) j1 += __shfl_xor_sync(0xffffffffu, j1, o);
   j1 *= 0.5;
@@ -769,7 +774,7 @@ mto_status indicators(mto_handle h, const double* u, const double* rho, const mt
     const BClass& b1 = h->bc_qr[ci];
     const PClass& c = h->pc[b.p];
     const int n0 = 2 * (b.p + 1) * (b.p + 1), n1 = 2 * (b.p + 2) * (b.p + 2);
-    size_t smem = sizeof(double) * ((size_t)n1 * n1 + packed_size(n1) + n0 + n1 + n1 + b.S + n0 + n1);
+    size_t smem = sizeof(double) * ((size_t)packed_size(n1) + n0 + n1 + n1 + b.S + n0 + n1 + n1 + 3 * n1);
     if (smem > 48 * 1024) cudaFuncSetAttribute(qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     qr_kernel<<<b.n, 32, smem, h->stream>>>(b.p, b.d, b.n, b.elem, b.slot, c.L, c.dpos, c.gmap, h->cons_d,
                                             c.K64, c.K32, c.K32lo, b1.K0T,

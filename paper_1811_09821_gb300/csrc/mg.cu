@@ -18,8 +18,13 @@
 // a power iteration (x 1.1), the same polynomial before and after the coarse correction, so the
 // cycle is a symmetric positive definite preconditioner.  Supported DOFs are masked on every level
 // (they coincide with vertices of the coarser grids for the clamped edge and the MBB supports; the
-// fine-level mask is applied to every transfer).  All levels keep FP64 vectors; level 0 applies
-// whichever element matrices were built (FP64 or the split-precision pair).
+// fine-level mask is applied to every transfer).  With FP64 matrices, or a mixed build with
+// mg_operator SPLIT, every level keeps FP64 vectors and level 0 applies the built matrices (FP64
+// or the split pair).  A mixed build otherwise runs the cycle on FP32 copies: FP32 vectors on
+// every level, the FP32 leading part of the split pair on level 0, FP32 stencils on the Q1 levels,
+// FP32 arithmetic in the level kernels; the coarsest inverse and the reductions stay FP64.  A
+// preconditioner only has to be a fixed operator; the outer PCG keeps the split pair and FP64
+// vectors, and its residuals are refined in FP64.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -38,6 +43,9 @@ constexpr int kPowerIts = 30;
 constexpr int kCoarseDegree = 4;      // Chebyshev degree on the Q1 levels (the fine level: the option)
 constexpr int kMaxDegree = 16;        // largest smoothing degree (coefficient table size)
 constexpr int kMGBlocks = 152 * 8;    // vector kernels: one full wave of 8 blocks per SM
+
+// the cycle runs on FP32 copies with FP32 vectors (mixed builds, mg_operator LEAD or AUTO)
+bool mg_fp32_cycle(mto_handle h) { return h->mg_lead && h->built_precision == MTO_MIXED; }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -232,9 +240,9 @@ __global__ void __launch_bounds__(256) mg_stencil_kernel(int nx, int ny, const d
 // FP64 stencil and arithmetic, or (TS = float, the cycle's FP32 copy) the stencil rounded to FP32
 // with x rounded to FP32 and FP32 products and sums (36 FP64 FMAs per vertex would make the apply
 // bound by GB300's FP64 pipes rather than by memory)
-template <typename TS>
+template <typename TS, typename V>
 __global__ void __launch_bounds__(256) mg_stencil_apply_kernel(int nx, int ny, const TS* __restrict__ S,
-                                                               const double* __restrict__ x, double* __restrict__ y,
+                                                               const V* __restrict__ x, V* __restrict__ y,
                                                                const int* __restrict__ done) {
   if (done && *done) return;
   const int64_t nv = (int64_t)(nx + 1) * (ny + 1);
@@ -256,8 +264,8 @@ __global__ void __launch_bounds__(256) mg_stencil_apply_kernel(int nx, int ny, c
         y1 = fma(S[(size_t)(o * 4 + 3) * nv + v], x1, y1);
       }
     }
-    y[2 * v] = (double)y0;
-    y[2 * v + 1] = (double)y1;
+    y[2 * v] = (V)y0;
+    y[2 * v + 1] = (V)y1;
   }
 }
 
@@ -320,45 +328,58 @@ __global__ void __launch_bounds__(256) mg_gj_step_kernel(int N, int k, const dou
   }
 }
 
-// x = Ainv b (one warp per row)
+// x = Ainv b (one warp per row; FP64 inverse and sums, vectors of the cycle's type)
+template <typename V>
 __global__ void __launch_bounds__(256) mg_coarse_solve_kernel(int N, const double* __restrict__ Ainv,
-                                                              const double* __restrict__ b, double* __restrict__ x,
+                                                              const V* __restrict__ b, V* __restrict__ x,
                                                               const int* __restrict__ done) {
   if (done && *done) return;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, l = threadIdx.x & 31;
   if (w >= N) return;
   double s = 0.0;
-  for (int j = l; j < N; j += 32) s = fma(Ainv[(size_t)w * N + j], b[j], s);
+  for (int j = l; j < N; j += 32) s = fma(Ainv[(size_t)w * N + j], (double)b[j], s);
   s = warp_sum(s);
-  if (l == 0) x[w] = s;
+  if (l == 0) x[w] = (V)s;
 }
 
 // ---------------------------------------------------------------- smoothing and transfers
+// The cycle's vectors are of type V: double, or float for the cycle on FP32 copies (mixed builds,
+// mg_operator LEAD), where the level kernels then also compute in FP32.
+//
 // One Chebyshev step on level vectors: r = D^-1 (b - q) (q = A x, then cleared), step 0:
 // d = r / theta, step s > 0: d = rho_s rho_{s-1} d + (2 rho_s / delta) r; x = d (xzero) or x += d.
 // With dpart set, also b^T x of the updated x (the PCG's r^T z after the cycle's last step),
-// reduced by the last block to finish in index order into *dres.
-__global__ void __launch_bounds__(256) mg_cheb_kernel(int64_t n, const double* __restrict__ b, double* __restrict__ q,
-                                                      const double* __restrict__ invd, double* __restrict__ x,
-                                                      double* __restrict__ d, const double2* __restrict__ coef,
+// reduced by the last block to finish in index order into *dres.  With zout set (the FP32
+// cycle's last step), the updated x goes to the FP64 output zout instead of x and the reduction
+// takes its b from bout (FP64).
+template <typename V>
+__global__ void __launch_bounds__(256) mg_cheb_kernel(int64_t n, const V* __restrict__ b, V* __restrict__ q,
+                                                      const V* __restrict__ invd, V* __restrict__ x,
+                                                      V* __restrict__ d, const double2* __restrict__ coef,
                                                       int step, int xzero, const int* __restrict__ done,
                                                       double* __restrict__ dpart, unsigned* __restrict__ dcnt,
-                                                      double* __restrict__ dres, int given, int zq) {
+                                                      double* __restrict__ dres, int given, int zq,
+                                                      double* __restrict__ zout, const double* __restrict__ bout) {
   if (done && *done) return;
   const double2 cc = coef[step];   // (c1, c2), precomputed per level
-  const double c1 = cc.x, c2 = cc.y;
+  const V c1 = (V)cc.x, c2 = (V)cc.y;
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double bi = b[i];
+    const V bi = b[i];
     // given: q already holds the preconditioned residual (element-block smoothing), else the
     // Jacobi-scaled residual is formed here from q = A x
-    const double r = given ? (invd[i] != 0.0 ? q[i] : 0.0) : invd[i] * (bi - q[i]);
-    if (zq) q[i] = 0.0;   // else a separate launch clears q (see mg_zero_kernel)
-    const double dn = step > 0 ? fma(c1, d[i], c2 * r) : c2 * r;   // c1 = 0 at step 0
+    const V r = given ? (invd[i] != V(0) ? q[i] : V(0)) : invd[i] * (bi - q[i]);
+    if (zq) q[i] = V(0);   // else a separate launch clears q (see mg_zero_kernel)
+    const V dn = step > 0 ? fma(c1, d[i], c2 * r) : c2 * r;   // c1 = 0 at step 0
     d[i] = dn;
-    const double xn = xzero ? dn : x[i] + dn;
-    x[i] = xn;
-    acc = fma(bi, xn, acc);
+    const V xn = xzero ? dn : x[i] + dn;
+    if (zout) {
+      zout[i] = (double)xn;
+      acc = fma(bout[i], (double)xn, acc);
+    } else {
+      x[i] = xn;
+      acc = fma((double)bi, (double)xn, acc);
+    }
   }
   if (!dpart) return;
   __shared__ int last;
@@ -382,22 +403,36 @@ __global__ void __launch_bounds__(256) mg_cheb_kernel(int64_t n, const double* _
 }
 
 // element-block smoothing: w = b - q on free DOFs (0 on supports); q is cleared by the next launch
-__global__ void __launch_bounds__(256) mg_block_resid_kernel(int64_t n, const double* __restrict__ b,
-                                                             const double* __restrict__ q,
-                                                             const double* __restrict__ invd,
-                                                             double* __restrict__ w, const int* __restrict__ done) {
+template <typename V>
+__global__ void __launch_bounds__(256) mg_block_resid_kernel(int64_t n, const V* __restrict__ b,
+                                                             const V* __restrict__ q, const V* __restrict__ invd,
+                                                             V* __restrict__ w, const int* __restrict__ done) {
   if (done && *done) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    w[i] = invd[i] != 0.0 ? (b ? b[i] : 0.0) - q[i] : 0.0;
+    w[i] = invd[i] != V(0) ? (b ? b[i] : V(0)) - q[i] : V(0);
 }
 
 // v = 0 as its own launch: on GB300 a kernel that reads an array and stores zeros into it streams
 // at about a third of the rate of the same kernel without that store (see zero_kernel in apply.cu),
 // so the large accumulators are cleared separately
-__global__ void __launch_bounds__(256) mg_zero_kernel(int64_t n, double* __restrict__ v, const int* __restrict__ done) {
+template <typename V>
+__global__ void __launch_bounds__(256) mg_zero_kernel(int64_t n, V* __restrict__ v, const int* __restrict__ done) {
   if (done && *done) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    v[i] = 0.0;
+    v[i] = V(0);
+}
+
+// the FP32 cycle's entry: b32 = r (rounded), its level-0 vectors' FP32 copy of the inverse diagonal
+__global__ void __launch_bounds__(256) mg_demote_kernel(int64_t n, const double* __restrict__ r, float* __restrict__ b,
+                                                        const int* __restrict__ done) {
+  if (done && *done) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)r[i];
+}
+
+__global__ void __launch_bounds__(256) mg_round_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
 }
 
 // accumulators of at least this many entries are cleared by mg_zero_kernel (smaller ones, which stay
@@ -406,20 +441,20 @@ constexpr int64_t kSeparateZero = 1 << 20;
 
 // level 0 -> 1: b1 = P^T r by the vertex-wise transposed table, the residual r = b - q formed on
 // the fly on free DOFs (q = A x stays; the prolongation clears it)
+template <typename V>
 __global__ void __launch_bounds__(256) mg_restrict0_kernel(int64_t nv, const int* __restrict__ ptr,
                                                            const int* __restrict__ node, const double* __restrict__ w,
-                                                           const double* __restrict__ b, const double* __restrict__ q,
-                                                           const double* __restrict__ invd,
-                                                           const double* __restrict__ mask, double* __restrict__ b1,
-                                                           const int* __restrict__ done) {
+                                                           const V* __restrict__ b, const V* __restrict__ q,
+                                                           const V* __restrict__ invd, const V* __restrict__ mask,
+                                                           V* __restrict__ b1, const int* __restrict__ done) {
   if (done && *done) return;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
-    double s0 = 0.0, s1 = 0.0;
+    V s0 = V(0), s1 = V(0);
     for (int k = ptr[v]; k < ptr[v + 1]; ++k) {
-      const double wk = w[k];
+      const V wk = (V)w[k];
       const size_t g = 2 * (size_t)node[k];
-      if (invd[g] != 0.0) s0 = fma(wk, b[g] - q[g], s0);
-      if (invd[g + 1] != 0.0) s1 = fma(wk, b[g + 1] - q[g + 1], s1);
+      if (invd[g] != V(0)) s0 = fma(wk, b[g] - q[g], s0);
+      if (invd[g + 1] != V(0)) s1 = fma(wk, b[g + 1] - q[g + 1], s1);
     }
     b1[2 * v] = mask[2 * v] * s0;
     b1[2 * v + 1] = mask[2 * v + 1] * s1;
@@ -427,68 +462,70 @@ __global__ void __launch_bounds__(256) mg_restrict0_kernel(int64_t nv, const int
 }
 
 // level 1 -> 0: x += P x1 on free DOFs; q (A x of the pre-smoothed x) cleared
+template <typename V>
 __global__ void __launch_bounds__(256) mg_prolong0_kernel(int64_t nn, const int* __restrict__ idx,
-                                                          const double* __restrict__ w, const double* __restrict__ x1,
-                                                          const double* __restrict__ invd, double* __restrict__ x,
-                                                          double* __restrict__ q, const int* __restrict__ done) {
+                                                          const double* __restrict__ w, const V* __restrict__ x1,
+                                                          const V* __restrict__ invd, V* __restrict__ x,
+                                                          V* __restrict__ q, const int* __restrict__ done) {
   if (done && *done) return;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
-    double s0 = 0.0, s1 = 0.0;
+    V s0 = V(0), s1 = V(0);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const double wk = w[4 * g + k];
+      const V wk = (V)w[4 * g + k];
       const size_t v = 2 * (size_t)idx[4 * g + k];
       s0 = fma(wk, x1[v], s0);
       s1 = fma(wk, x1[v + 1], s1);
     }
-    if (invd[2 * g] != 0.0) x[2 * g] += s0;
-    if (invd[2 * g + 1] != 0.0) x[2 * g + 1] += s1;
-    q[2 * g] = 0.0;
-    q[2 * g + 1] = 0.0;
+    if (invd[2 * g] != V(0)) x[2 * g] += s0;
+    if (invd[2 * g + 1] != V(0)) x[2 * g + 1] += s1;
+    q[2 * g] = V(0);
+    q[2 * g + 1] = V(0);
   }
 }
 
 // level l -> l+1 on vertex grids (full weighting: the transpose of bilinear interpolation) of the
 // residual r = b - q formed on the fly on free DOFs (q stays; the prolongation clears it)
+template <typename V>
 __global__ void __launch_bounds__(256) mg_restrict_h_kernel(int nxc, int nyc, int nxf, int nyf,
-                                                            const double* __restrict__ b, const double* __restrict__ q,
-                                                            const double* __restrict__ invd,
-                                                            const double* __restrict__ mask,
-                                                            double* __restrict__ bc, const int* __restrict__ done) {
+                                                            const V* __restrict__ b, const V* __restrict__ q,
+                                                            const V* __restrict__ invd, const V* __restrict__ mask,
+                                                            V* __restrict__ bc, const int* __restrict__ done) {
   if (done && *done) return;
   const int64_t nvc = (int64_t)(nxc + 1) * (nyc + 1);
-  for (int64_t V = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; V < nvc; V += (int64_t)gridDim.x * blockDim.x) {
-    const int I = (int)(V % (nxc + 1)), J = (int)(V / (nxc + 1));
-    double s0 = 0.0, s1 = 0.0;
+  for (int64_t Vx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; Vx < nvc; Vx += (int64_t)gridDim.x * blockDim.x) {
+    const int I = (int)(Vx % (nxc + 1)), J = (int)(Vx / (nxc + 1));
+    V s0 = V(0), s1 = V(0);
     for (int dy = -1; dy <= 1; ++dy) {
       const int j = 2 * J + dy;
       if (j < 0 || j > nyf) continue;
-      const double wy = dy == 0 ? 1.0 : 0.5;
+      const V wy = dy == 0 ? V(1) : V(0.5);
       for (int dx = -1; dx <= 1; ++dx) {
         const int i = 2 * I + dx;
         if (i < 0 || i > nxf) continue;
-        const double wgt = wy * (dx == 0 ? 1.0 : 0.5);
+        const V wgt = wy * (dx == 0 ? V(1) : V(0.5));
         const size_t f = 2 * ((size_t)j * (nxf + 1) + i);
-        if (invd[f] != 0.0) s0 = fma(wgt, b[f] - q[f], s0);
-        if (invd[f + 1] != 0.0) s1 = fma(wgt, b[f + 1] - q[f + 1], s1);
+        if (invd[f] != V(0)) s0 = fma(wgt, b[f] - q[f], s0);
+        if (invd[f + 1] != V(0)) s1 = fma(wgt, b[f + 1] - q[f + 1], s1);
       }
     }
-    bc[2 * V] = mask[2 * V] * s0;
-    bc[2 * V + 1] = mask[2 * V + 1] * s1;
+    bc[2 * Vx] = mask[2 * Vx] * s0;
+    bc[2 * Vx + 1] = mask[2 * Vx + 1] * s1;
   }
 }
 
 // level l+1 -> l: x += bilinear interpolation of the coarse correction (free DOFs); q cleared
-__global__ void __launch_bounds__(256) mg_prolong_h_kernel(int nxc, int nxf, int nyf, const double* __restrict__ xc,
-                                                           const double* __restrict__ mask, double* __restrict__ xf,
-                                                           double* __restrict__ q, const int* __restrict__ done) {
+template <typename V>
+__global__ void __launch_bounds__(256) mg_prolong_h_kernel(int nxc, int nxf, int nyf, const V* __restrict__ xc,
+                                                           const V* __restrict__ mask, V* __restrict__ xf,
+                                                           V* __restrict__ q, const int* __restrict__ done) {
   if (done && *done) return;
   const int64_t nvf = (int64_t)(nxf + 1) * (nyf + 1);
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nvf; v += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(v % (nxf + 1)), j = (int)(v / (nxf + 1));
     const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1;
-    const double wi = (i & 1) ? 0.5 : 1.0, wj = (j & 1) ? 0.5 : 1.0;
-    double s0 = 0.0, s1 = 0.0;
+    const V wi = (i & 1) ? V(0.5) : V(1), wj = (j & 1) ? V(0.5) : V(1);
+    V s0 = V(0), s1 = V(0);
     const int is[2] = {i0, i1}, js[2] = {j0, j1};
     const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1;
     for (int b = 0; b < nj; ++b)
@@ -499,8 +536,8 @@ __global__ void __launch_bounds__(256) mg_prolong_h_kernel(int nxc, int nxf, int
       }
     xf[2 * v] += mask[2 * v] * s0;
     xf[2 * v + 1] += mask[2 * v + 1] * s1;
-    q[2 * v] = 0.0;
-    q[2 * v + 1] = 0.0;
+    q[2 * v] = V(0);
+    q[2 * v + 1] = V(0);
   }
 }
 
@@ -583,17 +620,19 @@ int vec_grid(int64_t n) { return grid_for(n, 256, kMGBlocks); }
 // ---------------------------------------------------------------- host side
 void mg_release(mto_handle h) {
   for (auto& l : h->mg)
-    for (void* p : {(void*)l.gmap, (void*)l.K, (void*)l.S, (void*)l.S32, (void*)l.mask, (void*)l.invd, (void*)l.x, (void*)l.b,
+    for (void* p : {(void*)l.gmap, (void*)l.K, (void*)l.S, (void*)l.S32, (void*)l.invd32, (void*)l.mask32, (void*)l.mask, (void*)l.invd, (void*)l.x, (void*)l.b,
                     (void*)l.q, (void*)l.d})
       cudaFree(p);
   h->mg.clear();
   for (void* p : {(void*)h->mg_pidx, (void*)h->mg_pw, (void*)h->mg_rptr, (void*)h->mg_rnode, (void*)h->mg_rw,
-                  (void*)h->mg_btab, (void*)h->mg_v0, (void*)h->mg_q0, (void*)h->mg_d0, (void*)h->mg_Ainv,
+                  (void*)h->mg_btab, (void*)h->mg_v0, (void*)h->mg_q0, (void*)h->mg_d0, (void*)h->mg_f32,
+                  (void*)h->mg_Ainv,
                   (void*)h->mg_Awork,
                   (void*)h->mg_lmax, (void*)h->mg_coef, (void*)h->mg_part, (void*)h->mg_cnt, (void*)h->mg_res})
     cudaFree(p);
   h->mg_pidx = nullptr;
   h->mg_pw = h->mg_rw = h->mg_btab = h->mg_v0 = h->mg_q0 = h->mg_d0 = h->mg_Ainv = h->mg_lmax = nullptr;
+  h->mg_f32 = nullptr;
   h->mg_Awork = h->mg_Acur = nullptr;
   h->mg_coef = nullptr;
   h->mg_part = h->mg_res = nullptr;
@@ -643,6 +682,7 @@ mto_status mg_setup(mto_handle h) {
       MTO_TRY(mto_alloc(h, &L.S32, (size_t)36 * L.nv));
     }
     for (double** v : {&L.mask, &L.invd, &L.x, &L.b, &L.q, &L.d}) MTO_TRY(mto_alloc(h, v, L.n));
+    for (float** v : {&L.invd32, &L.mask32}) MTO_TRY(mto_alloc(h, v, L.n));
     MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(L.q, 0, L.n * sizeof(double), h->stream), "memset"));
   }
 
@@ -719,6 +759,7 @@ mto_status mg_setup(mto_handle h) {
   MTO_TRY(mto_cuda_check(h, cudaMemcpy(h->mg_rw, rw.data(), rw.size() * sizeof(double), cudaMemcpyHostToDevice), "upload"));
 
   for (double** v : {&h->mg_v0, &h->mg_q0, &h->mg_d0}) MTO_TRY(mto_alloc(h, v, h->ndof));
+  MTO_TRY(mto_alloc(h, &h->mg_f32, (size_t)6 * h->ndof));
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->mg_q0, 0, h->ndof * sizeof(double), h->stream), "memset"));
   MTO_TRY(mto_alloc(h, &h->mg_Ainv, (size_t)ncoarse * ncoarse));
   MTO_TRY(mto_alloc(h, &h->mg_Awork, (size_t)ncoarse * ncoarse));
@@ -763,6 +804,23 @@ mto_status mg_set_masks(mto_handle h) {
 
 namespace {
 
+// y = A x on Q1 level l (written, not accumulated): the vertex stencil where it exists, in FP32
+// when the cycle runs on FP32 copies (FP32 vectors in the cycle, FP64 ones in the power
+// iteration), else in FP64; the coarsest level (no stencil) by its element matrices
+mto_status mg_level_apply(mto_handle h, const MGLevel& l, const double* x, double* y, const int* done) {
+  if (!l.S) return apply_q1(h, l, x, y, done);
+  if (mg_fp32_cycle(h))
+    mg_stencil_apply_kernel<float, double><<<vec_grid(l.nv), 256, 0, h->stream>>>(l.nx, l.ny, l.S32, x, y, done);
+  else
+    mg_stencil_apply_kernel<double, double><<<vec_grid(l.nv), 256, 0, h->stream>>>(l.nx, l.ny, l.S, x, y, done);
+  return mto_after_launch(h, "mg_stencil_apply_kernel");
+}
+mto_status mg_level_apply(mto_handle h, const MGLevel& l, const float* x, float* y, const int* done) {
+  if (!l.S32) return mto_fail(h, MTO_EINVAL, "mg: no stencil on this level");
+  mg_stencil_apply_kernel<float, float><<<vec_grid(l.nv), 256, 0, h->stream>>>(l.nx, l.ny, l.S32, x, y, done);
+  return mto_after_launch(h, "mg_stencil_apply_kernel");
+}
+
 // lmax of D^-1 A on one level by power iteration (level < 0: the fine operator)
 mto_status mg_power(mto_handle h, int level, double* lmax_out) {
   const bool fine = level < 0;
@@ -776,14 +834,14 @@ mto_status mg_power(mto_handle h, int level, double* lmax_out) {
   MTO_TRY(mto_after_launch(h, "mg_pow_init_kernel"));
   const bool block = fine && h->mg_block;   // lmax of M^-1 A, M^-1 the element-block inverse
   for (int it = 0; it < kPowerIts; ++it) {
-    if (fine) MTO_TRY(apply_fine(h, v, q, nullptr, h->mg_lead != 0));
-    else MTO_TRY(mg_apply_level(h, h->mg[level], v, q, nullptr));
+    if (fine) MTO_TRY(apply_fine(h, v, q, nullptr, h->mg_lead));
+    else MTO_TRY(mg_level_apply(h, h->mg[level], v, q, nullptr));
     if (block) {
-      mg_block_resid_kernel<<<grd, 256, 0, h->stream>>>(n, nullptr, q, invd, w, nullptr);   // w = -A v
+      mg_block_resid_kernel<double><<<grd, 256, 0, h->stream>>>(n, nullptr, q, invd, w, nullptr);   // w = -A v
       MTO_TRY(mto_after_launch(h, "mg_block_resid_kernel"));
-      mg_zero_kernel<<<grd, 256, 0, h->stream>>>(n, q, nullptr);
+      mg_zero_kernel<double><<<grd, 256, 0, h->stream>>>(n, q, nullptr);
       MTO_TRY(mto_after_launch(h, "mg_zero_kernel"));
-      MTO_TRY(apply_block(h, w, q, nullptr, h->mg_lead & 1));
+      MTO_TRY(apply_block(h, w, q, nullptr, h->mg_lead));
     }
     mg_pow_step_kernel<<<grd, 256, 0, h->stream>>>(n, q, invd, w, h->mg_part, h->mg_cnt, h->mg_res, block);
     MTO_TRY(mto_after_launch(h, "mg_pow_step_kernel"));
@@ -811,12 +869,13 @@ mto_status mg_select_smoother(mto_handle h, int smoother) {
   return MTO_OK;
 }
 
-// The copy of the element matrices the cycle applies with the MTO_MIXED build (all its split-pair
-// applies on the FP32 leading part, or none); a change rebuilds the bounds and drops the graphs.
+// The copy of the matrices the cycle applies with the MTO_MIXED build (FP32 copies and FP32
+// vectors, or the split pair and FP64 stencils with FP64 vectors); a change rebuilds the bounds and
+// drops the graphs.
 mto_status mg_select_operator(mto_handle h, int op) {
   if (op != MTO_MG_OP_AUTO && op != MTO_MG_OP_SPLIT && op != MTO_MG_OP_LEAD)
     return mto_fail(h, MTO_EINVAL, "mto_solve: bad mg_operator");
-  const int lead = op == MTO_MG_OP_SPLIT ? 0 : 7;
+  const bool lead = op != MTO_MG_OP_SPLIT;
   if (lead == h->mg_lead) return MTO_OK;
   MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "mto_solve"));
   h->mg_lead = lead;
@@ -898,6 +957,16 @@ mto_status mg_build(mto_handle h) {
   MTO_TRY(mto_after_launch(h, "mg_cheb_coef_kernel"));
   for (auto& L : h->mg) MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(L.q, 0, L.n * sizeof(double), h->stream), "memset"));
   MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->mg_q0, 0, h->ndof * sizeof(double), h->stream), "memset"));
+  // FP32 copies of the masks and inverse diagonals for the FP32 cycle; its level-0 vectors cleared
+  for (auto& L : h->mg) {
+    mg_round_kernel<<<vec_grid(L.n), 256, 0, h->stream>>>(L.n, L.invd, L.invd32);
+    MTO_TRY(mto_after_launch(h, "mg_round_kernel"));
+    mg_round_kernel<<<vec_grid(L.n), 256, 0, h->stream>>>(L.n, L.mask, L.mask32);
+    MTO_TRY(mto_after_launch(h, "mg_round_kernel"));
+  }
+  MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(h->mg_f32, 0, 5 * h->ndof * sizeof(float), h->stream), "memset"));
+  mg_round_kernel<<<vec_grid(h->ndof), 256, 0, h->stream>>>(h->ndof, h->invd64, h->mg_f32 + 5 * h->ndof);
+  MTO_TRY(mto_after_launch(h, "mg_round_kernel"));
   int err = 0;
   MTO_TRY(mto_cuda_check(h, cudaMemcpyAsync(h->host_flags + 8, h->flags + 6, sizeof(int), cudaMemcpyDeviceToHost,
                                             h->stream), "copy"));
@@ -908,14 +977,46 @@ mto_status mg_build(mto_handle h) {
   return MTO_OK;
 }
 
-// z = M^-1 r: one V-cycle.  Level-0 vectors: b = r, x = z, q = mg_q0 (A x, kept zero between
-// uses), d = mg_d0 (Chebyshev direction).  With dot_part set, the last smoothing step also reduces
-// r^T z into *dot_res (block partials in dot_part, counter dot_cnt).
-mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const int* done, double* dot_part,
-                     unsigned* dot_cnt, double* dot_res) {
+namespace {
+
+// the level vectors in the cycle's type (the FP32 cycle keeps its FP32 vectors in the FP64 buffers)
+template <typename V>
+struct LevelV {
+  V *x, *b, *q, *d;
+  const V *invd, *mask;
+};
+template <typename V>
+LevelV<V> level_vecs(const MGLevel& L);
+template <>
+LevelV<double> level_vecs<double>(const MGLevel& L) {
+  return {L.x, L.b, L.q, L.d, L.invd, L.mask};
+}
+template <>
+LevelV<float> level_vecs<float>(const MGLevel& L) {
+  return {reinterpret_cast<float*>(L.x), reinterpret_cast<float*>(L.b), reinterpret_cast<float*>(L.q),
+          reinterpret_cast<float*>(L.d), L.invd32, L.mask32};
+}
+
+// y += A x (block: the element blocks) on level 0 in the cycle's vector type
+mto_status fine_apply(mto_handle h, const double* x, double* y, const int* done, bool lead, bool block) {
+  return block ? apply_block(h, x, y, done, lead) : apply_fine(h, x, y, done, lead);
+}
+mto_status fine_apply(mto_handle h, const float* x, float* y, const int* done, bool, bool block) {
+  return block ? apply_block32(h, x, y, done) : apply_fine32(h, x, y, done);
+}
+
+// One V-cycle in vector type V.  Level-0 vectors: b (the residual), x (the output), q (A x, kept
+// zero between uses), d (Chebyshev direction), v (element-block scratch), invd.  With dot_part
+// set, the last smoothing step also reduces b^T x into *dot_res; with zout set (the FP32 cycle),
+// that step writes x to zout in FP64 and takes the reduction's b from bout.
+template <typename V>
+mto_status mg_cycle(mto_handle h, const V* b0, V* x0, V* q0, V* d0, V* v0, const V* invd0, int degree,
+                    const int* done, double* dot_part, unsigned* dot_cnt, double* dot_res, double* zout,
+                    const double* bout) {
   const int nl = (int)h->mg.size();
-  auto smooth = [&](int lev, const double* b, double* x, double* q, double* d, const double* invd, int64_t n,
-                    bool pre, bool with_dot) -> mto_status {
+  const bool lead = h->mg_lead;
+  auto smooth = [&](int lev, const V* b, V* x, V* q, V* d, const V* invd, int64_t n, bool pre,
+                    bool last) -> mto_status {
     const int k = lev < 0 ? degree : (h->mg_q1deg > 0 ? h->mg_q1deg : kCoarseDegree);
     const double2* cf = h->mg_coef + (size_t)(lev + 1) * kMaxDegree;
     const int grd = vec_grid(n);
@@ -923,93 +1024,117 @@ mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const
     for (int s = 0; s < k; ++s) {
       const bool skip_apply = pre && s == 0;   // x = 0: A x = 0
       if (!skip_apply) {
-        if (lev < 0) MTO_TRY(apply_fine(h, x, q, done, h->mg_lead & (pre ? 2 : 4)));
+        if (lev < 0) MTO_TRY(fine_apply(h, x, q, done, lead, false));
         else {
           TimedScope ts(h, F_PRECOND);
-          MTO_TRY(mg_apply_level(h, h->mg[lev], x, q, done));
+          MTO_TRY(mg_level_apply(h, h->mg[lev], x, q, done));
         }
       }
       if (block) {   // q <- M^-1 (b - A x)
         {
           TimedScope ts(h, F_PRECOND);
-          mg_block_resid_kernel<<<grd, 256, 0, h->stream>>>(n, b, q, invd, h->mg_v0, done);
+          mg_block_resid_kernel<V><<<grd, 256, 0, h->stream>>>(n, b, q, invd, v0, done);
           MTO_TRY(mto_after_launch(h, "mg_block_resid_kernel"));
-          mg_zero_kernel<<<grd, 256, 0, h->stream>>>(n, q, done);
+          mg_zero_kernel<V><<<grd, 256, 0, h->stream>>>(n, q, done);
           MTO_TRY(mto_after_launch(h, "mg_zero_kernel"));
         }
-        MTO_TRY(apply_block(h, h->mg_v0, q, done, h->mg_lead & 1));
+        MTO_TRY(fine_apply(h, v0, q, done, lead, true));
       }
       TimedScope ts(h, F_PRECOND);
-      const bool dot = with_dot && s == k - 1;
+      const bool fin = last && s == k - 1;
       const bool sep = n >= kSeparateZero;
-      mg_cheb_kernel<<<grd, 256, 0, h->stream>>>(n, b, q, invd, x, d, cf, s, pre && s == 0, done,
-                                                  dot ? dot_part : nullptr, dot_cnt, dot_res, block, !sep);
+      mg_cheb_kernel<V><<<grd, 256, 0, h->stream>>>(n, b, q, invd, x, d, cf, s, pre && s == 0, done,
+                                                     fin ? dot_part : nullptr, dot_cnt, dot_res, block, !sep,
+                                                     fin ? zout : nullptr, bout);
       MTO_TRY(mto_after_launch(h, "mg_cheb_kernel"));
       if (sep) {
-        mg_zero_kernel<<<grd, 256, 0, h->stream>>>(n, q, done);
+        mg_zero_kernel<V><<<grd, 256, 0, h->stream>>>(n, q, done);
         MTO_TRY(mto_after_launch(h, "mg_zero_kernel"));
       }
     }
     return MTO_OK;
   };
   // level 0 pre-smoothing and residual
-  MTO_TRY(smooth(-1, r, z, h->mg_q0, h->mg_d0, h->invd64, h->ndof, true, false));
-  MTO_TRY(apply_fine(h, z, h->mg_q0, done, h->mg_lead & 2));
+  MTO_TRY(smooth(-1, b0, x0, q0, d0, invd0, h->ndof, true, false));
+  MTO_TRY(fine_apply(h, x0, q0, done, lead, false));
   {
     TimedScope ts(h, F_PRECOND);
-    MGLevel& L1 = h->mg[0];
-    mg_restrict0_kernel<<<vec_grid(L1.nv), 256, 0, h->stream>>>(L1.nv, h->mg_rptr, h->mg_rnode, h->mg_rw, r,
-                                                               h->mg_q0, h->invd64, L1.mask, L1.b, done);
+    const LevelV<V> L1 = level_vecs<V>(h->mg[0]);
+    mg_restrict0_kernel<V><<<vec_grid(h->mg[0].nv), 256, 0, h->stream>>>(
+        h->mg[0].nv, h->mg_rptr, h->mg_rnode, h->mg_rw, b0, q0, invd0, L1.mask, L1.b, done);
     MTO_TRY(mto_after_launch(h, "mg_restrict0_kernel"));
   }
   // Q1 levels down
   for (int l = 0; l < nl - 1; ++l) {
-    MGLevel& L = h->mg[l];
-    MGLevel& C = h->mg[l + 1];
-    MTO_TRY(smooth(l, L.b, L.x, L.q, L.d, L.invd, L.n, true, false));
+    const MGLevel& L = h->mg[l];
+    const MGLevel& C = h->mg[l + 1];
+    const LevelV<V> lv = level_vecs<V>(L), cv = level_vecs<V>(C);
+    MTO_TRY(smooth(l, lv.b, lv.x, lv.q, lv.d, lv.invd, L.n, true, false));
     TimedScope ts(h, F_PRECOND);
-    MTO_TRY(mg_apply_level(h, L, L.x, L.q, done));
-    mg_restrict_h_kernel<<<vec_grid(C.nv), 256, 0, h->stream>>>(C.nx, C.ny, L.nx, L.ny, L.b, L.q, L.invd, C.mask,
-                                                                C.b, done);
+    MTO_TRY(mg_level_apply(h, L, lv.x, lv.q, done));
+    mg_restrict_h_kernel<V><<<vec_grid(C.nv), 256, 0, h->stream>>>(C.nx, C.ny, L.nx, L.ny, lv.b, lv.q, lv.invd,
+                                                                   cv.mask, cv.b, done);
     MTO_TRY(mto_after_launch(h, "mg_restrict_h_kernel"));
   }
   {
     TimedScope ts(h, F_PRECOND);
     const MGLevel& C = h->mg.back();
-    mg_coarse_solve_kernel<<<(int)((C.n * 32 + 255) / 256), 256, 0, h->stream>>>((int)C.n, h->mg_Acur, C.b, C.x,
-                                                                                   done);
+    const LevelV<V> cv = level_vecs<V>(C);
+    mg_coarse_solve_kernel<V><<<(int)((C.n * 32 + 255) / 256), 256, 0, h->stream>>>((int)C.n, h->mg_Acur, cv.b,
+                                                                                      cv.x, done);
     MTO_TRY(mto_after_launch(h, "mg_coarse_solve_kernel"));
   }
   // up
   for (int l = nl - 2; l >= 0; --l) {
-    MGLevel& L = h->mg[l];
+    const MGLevel& L = h->mg[l];
     const MGLevel& C = h->mg[l + 1];
+    const LevelV<V> lv = level_vecs<V>(L), cv = level_vecs<V>(C);
     {
       TimedScope ts(h, F_PRECOND);
-      mg_prolong_h_kernel<<<vec_grid(L.nv), 256, 0, h->stream>>>(C.nx, L.nx, L.ny, C.x, L.mask, L.x, L.q, done);
+      mg_prolong_h_kernel<V><<<vec_grid(L.nv), 256, 0, h->stream>>>(C.nx, L.nx, L.ny, cv.x, lv.mask, lv.x, lv.q,
+                                                                     done);
       MTO_TRY(mto_after_launch(h, "mg_prolong_h_kernel"));
     }
-    MTO_TRY(smooth(l, L.b, L.x, L.q, L.d, L.invd, L.n, false, false));
+    MTO_TRY(smooth(l, lv.b, lv.x, lv.q, lv.d, lv.invd, L.n, false, false));
   }
   {
     TimedScope ts(h, F_PRECOND);
-    mg_prolong0_kernel<<<vec_grid(h->n_nodes), 256, 0, h->stream>>>(h->n_nodes, h->mg_pidx, h->mg_pw, h->mg[0].x,
-                                                                    h->invd64, z, h->mg_q0, done);
+    const LevelV<V> L1 = level_vecs<V>(h->mg[0]);
+    mg_prolong0_kernel<V><<<vec_grid(h->n_nodes), 256, 0, h->stream>>>(h->n_nodes, h->mg_pidx, h->mg_pw, L1.x,
+                                                                        invd0, x0, q0, done);
     MTO_TRY(mto_after_launch(h, "mg_prolong0_kernel"));
   }
-  return smooth(-1, r, z, h->mg_q0, h->mg_d0, h->invd64, h->ndof, false, true);
+  return smooth(-1, b0, x0, q0, d0, invd0, h->ndof, false, true);
+}
+
+}  // namespace
+
+// z = M^-1 r: one V-cycle, with r^T z into *dot_res when dot_part is set (block partials in
+// dot_part, counter dot_cnt).  FP64 cycle: level-0 vectors b = r, x = z, q = mg_q0, d = mg_d0,
+// v = mg_v0.  FP32 cycle (the cycle on FP32 copies of a mixed build): r rounded into its own FP32
+// level-0 vectors, z and r^T z written in FP64 by the last smoothing step.
+mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const int* done, double* dot_part,
+                     unsigned* dot_cnt, double* dot_res) {
+  if (mg_fp32_cycle(h)) {
+    const int64_t n = h->ndof;
+    float* F = h->mg_f32;
+    float *b = F, *x = F + n, *q = F + 2 * n, *d = F + 3 * n, *v = F + 4 * n;
+    const float* invd = F + 5 * n;
+    {
+      TimedScope ts(h, F_PRECOND);
+      mg_demote_kernel<<<vec_grid(n), 256, 0, h->stream>>>(n, r, b, done);
+      MTO_TRY(mto_after_launch(h, "mg_demote_kernel"));
+    }
+    return mg_cycle<float>(h, b, x, q, d, v, invd, degree, done, dot_part, dot_cnt, dot_res, z, r);
+  }
+  return mg_cycle<double>(h, r, z, h->mg_q0, h->mg_d0, h->mg_v0, h->invd64, degree, done, dot_part, dot_cnt,
+                          dot_res, nullptr, r);
 }
 
 // y = A x on Q1 level l (y is written, not accumulated): the vertex stencil where it exists (the
-// smoothed levels; rounded to FP32 when the cycle runs on the leading parts of a mixed build), else
-// the element matrices
+// smoothed levels; rounded to FP32 when the cycle runs on FP32 copies), else the element matrices
 mto_status mg_apply_level(mto_handle h, const MGLevel& l, const double* x, double* y, const int* done) {
-  if (!l.S) return apply_q1(h, l, x, y, done);
-  if (h->mg_lead && h->built_precision == MTO_MIXED)
-    mg_stencil_apply_kernel<float><<<vec_grid(l.nv), 256, 0, h->stream>>>(l.nx, l.ny, l.S32, x, y, done);
-  else
-    mg_stencil_apply_kernel<double><<<vec_grid(l.nv), 256, 0, h->stream>>>(l.nx, l.ny, l.S, x, y, done);
-  return mto_after_launch(h, "mg_stencil_apply_kernel");
+  return mg_level_apply(h, l, x, y, done);
 }
 
 }  // namespace mto

@@ -102,6 +102,8 @@ struct MGLevel {
   double* S = nullptr;             // [36][nv] the assembled operator as a vertex stencil: entry
                                    // (o * 4 + 2 c + c') of vertex v couples (v, c) with (v + offset o, c')
   float* S32 = nullptr;            // [36][nv] the same rounded to FP32 (the cycle's copy with mg_operator LEAD)
+  float *invd32 = nullptr, *mask32 = nullptr;   // [n] FP32 copies for the FP32 cycle (which keeps its
+                                                // vectors x, b, q, d in the FP64 buffers)
   double* mask = nullptr;          // [n] 0 on supported DOFs, else 1
   double* invd = nullptr;          // [n] inverse diagonal, 0 on supported DOFs
   double *x = nullptr, *b = nullptr, *q = nullptr, *d = nullptr;   // [n] cycle vectors
@@ -226,8 +228,8 @@ struct mto_handle_s {
   bool solve_log = false;                      // MTO_SOLVE_LOG=1: one stderr line per refinement step
   double mg_ratio = 0.0;                       // MTO_MG_RATIO: Chebyshev interval lmax / ratio .. lmax (0: 100)
   int mg_q1deg = 0;                            // MTO_MG_Q1DEG: smoothing degree on the Q1 levels (0: 4)
-  int mg_lead = 7;   // split-pair applies of the cycle taken on the FP32 leading part (mg_operator):
-                     // bit 0 element blocks, bit 1 pre-smoothing and restriction residual, bit 2 post-smoothing
+  bool mg_lead = true;   // mg_operator: the cycle of a mixed build on FP32 copies with FP32 vectors
+  float* mg_f32 = nullptr;   // [6][ndof] the FP32 cycle's level-0 vectors b, x, q, d, v and invd
   int mg_smoother = 0;                         // fine-level smoothing: MTO_SMOOTH_JACOBI or MTO_SMOOTH_BLOCK
   bool mg_block = false;                       // element-block smoothing in use (set by mg_build)
   std::vector<mto::GraphEntry*> graphs;
@@ -453,6 +455,9 @@ mto_status autotune_operator(mto_handle h, int32_t* choice, double* us);        
 mto_status apply_fine(mto_handle h, const double* x, double* y, const int* done, bool lead = false);
 mto_status mg_select_operator(mto_handle h, int op);   // mg_operator of mto_solve_opts
 mto_status apply_block(mto_handle h, const double* x, double* y, const int* done, bool lead = false);  // element blocks
+// the same on FP32 vectors with the leading part (the FP32 multigrid cycle)
+mto_status apply_fine32(mto_handle h, const float* x, float* y, const int* done);
+mto_status apply_block32(mto_handle h, const float* x, float* y, const int* done);
 mto_status apply_q1(mto_handle h, const MGLevel& l, const double* x, double* y, const int* done);
 mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts* o, int32_t* iters,
                  double* relres);
