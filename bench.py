@@ -250,10 +250,48 @@ def whole_job_rate(world, steps, max_ms):
     return world * steps / (max_ms * 1e-3)
 
 
-# DRAM bytes (read + write) of one launch of ebe_df_tma_kernel<3,double>, from an ncu capture of the
-# 480 x 240 beam's operator (115,200 Q3 elements; profiles/ebe_df_tma_kernel_mbb480x240.md), per
-# element; the kernel has not changed since.  Scaled to a launch by the elements it processes.
-TMA_TRAFFIC_PER_ELEMENT = (542046208 + 15458560) / 115200
+# DRAM bytes (read + write) of one launch of the staged operator kernels, from ncu captures on the
+# 480 x 240 beam (115,200 Q3 elements), per element; scaled to a launch by the elements it
+# processes.  Split pair with FP64 vectors (the
+# outer PCG), and the FP32 leading part with FP32 vectors (the multigrid cycle).
+TMA_TRAFFIC_PER_ELEMENT = {"split": (542053376 + 16044544) / 115200, "lead": (274732032 + 8256256) / 115200}
+
+
+def lead_bytes(pr, ndof):
+    """Algorithmic bytes of one launch of the leading-part operator of the FP32 multigrid cycle: per
+    element the hi row of its matrix ((n_e/2 + 1) n_e entries, 4 bytes) and its node map (4 bytes
+    per node); per DOF one FP32 read of x and one FP32 write of y."""
+    nn = [(int(p) + 1) ** 2 for p in pr.p]
+    return sum(4 * (n + 1) * (2 * n) + 4 * n for n in nn) + 8 * ndof
+
+
+def roofline(families, fam, bytes_per_launch, pr, hbm, lead):
+    """HBM roofline of one operator kernel from the sampled CUDA-event timing of its family (average
+    launch duration; one apply = one launch per order class)."""
+    n, ms = families.get(fam, (0, 0.0))
+    if not n:
+        return None
+    ncls = len(set(int(p) for p in pr.p))
+    avg_ms = ms / n * ncls
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    p0 = int(pr.p[0])
+    row_bytes = len(pr.p) * ((2 * (p0 + 1) ** 2) // 2 + 1) * 2 * (p0 + 1) ** 2 * (4 if lead else 8)
+    big = row_bytes > (64 << 20)
+    if lead:
+        kernel = ("ebe_df_tma_kernel<3,false,float> (FP32 leading part of the split pair, FP32 vectors: the "
+                  "multigrid cycle's operator)" if big else "ebe_df_pipe_kernel<3,false,float> (FP32 leading part)")
+    else:
+        kernel = ("ebe_df_tma_kernel<3,true,double> (split-precision pair, FP64 vectors: the outer PCG's "
+                  "operator)" if big else "ebe_df_pipe_kernel<3,true,double> (split-precision pair)")
+    key = "lead" if lead else "split"
+    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": (achieved / hbm) if hbm else None,
+            "traffic": TMA_TRAFFIC_PER_ELEMENT[key] * len(pr.p) if big else None,
+            "traffic_note": ("stored ncu capture of this kernel on the 480x240 beam (115,200 elements), "
+                             "dram__bytes_read.sum + dram__bytes_write.sum scaled by elements to this launch; "
+                             "not measured in this run" if big else "no stored capture for this kernel here"),
+            "peak_note": "measured HBM copy of MEASURED_PEAKS.json" if hbm else "no measured peak file",
+            "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_ms * 1e3, "sampled_launches": n}
 
 
 def smoother_of(args):
@@ -445,14 +483,12 @@ def run_gpu(args, rank, world, local_rank):
 
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
-    n_apply, apply_ms = mixed["families"]["applydf64"]
-    bytes_per_launch = operator_bytes(pr, run.ndof)
-    ncls = len(set(int(p) for p in pr.p))
-    avg_ms = apply_ms / max(n_apply, 1) * ncls     # one apply = ncls class launches
-    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9 if n_apply else None
-    big = (len(pr.p) * ((2 * (int(pr.p[0]) + 1) ** 2) // 2 + 1) * 2 * (int(pr.p[0]) + 1) ** 2 * 8) > (64 << 20)
-    kernel = ("ebe_df_tma_kernel<3,double> (split-precision element operator, bulk-copy staged rows)" if big else
-              "ebe_df_pipe_kernel<3,double> (split-precision element operator, register-pipelined rows)")
+    rl_split = roofline(mixed["families"], "applydf64", operator_bytes(pr, run.ndof), pr, hbm, lead=False)
+    rl_lead = roofline(mixed["families"], "applylead", lead_bytes(pr, run.ndof), pr, hbm, lead=True)
+    # the dominant kernel: the one with more of the step's time (per-family totals of the bracketed step)
+    t_split = breakdown.get("applydf64", {}).get("ms", 0.0)
+    t_lead = breakdown.get("applylead", {}).get("ms", 0.0)
+    rl_main, rl_other = (rl_lead, rl_split) if (rl_lead and t_lead > t_split) else (rl_split, rl_lead)
     out = {
         "metric": METRIC,
         "value": whole_job_rate(world, steps, mixed_ms_max),
@@ -484,15 +520,9 @@ def run_gpu(args, rank, world, local_rank):
         "sampled_operator_launches": {k: {"launches": v[0], "avg_us": round(1e3 * v[1] / max(v[0], 1), 3)}
                                       for k, v in mixed["families"].items() if v[0]},
         "gpu_launches": mixed["launches"],
-        "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if (achieved and hbm) else None,
-                     "traffic": TMA_TRAFFIC_PER_ELEMENT * len(pr.p) if big else None,
-                     "traffic_note": ("stored ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of "
-                                      "ebe_df_tma_kernel<3,double> on the 480x240 beam, 115,200 elements), scaled "
-                                      "by elements to this launch; not measured in this run"
-                                      if big else "no stored capture for this kernel on this workload"),
-                     "peak_note": "measured HBM copy of MEASURED_PEAKS.json" if hbm else "no measured peak file",
-                     "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_ms * 1e3},
+        "roofline": rl_main,
+        "roofline_other_operator": rl_other,
+        "operator_step_ms": {"applylead": t_lead, "applydf64": t_split},
         "accuracy": checks,
         "step_breakdown_ms": breakdown,
         "clocks": clk.summary(),

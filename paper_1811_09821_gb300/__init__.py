@@ -73,7 +73,7 @@ SYMBOLS = ["mto_create", "mto_destroy", "mto_last_error", "mto_set_stream", "mto
            "mto_filter", "mto_filter_adjoint", "mto_transfer_design", "mto_compliance_energy",
            "mto_autotune", "mto_build_elements_batched", "mto_solve_batched", "mto_sensitivity_batched"]
 TIME_FAMILIES = {"apply32": 0, "apply64": 1, "build": 2, "sens": 3, "indicator": 4, "vector": 5, "applydf64": 6,
-                 "precond": 7, "oc": 8}
+                 "precond": 7, "oc": 8, "applylead": 9}
 
 _lib = None
 

@@ -441,8 +441,8 @@ constexpr unsigned kWaitLimit = 1u << 24;
 // The split-precision operator for n_e <= 32 with the element rows staged by bulk copies: every
 // warp walks its own sequence of element groups (G elements of W lanes, G = 32 / W) and keeps
 // kStages groups' hi/lo rows in flight in its shared-memory ring, so the row stream no longer
-// depends on how many warps the registers allow.  Node maps and x values run one group ahead in
-// registers.  Same arithmetic and reduction as ebe_kernel (kLo = false: the hi rows alone, staged
+// depends on how many warps the registers allow.  x values run two groups ahead in registers and
+// node maps two groups ahead of x.  Same arithmetic and reduction as ebe_kernel (kLo = false: the hi rows alone, staged
 // and summed as in lead_rows).  Every wait is bounded: on expiry the warp records MTO_ETIMEOUT,
 // waits (bounded) for its copies still in flight, and stops.
 template <int PO, bool kLo, typename TX>
@@ -500,18 +500,20 @@ __global__ void __launch_bounds__(kTmaWarps * 32) ebe_df_tma_kernel(const float*
     for (int q = 0; q < c.cnt; ++q) v += c.w[q] * (double)x[2 * (size_t)c.node[q] + (li & 1)];
     return v;
   };
-  int g_cur = load_g(first + gid);
-  double x_cur = load_x(first + gid, g_cur);
-  int g_next = load_g(first + stride + gid);
+  // x runs two groups ahead of the arithmetic and the node maps two groups ahead of x, so every
+  // gather has two groups of arithmetic to arrive in
+  int g0 = load_g(first + gid), g1 = load_g(first + stride + gid);
+  int g2 = load_g(first + 2 * stride + gid), g3 = load_g(first + 3 * stride + gid);
+  double x0 = load_x(first + gid, g0), x1 = load_x(first + stride + gid, g1);
   double dot = 0.0;
   bool ok = true;
   int it = 0;
   for (int base = first; base < n; base += stride, ++it) {
     const int e = base + gid;
     const bool act = e < n && li < NE;
-    // x of the next group and the node map after it, in flight during this group's arithmetic
-    const double x_next = load_x(e + stride, g_next);
-    const int g_next2 = load_g(e + 2 * stride);
+    const double x2 = load_x(e + 2 * stride, g2);
+    const int g4 = load_g(e + 4 * stride);
+    const int g_cur = g0;
     // wait for this group's rows
     const int st = it % kStages;
     const uint32_t parity = (uint32_t)((it / kStages) & 1);
@@ -525,7 +527,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32) ebe_df_tma_kernel(const float*
     if (!__all_sync(0xffffffffu, ok)) break;
     const float* rh = ring + (size_t)st * NM * stage_floats + (size_t)gid * L;
     const float* rl = rh + stage_floats;
-    const double xd = x_cur;
+    const double xd = x0;
     float sh = 0.0f, sl = 0.0f;
     if constexpr (kLo) {
       const float xh = (float)xd;
@@ -571,9 +573,12 @@ __global__ void __launch_bounds__(kTmaWarps * 32) ebe_df_tma_kernel(const float*
       }
       if (red.part) dot += xd * yv;
     }
-    g_cur = g_next;
-    x_cur = x_next;
-    g_next = g_next2;
+    g0 = g1;
+    g1 = g2;
+    g2 = g3;
+    g3 = g4;
+    x0 = x1;
+    x1 = x2;
   }
   if (!__all_sync(0xffffffffu, ok)) {
     // a wait expired: report, then let this warp's outstanding copies land before the block exits
@@ -707,7 +712,9 @@ mto_status apply_all(mto_handle h, int which, const T* x, T* y, int slot, const 
                      int* nres = nullptr, bool lead = false) {
   const bool mixed_build = h->built_precision == MTO_MIXED;
   const bool df = which == 1 ? mixed_build : (sizeof(T) == 4 || (mixed_build && (h->inner_split || lead)));
-  const int fam = (which == 1 || lead) ? F_PRECOND : (df ? (sizeof(T) == 8 ? F_APPLYDF64 : F_APPLY32) : F_APPLY64);
+  const int fam = which == 1 ? F_PRECOND
+                  : lead     ? F_APPLYLEAD
+                             : (df ? (sizeof(T) == 8 ? F_APPLYDF64 : F_APPLY32) : F_APPLY64);
   TimedScope ts(h, fam);
   int ci = 0;
   for (int p = 1; p <= MTO_P_MAX; ++p) {
@@ -1080,7 +1087,12 @@ mto_status cg_iteration(mto_handle h, const CGVecs<T>& v, int pc, int deg, int n
     zero_kernel<T><<<kVecBlocks, 256, 0, h->stream>>>(n, v.q, h->flags);
     MTO_TRY(mto_after_launch(h, "zero_kernel"));
   }
-  if (!jac) MTO_TRY(precond_step<T>(h, v, pc, deg, kGam + nxt, h->flags));
+  if (!jac) {
+    h->timing.sample_lead = local == 0;   // sampled timing: the cycle's leading-part launches too
+    const mto_status sp = precond_step<T>(h, v, pc, deg, kGam + nxt, h->flags);
+    h->timing.sample_lead = false;
+    MTO_TRY(sp);
+  }
   {
     TimedScope ts(h, F_VECTOR);
     ConvTest cv{res_slot(h, nrm == 1 ? kRD + nxt : kRR + nxt), 1, ref, tol2, h->cg_base, local, h->flags, h->flags + 1,

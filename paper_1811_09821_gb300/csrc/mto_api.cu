@@ -54,7 +54,8 @@ cudaEvent_t take_event(mto_handle h) {
 }  // namespace
 
 TimedScope::TimedScope(mto_handle h_, int fam_) : h(h_), fam(fam_), launches0(h_->launches) {
-  if (!h->timing.on || (h->timing.sampled && !h->timing.sample)) return;
+  if (!h->timing.on) return;
+  if (h->timing.sampled && !h->timing.sample && !(fam == F_APPLYLEAD && h->timing.sample_lead)) return;
   if (!h->timing.capture_list && h->timing.pending.size() > 4096) {
     cudaStreamSynchronize(h->stream);
     timing_harvest(h);

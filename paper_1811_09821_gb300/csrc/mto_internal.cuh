@@ -77,12 +77,13 @@ struct QRTab {
 
 // Kernel families timed with CUDA events when timing is enabled (see mto_timing_enable).
 enum Family { F_APPLY32 = 0, F_APPLY64 = 1, F_BUILD = 2, F_SENS = 3, F_INDICATOR = 4, F_VECTOR = 5,
-              F_APPLYDF64 = 6, F_PRECOND = 7, F_OC = 8, F_COUNT = 9 };
+              F_APPLYDF64 = 6, F_PRECOND = 7, F_OC = 8, F_APPLYLEAD = 9, F_COUNT = 10 };
 
 struct Timing {
   bool on = false;
   bool sampled = false;   // record only the operator launches marked by `sample` (low overhead)
   bool sample = false;
+  bool sample_lead = false;   // also the leading-part operator launches (F_APPLYLEAD) while set
   struct Pending { int fam; int launches; cudaEvent_t a, b; };
   std::vector<cudaEvent_t> pool;
   std::vector<Pending> pending;
