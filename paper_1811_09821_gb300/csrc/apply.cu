@@ -11,6 +11,7 @@
 #include <map>
 #include <mutex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "mto_internal.cuh"
@@ -434,18 +435,19 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-constexpr int kStages = 3;        // element groups in flight per warp
+// element groups in flight per warp (ring stages): chosen per variant in launch_ebe
 constexpr int kTmaWarps = 8;      // warps per block
 constexpr unsigned kWaitLimit = 1u << 24;
 
 // The split-precision operator for n_e <= 32 with the element rows staged by bulk copies: every
 // warp walks its own sequence of element groups (G elements of W lanes, G = 32 / W) and keeps
-// kStages groups' hi/lo rows in flight in its shared-memory ring, so the row stream no longer
+// kStages groups' hi/lo rows in its shared-memory ring (a group is refilled as soon as its
+// arithmetic is done), so the row stream no longer
 // depends on how many warps the registers allow.  x values run two groups ahead in registers and
 // node maps two groups ahead of x.  Same arithmetic and reduction as ebe_kernel (kLo = false: the hi rows alone, staged
 // and summed as in lead_rows).  Every wait is bounded: on expiry the warp records MTO_ETIMEOUT,
 // waits (bounded) for its copies still in flight, and stops.
-template <int PO, bool kLo, typename TX>
+template <int PO, bool kLo, typename TX, int kStages>
 __global__ void __launch_bounds__(kTmaWarps * 32) ebe_df_tma_kernel(const float* __restrict__ Kh,
                                                                     const float* __restrict__ Kl, int L, int n,
                                                                     const int* __restrict__ gmap,
@@ -597,8 +599,8 @@ __global__ void __launch_bounds__(kTmaWarps * 32) ebe_df_tma_kernel(const float*
   if (red.part) reduce_out(dot, red);
 }
 
-size_t tma_smem_bytes(int L, int G, int nm) {
-  return (size_t)kTmaWarps * kStages * nm * G * L * sizeof(float) + (size_t)kTmaWarps * kStages * sizeof(uint64_t);
+size_t tma_smem_bytes(int L, int G, int nm, int stages) {
+  return (size_t)kTmaWarps * stages * nm * G * L * sizeof(float) + (size_t)kTmaWarps * stages * sizeof(uint64_t);
 }
 
 }  // namespace
@@ -625,6 +627,55 @@ int ebe_blocks(int p, int n) {
 
 namespace {
 
+// Ring stages of the staged operator: the split pair and the leading part (MTO_TMA_STAGES="s,l"
+// overrides, each of 2, 3, 4, 6; read once per process).  Two stages, measured on the 1024 x 512
+// beam: the split pair 438 us per launch against 509 us with three stages, 752 with four and 792
+// with six; the leading part 247 us against 263, 316 and 411 us.  The smaller ring leaves room for
+// more blocks per SM, and both kernels need those warps more than a deeper ring.
+int tma_stages(bool split) {
+  static int st[2] = {0, 0};
+  if (!st[0]) {
+    st[0] = 2;   // split pair
+    st[1] = 2;   // leading part
+    if (const char* e = std::getenv("MTO_TMA_STAGES")) {
+      int a = 0, b = 0;
+      if (std::sscanf(e, "%d,%d", &a, &b) == 2) {
+        st[0] = a;
+        st[1] = b;
+      }
+    }
+  }
+  return st[split ? 0 : 1];
+}
+
+// The staged operator, persistent: as many 8-warp blocks per SM as shared memory and registers allow
+// (the occupancy calculator, once per kernel instance; the shared-memory attribute set with it).
+template <int PO, bool kLo, typename TX, int NS>
+void launch_tma(mto_handle h, const PClass& c, const float* Mh, const float* Ml, const TX* x, TX* y, Red red,
+                const int* done) {
+  constexpr int NE = 2 * (PO + 1) * (PO + 1);
+  const int warps = (c.n + WarpShape<NE>::G - 1) / WarpShape<NE>::G;
+  const size_t smem = tma_smem_bytes(c.L, WarpShape<NE>::G, kLo ? 2 : 1, NS);
+  static int per_sm = 0;
+  if (!per_sm) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(ebe_df_tma_kernel<PO, kLo, TX, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ebe_df_tma_kernel<PO, kLo, TX, NS>, kTmaWarps * 32, smem) !=
+            cudaSuccess ||
+        nb < 1) {
+      cudaGetLastError();
+      nb = 1;
+    }
+    per_sm = nb;
+  }
+  int blocks = (warps + kTmaWarps - 1) / kTmaWarps;
+  if (blocks > 152 * per_sm) blocks = 152 * per_sm;
+  ebe_df_tma_kernel<PO, kLo, TX, NS><<<blocks, kTmaWarps * 32, smem, h->stream>>>(Mh, Ml, c.L, c.n, c.gmap,
+                                                                                   h->cons_d, x, y, red, done,
+                                                                                   h->flags + 1);
+}
+
 template <int PO, bool kDF, typename TX>
 void launch_ebe(mto_handle h, const PClass& c, const double* M64, const float* Mh, const float* Ml, const TX* x,
                 TX* y, Red red, const int* done, const ConvTest& cv) {
@@ -639,27 +690,22 @@ void launch_ebe(mto_handle h, const PClass& c, const double* M64, const float* M
       const bool lo = Ml != nullptr;   // null: the hi rows alone (a preconditioner's copy)
       const bool big = (size_t)c.n * c.L * (lo ? 2 : 1) * sizeof(float) > ((size_t)64 << 20);
       if (opk == 1 || (opk < 0 && big)) {
-        // bulk-copy staging: persistent, as many 8-warp blocks per SM as the shared memory holds
-        const size_t smem = tma_smem_bytes(c.L, WarpShape<NE>::G, lo ? 2 : 1);
-        const int per_sm = smem > 0 ? (int)((227u * 1024u) / smem) : 1;
-        int blocks = (warps + kTmaWarps - 1) / kTmaWarps;
-        const int cap = 152 * (per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm));
-        if (blocks > cap) blocks = cap;
-        static bool attr_set = false;   // once per process (both variants), before any stream capture
-        if (!attr_set) {
-          const int s2 = (int)tma_smem_bytes(c.L, WarpShape<NE>::G, 2), s1 = (int)tma_smem_bytes(c.L, WarpShape<NE>::G, 1);
-          if (s2 > 48 * 1024)
-            cudaFuncSetAttribute(ebe_df_tma_kernel<PO, true, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
-          if (s1 > 48 * 1024)
-            cudaFuncSetAttribute(ebe_df_tma_kernel<PO, false, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
-          attr_set = true;
+        const int ns = tma_stages(lo);
+        if (lo) {
+          switch (ns) {
+            case 2: launch_tma<PO, true, TX, 2>(h, c, Mh, Ml, x, y, red, done); break;
+            case 4: launch_tma<PO, true, TX, 4>(h, c, Mh, Ml, x, y, red, done); break;
+            case 6: launch_tma<PO, true, TX, 6>(h, c, Mh, Ml, x, y, red, done); break;
+            default: launch_tma<PO, true, TX, 3>(h, c, Mh, Ml, x, y, red, done); break;
+          }
+        } else {
+          switch (ns) {
+            case 2: launch_tma<PO, false, TX, 2>(h, c, Mh, Ml, x, y, red, done); break;
+            case 4: launch_tma<PO, false, TX, 4>(h, c, Mh, Ml, x, y, red, done); break;
+            case 6: launch_tma<PO, false, TX, 6>(h, c, Mh, Ml, x, y, red, done); break;
+            default: launch_tma<PO, false, TX, 3>(h, c, Mh, Ml, x, y, red, done); break;
+          }
         }
-        if (lo)
-          ebe_df_tma_kernel<PO, true, TX><<<blocks, kTmaWarps * 32, smem, h->stream>>>(
-              Mh, Ml, c.L, c.n, c.gmap, h->cons_d, x, y, red, done, h->flags + 1);
-        else
-          ebe_df_tma_kernel<PO, false, TX><<<blocks, kTmaWarps * 32, smem, h->stream>>>(
-              Mh, Ml, c.L, c.n, c.gmap, h->cons_d, x, y, red, done, h->flags + 1);
         return;
       }
       // persistent: two blocks of 8 warps per SM (the register budget of the pipelined rows)
