@@ -265,6 +265,18 @@ def lead_bytes(pr, ndof):
     return sum(4 * (n + 1) * (2 * n) + 4 * n for n in nn) + 8 * ndof
 
 
+def iteration_share(breakdown, iters):
+    """Per PCG iteration of the bracketed step: the element-operator kernels' time (the outer PCG's
+    split pair, the cycle's leading parts of the operator and of the element blocks) against the
+    time of the solve's families (operators, the rest of the cycle and its per-step set-up,
+    vectors)."""
+    ms = lambda k: breakdown.get(k, {}).get("ms", 0.0)
+    op = ms("applydf64") + ms("applylead")
+    it = op + ms("precond") + ms("vector")
+    return {"operator_ms_per_iter": op / max(iters, 1), "solve_ms_per_iter": it / max(iters, 1),
+            "ratio": it / op if op else None}
+
+
 def roofline(families, fam, bytes_per_launch, pr, hbm, lead):
     """HBM roofline of one operator kernel from the sampled CUDA-event timing of its family (average
     launch duration; one apply = one launch per order class)."""
@@ -520,6 +532,9 @@ def run_gpu(args, rank, world, local_rank):
         "sampled_operator_launches": {k: {"launches": v[0], "avg_us": round(1e3 * v[1] / max(v[0], 1), 3)}
                                       for k, v in mixed["families"].items() if v[0]},
         "gpu_launches": mixed["launches"],
+        "launches_per_step": mixed["launches"] / steps,
+        "launches_per_pcg_iter": mixed["launches"] / max(mixed["iters"], 1),   # includes the per-step kernels
+        "operator_share_of_iteration": iteration_share(breakdown, mixed["iters"] / steps),
         "roofline": rl_main,
         "roofline_other_operator": rl_other,
         "operator_step_ms": {"applylead": t_lead, "applydf64": t_split},

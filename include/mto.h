@@ -453,9 +453,9 @@ mto_status mto_oc_update(mto_handle h, const double* rho, const double* dc, doub
 #define MTO_TIME_APPLYDF64 6 /* split-precision operator on FP64 vectors (refinement residuals) */
 #define MTO_TIME_PRECOND 7   /* preconditioner: multigrid cycle, element blocks, their set-up */
 #define MTO_TIME_OC 8        /* optimality-criteria update */
-#define MTO_TIME_APPLYLEAD 9 /* the FP32 leading part of the split operator inside the multigrid cycle
-                                (level 0: smoothing, restriction residual, power iteration; not
-                                the element blocks, which stay in MTO_TIME_PRECOND) */
+#define MTO_TIME_APPLYLEAD 9 /* the FP32 leading parts inside the multigrid cycle: level 0's operator
+                                (smoothing, restriction residual, power iteration) and its element
+                                blocks */
 mto_status mto_timing_enable(mto_handle h, int32_t enable);
 mto_status mto_timing_read(mto_handle h, int32_t family, int64_t* launches, double* total_ms);
 

@@ -758,9 +758,9 @@ mto_status apply_all(mto_handle h, int which, const T* x, T* y, int slot, const 
                      int* nres = nullptr, bool lead = false) {
   const bool mixed_build = h->built_precision == MTO_MIXED;
   const bool df = which == 1 ? mixed_build : (sizeof(T) == 4 || (mixed_build && (h->inner_split || lead)));
-  const int fam = which == 1 ? F_PRECOND
-                  : lead     ? F_APPLYLEAD
-                             : (df ? (sizeof(T) == 8 ? F_APPLYDF64 : F_APPLY32) : F_APPLY64);
+  const int fam = lead       ? F_APPLYLEAD
+                  : which == 1 ? F_PRECOND
+                               : (df ? (sizeof(T) == 8 ? F_APPLYDF64 : F_APPLY32) : F_APPLY64);
   TimedScope ts(h, fam);
   int ci = 0;
   for (int p = 1; p <= MTO_P_MAX; ++p) {

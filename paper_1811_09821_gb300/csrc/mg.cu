@@ -269,6 +269,60 @@ __global__ void __launch_bounds__(256) mg_stencil_apply_kernel(int nx, int ny, c
   }
 }
 
+// One Chebyshev step on a Q1 level with q = A x formed in place by the vertex stencil (the apply and
+// the update of mg_cheb_kernel in one pass): reads x from xin, writes the updated x to xout (the
+// level's two x buffers alternate, so no vertex reads a neighbour's new value), d in place.
+// xzero: x = 0 before the step (A x = 0, xin not read).  Stencil and arithmetic as in
+// mg_stencil_apply_kernel.
+template <typename TS, typename V>
+__global__ void __launch_bounds__(256) mg_stencil_cheb_kernel(int nx, int ny, const TS* __restrict__ S,
+                                                              const V* __restrict__ xin, V* __restrict__ xout,
+                                                              const V* __restrict__ b, const V* __restrict__ invd,
+                                                              V* __restrict__ d, const double2* __restrict__ coef,
+                                                              int step, int xzero, const int* __restrict__ done) {
+  if (done && *done) return;
+  const double2 cc = coef[step];
+  const V c1 = (V)cc.x, c2 = (V)cc.y;
+  const int64_t nv = (int64_t)(nx + 1) * (ny + 1);
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(v % (nx + 1)), j = (int)(v / (nx + 1));
+    TS y0 = 0, y1 = 0;
+    if (!xzero) {
+#pragma unroll
+      for (int dj = -1; dj <= 1; ++dj) {
+#pragma unroll
+        for (int di = -1; di <= 1; ++di) {
+          const int ii = i + di, jj = j + dj;
+          if (ii < 0 || ii > nx || jj < 0 || jj > ny) continue;
+          const int o = 3 * (dj + 1) + di + 1;
+          const size_t w = 2 * ((size_t)jj * (nx + 1) + ii);
+          const TS x0 = (TS)xin[w], x1 = (TS)xin[w + 1];
+          y0 = fma(S[(size_t)(o * 4 + 0) * nv + v], x0, y0);
+          y0 = fma(S[(size_t)(o * 4 + 1) * nv + v], x1, y0);
+          y1 = fma(S[(size_t)(o * 4 + 2) * nv + v], x0, y1);
+          y1 = fma(S[(size_t)(o * 4 + 3) * nv + v], x1, y1);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const size_t k = 2 * (size_t)v + c;
+      const V r = invd[k] * (b[k] - (V)(c ? y1 : y0));
+      const V dn = step > 0 ? fma(c1, d[k], c2 * r) : c2 * r;
+      d[k] = dn;
+      xout[k] = (xzero ? V(0) : xin[k]) + dn;
+    }
+  }
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256) mg_copy_kernel(int64_t n, const V* __restrict__ a, V* __restrict__ b,
+                                                      const int* __restrict__ done) {
+  if (done && *done) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+
 // assembled diagonal of a Q1 level (atomics), then the masked inverse
 __global__ void mg_diag_kernel(int nel, const int* __restrict__ gmap, const double* __restrict__ K,
                                double* __restrict__ diag) {
@@ -620,7 +674,8 @@ int vec_grid(int64_t n) { return grid_for(n, 256, kMGBlocks); }
 // ---------------------------------------------------------------- host side
 void mg_release(mto_handle h) {
   for (auto& l : h->mg)
-    for (void* p : {(void*)l.gmap, (void*)l.K, (void*)l.S, (void*)l.S32, (void*)l.invd32, (void*)l.mask32, (void*)l.mask, (void*)l.invd, (void*)l.x, (void*)l.b,
+    for (void* p : {(void*)l.gmap, (void*)l.K, (void*)l.S, (void*)l.S32, (void*)l.invd32, (void*)l.mask32, (void*)l.xa,
+                    (void*)l.mask, (void*)l.invd, (void*)l.x, (void*)l.b,
                     (void*)l.q, (void*)l.d})
       cudaFree(p);
   h->mg.clear();
@@ -681,7 +736,7 @@ mto_status mg_setup(mto_handle h) {
       MTO_TRY(mto_alloc(h, &L.S, (size_t)36 * L.nv));
       MTO_TRY(mto_alloc(h, &L.S32, (size_t)36 * L.nv));
     }
-    for (double** v : {&L.mask, &L.invd, &L.x, &L.b, &L.q, &L.d}) MTO_TRY(mto_alloc(h, v, L.n));
+    for (double** v : {&L.mask, &L.invd, &L.x, &L.xa, &L.b, &L.q, &L.d}) MTO_TRY(mto_alloc(h, v, L.n));
     for (float** v : {&L.invd32, &L.mask32}) MTO_TRY(mto_alloc(h, v, L.n));
     MTO_TRY(mto_cuda_check(h, cudaMemsetAsync(L.q, 0, L.n * sizeof(double), h->stream), "memset"));
   }
@@ -819,6 +874,20 @@ mto_status mg_level_apply(mto_handle h, const MGLevel& l, const float* x, float*
   if (!l.S32) return mto_fail(h, MTO_EINVAL, "mg: no stencil on this level");
   mg_stencil_apply_kernel<float, float><<<vec_grid(l.nv), 256, 0, h->stream>>>(l.nx, l.ny, l.S32, x, y, done);
   return mto_after_launch(h, "mg_stencil_apply_kernel");
+}
+
+// one fused Chebyshev step on a smoothed Q1 level (FP64 stencil in the FP64 cycle, FP32 in the FP32 one)
+mto_status mg_level_cheb(mto_handle h, const MGLevel& l, const double* xin, double* xout, const double* b,
+                         const double* invd, double* d, const double2* cf, int step, bool xzero, const int* done) {
+  mg_stencil_cheb_kernel<double, double><<<vec_grid(l.nv), 256, 0, h->stream>>>(l.nx, l.ny, l.S, xin, xout, b, invd,
+                                                                                d, cf, step, xzero, done);
+  return mto_after_launch(h, "mg_stencil_cheb_kernel");
+}
+mto_status mg_level_cheb(mto_handle h, const MGLevel& l, const float* xin, float* xout, const float* b,
+                         const float* invd, float* d, const double2* cf, int step, bool xzero, const int* done) {
+  mg_stencil_cheb_kernel<float, float><<<vec_grid(l.nv), 256, 0, h->stream>>>(l.nx, l.ny, l.S32, xin, xout, b, invd,
+                                                                              d, cf, step, xzero, done);
+  return mto_after_launch(h, "mg_stencil_cheb_kernel");
 }
 
 // lmax of D^-1 A on one level by power iteration (level < 0: the fine operator)
@@ -982,19 +1051,19 @@ namespace {
 // the level vectors in the cycle's type (the FP32 cycle keeps its FP32 vectors in the FP64 buffers)
 template <typename V>
 struct LevelV {
-  V *x, *b, *q, *d;
+  V *x, *b, *q, *d, *xa;
   const V *invd, *mask;
 };
 template <typename V>
 LevelV<V> level_vecs(const MGLevel& L);
 template <>
 LevelV<double> level_vecs<double>(const MGLevel& L) {
-  return {L.x, L.b, L.q, L.d, L.invd, L.mask};
+  return {L.x, L.b, L.q, L.d, L.xa, L.invd, L.mask};
 }
 template <>
 LevelV<float> level_vecs<float>(const MGLevel& L) {
   return {reinterpret_cast<float*>(L.x), reinterpret_cast<float*>(L.b), reinterpret_cast<float*>(L.q),
-          reinterpret_cast<float*>(L.d), L.invd32, L.mask32};
+          reinterpret_cast<float*>(L.d), reinterpret_cast<float*>(L.xa), L.invd32, L.mask32};
 }
 
 // y += A x (block: the element blocks) on level 0 in the cycle's vector type
@@ -1020,16 +1089,25 @@ mto_status mg_cycle(mto_handle h, const V* b0, V* x0, V* q0, V* d0, V* v0, const
     const int k = lev < 0 ? degree : (h->mg_q1deg > 0 ? h->mg_q1deg : kCoarseDegree);
     const double2* cf = h->mg_coef + (size_t)(lev + 1) * kMaxDegree;
     const int grd = vec_grid(n);
-    const bool block = lev < 0 && h->mg_block;   // element-block (additive Schwarz) smoothing
+    if (lev >= 0) {   // Q1 level: one fused stencil + Chebyshev launch per step, x ping-ponged
+      const MGLevel& L = h->mg[lev];
+      V* cur = x;
+      V* nxt = level_vecs<V>(L).xa;
+      TimedScope ts(h, F_PRECOND);
+      for (int s = 0; s < k; ++s) {
+        MTO_TRY(mg_level_cheb(h, L, cur, nxt, b, invd, d, cf, s, pre && s == 0, done));
+        std::swap(cur, nxt);
+      }
+      if (cur != x) {   // odd degree: the result is in the other buffer
+        mg_copy_kernel<V><<<grd, 256, 0, h->stream>>>(n, cur, x, done);
+        MTO_TRY(mto_after_launch(h, "mg_copy_kernel"));
+      }
+      return MTO_OK;
+    }
+    const bool block = h->mg_block;   // element-block (additive Schwarz) smoothing of level 0
     for (int s = 0; s < k; ++s) {
       const bool skip_apply = pre && s == 0;   // x = 0: A x = 0
-      if (!skip_apply) {
-        if (lev < 0) MTO_TRY(fine_apply(h, x, q, done, lead, false));
-        else {
-          TimedScope ts(h, F_PRECOND);
-          MTO_TRY(mg_level_apply(h, h->mg[lev], x, q, done));
-        }
-      }
+      if (!skip_apply) MTO_TRY(fine_apply(h, x, q, done, lead, false));
       if (block) {   // q <- M^-1 (b - A x)
         {
           TimedScope ts(h, F_PRECOND);

@@ -108,6 +108,7 @@ struct MGLevel {
   double* mask = nullptr;          // [n] 0 on supported DOFs, else 1
   double* invd = nullptr;          // [n] inverse diagonal, 0 on supported DOFs
   double *x = nullptr, *b = nullptr, *q = nullptr, *d = nullptr;   // [n] cycle vectors
+  double* xa = nullptr;            // [n] the other x of the fused smoothing steps (ping-pong)
 };
 
 // A captured chunk of CG iterations, replayed until convergence.
