@@ -254,7 +254,7 @@ def whole_job_rate(world, steps, max_ms):
 # 480 x 240 beam (115,200 Q3 elements), per element; scaled to a launch by the elements it
 # processes.  Split pair with FP64 vectors (the
 # outer PCG), and the FP32 leading part with FP32 vectors (the multigrid cycle).
-TMA_TRAFFIC_PER_ELEMENT = {"split": (542053376 + 16044544) / 115200, "lead": (274732032 + 8256256) / 115200}
+TMA_TRAFFIC_PER_ELEMENT = {"split": (542182400 + 15464704) / 115200, "lead": (274720256 + 7731968) / 115200}
 
 
 def lead_bytes(pr, ndof):
