@@ -59,9 +59,11 @@ def parse(argv=None):
     ap.add_argument("--mg-degree", type=int, default=2, help="Chebyshev degree of the fine-level smoothing")
     ap.add_argument("--smoother", default="block", choices=["block", "jacobi"],
                     help="fine-level smoothing: element blocks (default) or point Jacobi")
-    ap.add_argument("--mg-operator", default="lead", choices=["lead", "split"],
-                    help="element matrices inside the multigrid cycle of the mixed path: the FP32 leading part "
-                         "of the split pair (default) or the pair itself")
+    ap.add_argument("--mg-operator", default=None, choices=["lead", "split", "auto"],
+                    help="the multigrid cycle of the mixed path: in FP32 on the leading part of the split pair "
+                         "(default for the single-instance workloads), on the split pair, or the library's "
+                         "choice (default for batched_64, whose binary instances the FP32-rounded element "
+                         "blocks do not always keep definite)")
     ap.add_argument("--build", default="tensor", choices=["tensor", "simt"],
                     help="element build: tcgen05 sliced GEMM (default) or FP64 CUDA cores")
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 leg")
@@ -311,9 +313,10 @@ def smoother_of(args):
     return mto.SMOOTH_BLOCK if args.smoother == "block" else mto.SMOOTH_JACOBI
 
 
-def mg_operator_of(args):
+def mg_operator_of(args, batched=False):
     import paper_1811_09821_gb300 as mto
-    return mto.MG_OP_LEAD if args.mg_operator == "lead" else mto.MG_OP_SPLIT
+    choice = args.mg_operator or ("auto" if batched else "lead")
+    return {"lead": mto.MG_OP_LEAD, "split": mto.MG_OP_SPLIT, "auto": mto.MG_OP_AUTO}[choice]
 
 
 def operator_bytes(pr, ndof):
@@ -522,8 +525,8 @@ def run_gpu(args, rank, world, local_rank):
                                                "one pass over the fixed design from a zero start"),
                    "solve_accuracy": f"relative compliance error {args.rtol:g} (energy test)",
                    "precond": (f"multigrid, {args.smoother} smoothing of degree {args.mg_degree} on the fine level; "
-                               + ("cycle on the FP32 leading part of the split matrices" if args.mg_operator == "lead"
-                                  else "cycle on the split pair")),
+                               + ("cycle on the FP32 leading part of the split matrices"
+                                  if mg_operator_of(args) == mto.MG_OP_LEAD else "cycle on the split pair")),
                    "element_build": "tcgen05 sliced GEMM" if args.build == "tensor" else "FP64 CUDA cores",
                    "l2_flush": "512 MB write before each timed step",
                    "parallelism": f"replicas x{world}"},
@@ -596,7 +599,7 @@ def run_batched(args, rank, world, local_rank):
         mto.build_elements_batched(hs, rhos, mat, prec)
         its, _, _ = mto.solve_batched(hs, fs, us, precision=prec, rtol=args.rtol, norm=mto.NORM_ENERGY,
                                       mg_degree=args.mg_degree, mg_smoother=smoother_of(args),
-                                      mg_operator=mg_operator_of(args))
+                                      mg_operator=mg_operator_of(args, batched=True))
         mto.sensitivity_batched(hs, us, fs, rhos, mat, dcs, want_C=False)
         torch.cuda.synchronize(dev)
         return int(its.sum())

@@ -102,7 +102,9 @@ typedef struct {
  *              error (not squared); *relres still reports the l2 residual.
  *              Needs FP64 vectors (MTO_FP64 or MTO_MIXED).  At 10^7 DOFs and stiffness contrasts
  *              of 1e9 the l2 residual of an FP64 evaluation floors near 1e-7, so l2 tolerances
- *              below that cannot be met there, while compliance accuracy can.
+ *              below that cannot be met there, while compliance accuracy can.  A correction solve
+ *              that does not meet the energy test within its iterations is followed by another one;
+ *              at max_iter the solve returns MTO_ENOCONV.
  *  precond     MTO_PREC_JACOBI (point Jacobi), MTO_PREC_SCHWARZ (element-block additive Schwarz:
  *              per element the inverse of K_e plus the neighbours' share of the assembled diagonal,
  *              which captures the near-null modes of solid/void elements) or MTO_PREC_MG (one
@@ -123,10 +125,14 @@ typedef struct {
  *  mg_operator MTO_PREC_MG with the MTO_MIXED build only: the copy of the matrices the cycle applies
  *              (fine level: its smoothing steps, the restriction residual, the element blocks and the
  *              power iteration of the Chebyshev bounds; Q1 levels: their vertex stencils).
- *              MTO_MG_OP_AUTO (default) = MTO_MG_OP_LEAD: the FP32 leading part of the split pair and
- *              the stencils rounded to FP32 (half the bytes; a preconditioner needs a fixed
- *              operator, not the operator's accuracy: the outer PCG keeps the split pair and the
- *              FP64 refinement).  MTO_MG_OP_SPLIT: the split pair and FP64 stencils.
+ *              MTO_MG_OP_LEAD: the cycle in FP32, i.e. the FP32 leading part of the split pair, the
+ *              stencils rounded to FP32, FP32 vectors (half the bytes; a preconditioner needs a
+ *              fixed operator, not the operator's accuracy: the outer PCG keeps the split pair and
+ *              the FP64 refinement).  MTO_MG_OP_SPLIT: the split pair, FP64 stencils and vectors.
+ *              MTO_MG_OP_AUTO (default): LEAD with MTO_SMOOTH_JACOBI, SPLIT with MTO_SMOOTH_BLOCK
+ *              (the FP32-rounded inverses of the element blocks can lose definiteness on binary
+ *              designs of extreme stiffness contrast; LEAD with block smoothing is then the
+ *              caller's choice, as on the graded designs of the bench).
  * CG iterations run in chunks of check_every (rounded up to a multiple of 4), each a CUDA graph;
  * the reported count stops at convergence, but a chunk already launched completes (cheaply). */
 typedef struct {

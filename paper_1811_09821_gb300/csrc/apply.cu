@@ -1506,6 +1506,7 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
   // 10x shows that the split pair's ~48-bit matrices limit it (condition number near 2^48); the
   // remaining steps then apply the FP64 matrices in the inner PCG too
   bool split = true;
+  bool step_converged = false;   // the last correction solve met its test (energy mode stops on it)
   double rr_prev = -1.0, asked = 0.0;
   mto_status st = MTO_ENOCONV;
   const auto t_start = std::chrono::steady_clock::now();
@@ -1524,9 +1525,11 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
       st = mto_fail(h, MTO_ENAN, "mto_solve: non-finite residual");
       break;
     }
-    if (ff == 0.0 || (!energy && rr <= o->rtol * o->rtol * ff) || (energy && outer > 0)) {
-      // the compliance-accuracy mode takes one correction solve: its energy test bounds the
-      // compliance error of u itself (the FP64 residual above is only reported)
+    if (ff == 0.0 || (!energy && rr <= o->rtol * o->rtol * ff) || (energy && outer > 0 && step_converged)) {
+      // the compliance-accuracy mode stops after a correction solve whose energy test was met:
+      // that test bounds the compliance error of u itself (the FP64 residual above is only
+      // reported); a correction solve that ran out of iterations is followed by another one
+      // while the budget lasts
       st = MTO_OK;
       break;
     }
@@ -1563,6 +1566,7 @@ mto_status solve(mto_handle h, const double* f, double* u, const mto_solve_opts*
                                    : run_cg<double>(h, h->s64, h->r64, pc, deg, nrm, h->red + 6, 1.0, budget, chunk, &it);
       h->inner_split = false;
       MTO_TRY(si);
+      step_converged = h->host_flags[0] != 0;
       TimedScope ts(h, F_VECTOR);
       axpy_kernel<<<grd, 256, 0, h->stream>>>(n, h->s64, u);
       MTO_TRY(mto_after_launch(h, "axpy_kernel"));
@@ -1614,6 +1618,7 @@ struct BatchJob {
   int outer = 0, total = 0, budget = 0;
   double rr = 0.0, ff = 0.0, rr_prev = -1.0, asked = 0.0;
   bool split = true;
+  bool converged = false;   // the last correction solve met its test
   CGRun<double> run;
   mto_status st = MTO_ENOCONV;
 };
@@ -1635,7 +1640,7 @@ mto_status job_on_residual(BatchJob& j) {
     job_finish(j, mto_fail(h, MTO_ENAN, "mto_solve_batched: non-finite residual"));
     return MTO_OK;
   }
-  if (j.ff == 0.0 || (!j.energy && j.rr <= o->rtol * o->rtol * j.ff) || (j.energy && j.outer > 0)) {
+  if (j.ff == 0.0 || (!j.energy && j.rr <= o->rtol * o->rtol * j.ff) || (j.energy && j.outer > 0 && j.converged)) {
     job_finish(j, MTO_OK);
     return MTO_OK;
   }
@@ -1678,6 +1683,7 @@ mto_status job_on_chunk(BatchJob& j) {
   int it = 0;
   const mto_status si = cg_result<double>(h, j.run, &it);
   h->inner_split = false;
+  j.converged = h->host_flags[0] != 0;
   j.total += it;
   if (si != MTO_OK) {
     job_finish(j, si);

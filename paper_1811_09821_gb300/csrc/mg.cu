@@ -940,11 +940,15 @@ mto_status mg_select_smoother(mto_handle h, int smoother) {
 
 // The copy of the matrices the cycle applies with the MTO_MIXED build (FP32 copies and FP32
 // vectors, or the split pair and FP64 stencils with FP64 vectors); a change rebuilds the bounds and
-// drops the graphs.
+// drops the graphs.  AUTO takes the FP32 cycle with point-Jacobi smoothing only: the FP32
+// rounding of the element blocks' inverses (K_e + Delta_e)^-1 can make them indefinite on binary
+// designs (measured: corrections that did not converge on 6 of 64 binary instances, which the split
+// pair and the Jacobi-smoothed FP32 cycle solved), so the element-block smoother keeps the split
+// pair unless LEAD is asked for.  The smoother is selected first.
 mto_status mg_select_operator(mto_handle h, int op) {
   if (op != MTO_MG_OP_AUTO && op != MTO_MG_OP_SPLIT && op != MTO_MG_OP_LEAD)
     return mto_fail(h, MTO_EINVAL, "mto_solve: bad mg_operator");
-  const bool lead = op != MTO_MG_OP_SPLIT;
+  const bool lead = op == MTO_MG_OP_LEAD || (op == MTO_MG_OP_AUTO && h->mg_smoother == MTO_SMOOTH_JACOBI);
   if (lead == h->mg_lead) return MTO_OK;
   MTO_TRY(mto_cuda_check(h, cudaStreamSynchronize(h->stream), "mto_solve"));
   h->mg_lead = lead;

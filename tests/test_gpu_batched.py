@@ -101,3 +101,36 @@ def test_autotune_choice_keeps_parity(mto):
     assert h2.autotune() == res
     h.close()
     h2.close()
+
+
+def test_binary_instance_cycle_choice_and_noconv_report(mto):
+    """A binary instance of the batched recipe (40 x 20, Q2, 2 x 2 density cells, MBB load) on
+    which the FP32 cycle with element-block smoothing does not converge (its FP32-rounded block
+    inverses lose definiteness at a stiffness contrast of 1e9): asked for explicitly with an
+    iteration cap, the compliance-accuracy solve reports MTO_ENOCONV instead of returning the
+    unconverged u; with the default choice (the split-pair cycle for block smoothing) it reaches
+    the oracle's exact compliance within 1e-8."""
+    pr = W.batched()[19]
+    assert (pr.nelx, pr.nely, int(pr.p[0]), int(pr.d[0]), pr.load) == (40, 20, 2, 2, W.MBB)
+    mat = mto.material()
+    h = mto.Handle(0)
+    h.setup(pr.nelx, pr.nely, pr.p, pr.d)
+    fixed, f = mto.load_case(h, pr.load)
+    h.set_supports(fixed)
+    h.build_elements(torch.tensor(pr.rho, device="cuda"), mat, mto.MTO_MIXED)
+    u = torch.zeros(h.ndof, dtype=torch.float64, device="cuda")
+    with pytest.raises(mto.MTOError) as ei:
+        h.solve(f, u, precision=mto.MTO_MIXED, rtol=1e-8, norm=mto.NORM_ENERGY, max_iter=3000, precond=mto.PREC_MG,
+                mg_degree=2, mg_smoother=mto.SMOOTH_BLOCK, mg_operator=mto.MG_OP_LEAD)
+    assert ei.value.status == 4
+    m = om.DPMesh(pr.nelx, pr.nely, pr.p, pr.d)
+    ofixed, of = om.mbb_bc(m)
+    K = osv.assemble(m, osv.element_matrices(m, pr.rho, pr.E0, pr.Emin, pr.nu, pr.q))
+    C_o = ose.compliance(of, osv.solve_direct(K, of, ofixed))
+    for sm in (mto.SMOOTH_BLOCK, mto.SMOOTH_JACOBI):
+        u.zero_()
+        h.solve(f, u, precision=mto.MTO_MIXED, rtol=1e-8, norm=mto.NORM_ENERGY, max_iter=40000, precond=mto.PREC_MG,
+                mg_degree=2, mg_smoother=sm)
+        C = float(f @ u)
+        assert abs(C - C_o) <= 1e-7 * abs(C_o), (sm, C, C_o)
+    h.close()
