@@ -1213,10 +1213,4 @@ mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const
                           dot_res, nullptr, r);
 }
 
-// y = A x on Q1 level l (y is written, not accumulated): the vertex stencil where it exists (the
-// smoothed levels; rounded to FP32 when the cycle runs on FP32 copies), else the element matrices
-mto_status mg_apply_level(mto_handle h, const MGLevel& l, const double* x, double* y, const int* done) {
-  return mg_level_apply(h, l, x, y, done);
-}
-
 }  // namespace mto

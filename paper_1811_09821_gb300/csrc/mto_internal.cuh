@@ -441,7 +441,6 @@ mto_status mg_setup(mto_handle h);                                      // hiera
 mto_status mg_set_masks(mto_handle h);                                  // supports on every level
 mto_status mg_build(mto_handle h);                                      // Galerkin operators, bounds
 mto_status mg_select_smoother(mto_handle h, int smoother);              // MTO_SMOOTH_* for next solves
-mto_status mg_apply_level(mto_handle h, const MGLevel& l, const double* x, double* y, const int* done);
 mto_status mg_vcycle(mto_handle h, const double* r, double* z, int degree, const int* done, double* dot_part,
                      unsigned* dot_cnt, double* dot_res);
 void mg_release(mto_handle h);
