@@ -344,7 +344,7 @@ mto_status mto_apply(mto_handle h, const double* x, double* y);
  *                 inner PCG of MTO_MIXED solves launches (needs the MTO_MIXED build);
  *   MTO_OP_LEAD   the pair's FP32 leading part alone (the hi rows, x rounded to FP32, FP32 sums per
  *                 element, FP64 assembly): the copy of the operator the multigrid cycle may apply
- *                 where it only needs a fixed operator (see mg_lead of mto_solve_opts; MTO_MIXED
+ *                 where it only needs a fixed operator (see mg_operator of mto_solve_opts; MTO_MIXED
  *                 build).  Entries differ from K by the FP32 rounding of the matrices.
  * x, y: device double[ndof].  *xKx (host, may be NULL: then asynchronous) receives x^T y as the
  * operator launches reduce it for CG (per order class, summed in class order).  Synchronises when
