@@ -68,3 +68,39 @@ def test_area_scaled_clip_sum():
         per = dv * np.minimum(np.maximum(t * c, lo), hi)
         scaled = np.minimum(np.maximum((dv * t) * c, dv * lo), dv * hi)
         assert np.allclose(per, scaled, rtol=4e-16, atol=0.0)
+
+
+def triangle_pair(t):
+    """The QR kernel's decode of a packed-triangle index (trailing-block pairs of the L D L^T
+    update, and the packed lower storage itself), as in the kernel: t = s (s + 1) / 2 + r with
+    0 <= r <= s, s first estimated in FP32 and then corrected."""
+    s = int((np.sqrt(np.float32(8.0) * np.float32(t) + np.float32(1.0)) - np.float32(1.0)) * np.float32(0.5))
+    while s * (s + 1) // 2 > t:
+        s -= 1
+    while (s + 1) * (s + 2) // 2 <= t:
+        s += 1
+    return s, t - s * (s + 1) // 2
+
+
+def test_packed_lower_index_round_trip():
+    """Row-major packed lower storage: index i (i + 1) / 2 + j decodes back to (i, j) for every entry
+    of the largest order-(p+1) matrix (n1 = 128, 8256 entries)."""
+    for i in range(128):
+        for j in range(i + 1):
+            assert triangle_pair(i * (i + 1) // 2 + j) == (i, j)
+
+
+def test_trailing_pairs_cover_the_block_once():
+    """Every pair (i, j), c < j <= i < n1, of the trailing block of pivot c comes from exactly one
+    t < m (m + 1) / 2 (m = n1 - 1 - c), for the element sizes of orders 2..7 (n1 = 2 (p+1)^2)."""
+    for n1 in (18, 32, 50, 72, 98, 128):
+        for c in range(n1):
+            m = n1 - 1 - c
+            seen = set()
+            for t in range(m * (m + 1) // 2):
+                s, r = triangle_pair(t)
+                assert 0 <= r <= s < m
+                i, j = n1 - 1 - r, n1 - 1 - s
+                assert c < j <= i < n1
+                seen.add((i, j))
+            assert len(seen) == m * (m + 1) // 2
